@@ -1,0 +1,189 @@
+/*
+ * lo_afqmc.h -- C ABI of the B300 (sm_103a) LO-AFQMC local-energy library.
+ *
+ * The library evaluates, for a batch of walkers, the phaseless-AFQMC local
+ * energy  E = <Phi_T|H|phi> / <Phi_T|phi>  of a single-determinant trial
+ * (Weber et al., arXiv 2202.00832, Sec. 2.1.1, generalized Wick form eq.
+ * 2e_general), through the half-rotated Cholesky vectors (Sec. 2.2, eq.
+ * 2e_HRchol_RCAS) -- the "full" path -- or with the exchange taken from the
+ * SVD-truncated localized-orbital pair blocks (Sec. 3.1, eqs. 2e_HR_RCAS_LO
+ * and 2e_HR_RCAS) -- the "LO" path.
+ *
+ * Conventions for every entry point
+ *   - Matrices are row-major, FP64 real or complex128 (re, im interleaved).
+ *   - M = basis size, X = number of Cholesky vectors, n_alpha / n_beta =
+ *     occupied orbitals per spin, W = walkers in a call.
+ *   - A closed shell (n_alpha == n_beta and no trial_b) uses one restricted
+ *     determinant per walker for both spins.
+ *   - "device" buffers are CUDA device pointers on the context's device;
+ *     "host" buffers are ordinary or pinned host memory.  Entry points that
+ *     accept either say so and detect the kind with cudaPointerGetAttributes.
+ *   - All GPU work is queued on the context's stream; calls return after the
+ *     results they write to host memory are complete.  Device outputs are
+ *     complete when the stream reaches the end of the call.
+ *   - Every call returns a loaf_status.  No call aborts, exits or traps on
+ *     the device; loaf_last_error() describes the most recent failure.
+ */
+#ifndef LO_AFQMC_H
+#define LO_AFQMC_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct loaf_ctx loaf_ctx; /* opaque; owns every device buffer it allocates */
+
+typedef enum {
+    LOAF_OK = 0,
+    LOAF_ERR_ARG = 1,         /* null pointer or out-of-range scalar argument */
+    LOAF_ERR_SHAPE = 2,       /* sizes inconsistent or beyond supported limits */
+    LOAF_ERR_CUDA = 3,        /* a CUDA runtime / library call failed */
+    LOAF_ERR_OOM = 4,         /* device allocation failed */
+    LOAF_ERR_SINGULAR = 5,    /* at least one walker overlap is singular */
+    LOAF_ERR_NOT_READY = 6,   /* required setup call has not been made */
+    LOAF_ERR_TIMEOUT = 7,     /* a bounded device wait gave up */
+    LOAF_ERR_NAN = 8,         /* non-finite input or result */
+    LOAF_ERR_UNSUPPORTED = 9  /* valid request this build does not provide */
+} loaf_status;
+
+enum { LOAF_MODE_FULL = 0, LOAF_MODE_LO = 1 };
+
+/*
+ * Arithmetic of the contractions (overlap, LU, log-det and Theta are FP64
+ * in every mode; so is the final per-walker accumulation):
+ *   LOAF_PREC_FP64   every step in FP64 (CUDA cores).
+ *   LOAF_PREC_FP16X3 Coulomb and LO-exchange contractions on the tcgen05
+ *                    tensor cores: operands split into FP16 hi + lo parts
+ *                    (power-of-two scaled), three products hi*hi + hi*lo +
+ *                    lo*hi accumulated in FP32, applied to Theta - Phi_T
+ *                    (the walker-independent trial part stays FP64).
+ *   LOAF_PREC_BF16X3 the same with BF16 hi + lo parts.
+ */
+enum { LOAF_PREC_FP64 = 0, LOAF_PREC_FP16X3 = 1, LOAF_PREC_BF16X3 = 2 };
+
+/* Per-walker status codes written to walker_status[] */
+enum { LOAF_WALKER_OK = 0, LOAF_WALKER_SINGULAR = 1, LOAF_WALKER_NAN = 2 };
+
+/* Supported limits of this build. */
+#define LOAF_MAX_NOCC 96      /* occupied orbitals per spin (LU held in shared memory) */
+#define LOAF_MAX_BASIS 1536
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (NULL: the context creates its own non-blocking stream).  On success *ctx
+ * owns no device memory yet. */
+loaf_status loaf_create(loaf_ctx **ctx, int device, void *cuda_stream);
+
+/* Free every device buffer and library handle the context owns. NULL is a no-op. */
+loaf_status loaf_destroy(loaf_ctx *ctx);
+
+/* Static description of a status code. */
+const char *loaf_status_str(loaf_status s);
+
+/* Message for the last failing call on this context (never NULL). */
+const char *loaf_last_error(const loaf_ctx *ctx);
+
+/*
+ * ao_load_cholesky -- load the Hamiltonian and the trial; half-rotate.
+ *
+ * Sec. 2.1 (H = sum h_pq c+_p c_q + 1/2 sum V_pqrs ..., V_pqrs = sum_g
+ * L^g_pr L^g_qs) and Sec. 2.2 (Lbar^g_ir = sum_p L^g_rp Phi_T,pi, computed
+ * once before propagation).
+ *   h        M x M, symmetric one-body matrix
+ *   L        X x M x M, each slice symmetric (Cholesky vectors)
+ *   trial_a  M x n_alpha, orthonormal columns (real trial determinant)
+ *   trial_b  M x n_beta, or NULL for a closed shell (n_beta == n_alpha)
+ *   e0       constant added to every energy
+ *   inputs_on_device  0: the four arrays are host memory; 1: device memory.
+ * The arrays are copied; the caller keeps ownership.  Re-calling replaces the
+ * system and drops any LO compression.  Errors: LOAF_ERR_SHAPE for M, X,
+ * n_alpha, n_beta outside (1..LOAF_MAX_BASIS, 1.., 1..min(M, LOAF_MAX_NOCC));
+ * LOAF_ERR_OOM when the device cannot hold L.
+ */
+loaf_status ao_load_cholesky(loaf_ctx *ctx, int M, int X, const double *h, const double *L,
+                             int n_alpha, int n_beta, const double *trial_a,
+                             const double *trial_b, double e0, int inputs_on_device);
+
+/*
+ * lo_localize_compress -- Foster-Boys localization and pair compression.
+ *
+ * Sec. 4 (Foster-Boys localization of the occupied orbitals) and Sec. 3.1.1:
+ * for every pair i <= j of localized orbitals the M x M block
+ * Y^[ij]_rs = sum_g Lbar^g_ir Lbar^g_js is factorised by SVD and truncated,
+ * keeping the singular values s >= t_svd (absolute, Hartree):
+ * Y^[ij] ~= Ubar Vbar with Ubar = U sqrt(s), Vbar = sqrt(s) V^T.
+ *   t_svd     >= 0; 0 keeps every singular value (exact)
+ *   r_ops     n_ops x M x M symmetric position-operator matrices in the
+ *             orthonormal basis (host memory), e.g. diag(x), diag(y), diag(z)
+ *   localize  1: Boys-localize first; 0: keep the canonical trial orbitals
+ *   compression_pct  out (host, may be NULL): (M - <M_SVD>)/M*100 over all
+ *             pairs and spins (Sec. 4)
+ *   m_svd_per_pair   out (host, may be NULL): kept rank of every pair, spin
+ *             alpha pairs (0,0),(0,1)..(0,N-1),(1,1).. then spin beta
+ * May be re-called with another t_svd or localize; the SVDs are recomputed.
+ * Errors: LOAF_ERR_NOT_READY before ao_load_cholesky.
+ */
+loaf_status lo_localize_compress(loaf_ctx *ctx, double t_svd, const double *r_ops, int n_ops,
+                                 int localize, double *compression_pct, int *m_svd_per_pair);
+
+/*
+ * walkers_energy -- local energies of W walkers (the hot path).
+ *
+ * For each walker: S = Phi_T^T phi (per spin), partial-pivot LU of S,
+ * log det S, Theta = phi S^-1 (eq. Q), then E = e0 + E1 + E_J - E_K with the
+ * one-body E1 = sum_sigma sum_ir hbar_ir Theta_ri, the Coulomb
+ * E_J = 1/2 sum_g (sum_sigma tr Lbar^sigma_g Theta^sigma)^2 and the exchange
+ * E_K = 1/2 sum_sigma sum_g tr(T T), T = Lbar^sigma_g Theta^sigma (mode FULL,
+ * eq. 2e_HRchol_RCAS) or E_K = 1/2 sum_sigma sum_ij e_ij with
+ * e_ij = (Ubar^[ij]T Theta_j).(Vbar^[ij] Theta_i) (mode LO, eq. 2e_HR_RCAS_LO).
+ *   W          >= 1 walkers
+ *   phi        W x M x Ntot complex128, Ntot = n_alpha (closed shell) or
+ *              n_alpha + n_beta (alpha columns first); host or device
+ *   mode       LOAF_MODE_FULL or LOAF_MODE_LO (LO needs lo_localize_compress)
+ *   precision  LOAF_PREC_*; the full mode supports FP64 and FP16X3/BF16X3
+ *              (Coulomb on tensor cores, exchange FP64)
+ *   e_out      W complex128 energies (host or device)
+ *   logdet_out W complex128 log <Phi_T|phi> = sum_sigma log det S^sigma, or NULL
+ *   walker_status  W ints (host or device), or NULL
+ * A singular overlap marks that walker LOAF_WALKER_SINGULAR, writes NaN to
+ * its energy and makes the call return LOAF_ERR_SINGULAR after finishing the
+ * others.  Workspace grows to the largest W seen and is kept by the context.
+ */
+loaf_status walkers_energy(loaf_ctx *ctx, int W, const void *phi, int mode, int precision,
+                           void *e_out, void *logdet_out, int *walker_status);
+
+/*
+ * walkers_theta -- the first stage alone: Theta = phi (Phi_T^T phi)^-1 and
+ * log det, per spin (eq. Q).  theta_out: W x Ntot x M complex128 (orbital-
+ * major: theta_out[w][i][r] = Theta_ri), logdet_out: W complex128.  The
+ * trial is the canonical one, or the localized one after
+ * lo_localize_compress(localize=1) (Theta changes by that rotation).
+ * Buffers host or device.
+ */
+loaf_status walkers_theta(loaf_ctx *ctx, int W, const void *phi, void *theta_out,
+                          void *logdet_out, int *walker_status);
+
+/*
+ * walkers_pair_exchange -- the LO pair values e^sigma_ij(w) of eq. 2e_HR_RCAS
+ * (exchange part), unweighted, for every stored pair i <= j.
+ *   e_pairs_out  n_pairs_total x W complex128 (pair-major; pair order as in
+ *                m_svd_per_pair), host or device
+ */
+loaf_status walkers_pair_exchange(loaf_ctx *ctx, int W, const void *phi, int precision,
+                                  void *e_pairs_out);
+
+/* Number of stored pairs over all spins (0 before lo_localize_compress). */
+int loaf_num_pairs(const loaf_ctx *ctx);
+
+/*
+ * lo_get_localized_trial -- copy the trial orbitals the LO factors were built
+ * from (M x n_sigma, host) for spin 0 (alpha) or 1 (beta).
+ */
+loaf_status lo_get_localized_trial(const loaf_ctx *ctx, int spin, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LO_AFQMC_H */

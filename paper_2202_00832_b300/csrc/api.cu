@@ -1,0 +1,329 @@
+// C ABI entry points (declared in include/lo_afqmc.h): argument checks,
+// host/device buffer staging, workspace management and stage dispatch.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+using namespace loaf;
+
+namespace {
+
+template <class F>
+loaf_status guarded(loaf_ctx* c, F&& f) {
+    try {
+        f();
+        if (c) c->err.clear();
+        return LOAF_OK;
+    } catch (const Error& e) {
+        if (c) c->err = e.msg;
+        return e.code;
+    } catch (const std::exception& e) {
+        if (c) c->err = e.what();
+        return LOAF_ERR_CUDA;
+    }
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // plain host memory on older drivers
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// per-walker status / logdet / energy from the per-spin parts
+__global__ void finalize_kernel(int W, int nspin, double m0, double m1, double e0,
+                                const double2* __restrict__ ld_part, const int* __restrict__ st_part,
+                                const double2* __restrict__ e1, const double2* __restrict__ ej,
+                                const double2* __restrict__ ek, double2* __restrict__ e_out,
+                                double2* __restrict__ ld_out, int* __restrict__ st_out,
+                                int* __restrict__ any_bad) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    int st = st_part[w];
+    double2 ld = cscale(ld_part[w], m0 == 2.0 ? 2.0 : 1.0);
+    if (nspin > 1) {
+        st = max(st, st_part[W + w]);
+        ld = cadd(ld, ld_part[W + w]);
+    }
+    (void)m1;
+    double2 e = make_double2(e0, 0.0);
+    if (e1) e = cadd(e, e1[w]);
+    if (ej) e = cadd(e, ej[w]);
+    if (ek) e = csub(e, ek[w]);
+    if (st == LOAF_WALKER_OK && !(isfinite(e.x) && isfinite(e.y))) st = LOAF_WALKER_NAN;
+    if (st != LOAF_WALKER_OK) {
+        const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+        e = make_double2(qnan, qnan);
+        atomicMax(any_bad, st);
+    }
+    if (e_out) e_out[w] = e;
+    if (ld_out) ld_out[w] = ld;
+    if (st_out) st_out[w] = st;
+}
+
+struct Staged {
+    const double2* phi = nullptr;  // device copy of the walkers
+};
+
+// Workspace sized for W walkers (grown, never shrunk).
+void ensure_workspace(loaf_ctx* c, int W, int mode) {
+    const size_t wm = (size_t)W * c->ntot * c->M;
+    c->w_phi.ensure(wm * sizeof(double2));
+    c->w_theta.ensure(wm * sizeof(double2));
+    c->w_z.ensure(wm * sizeof(double2));
+    c->w_logdet.ensure((size_t)2 * W * sizeof(double2));
+    c->w_status.ensure((size_t)2 * W * sizeof(int) + 16);
+    c->w_out.ensure((size_t)3 * W * sizeof(double2));
+    c->w_part2.ensure((size_t)W * (c->X + 1) * sizeof(double2));
+    c->w_host_stage.ensure((size_t)W * (2 * sizeof(double2) + sizeof(int)) + 64);
+    if (mode == LOAF_MODE_LO) {
+        long np = 0;
+        for (int s = 0; s < c->nspin; ++s) np += c->sp[s].pairs.npairs;
+        c->w_part.ensure((size_t)std::max<long>(np, 1) * W * sizeof(double2));
+    }
+    c->ws_W = std::max(c->ws_W, W);
+}
+
+const double2* stage_walkers(loaf_ctx* c, int W, const void* phi) {
+    const size_t bytes = (size_t)W * c->M * c->ntot * sizeof(double2);
+    if (is_device_ptr(phi)) return static_cast<const double2*>(phi);
+    LOAF_CUDA(cudaMemcpyAsync(c->w_phi.ptr, phi, bytes, cudaMemcpyHostToDevice, c->stream));
+    return c->w_phi.as<double2>();
+}
+
+// copy a device result to a user buffer that may live on the host
+void deliver(loaf_ctx* c, void* user, const void* dev, size_t bytes) {
+    if (!user) return;
+    if (is_device_ptr(user)) {
+        if (user != dev)
+            LOAF_CUDA(cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        LOAF_CUDA(cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
+    }
+}
+
+void check_ready(loaf_ctx* c, int W, const void* phi, int mode, int precision) {
+    LOAF_REQUIRE(c->loaded, LOAF_ERR_NOT_READY, "ao_load_cholesky has not been called");
+    LOAF_REQUIRE(W >= 1, LOAF_ERR_ARG, "W must be >= 1");
+    LOAF_REQUIRE(phi != nullptr, LOAF_ERR_ARG, "phi is NULL");
+    LOAF_REQUIRE(mode == LOAF_MODE_FULL || mode == LOAF_MODE_LO, LOAF_ERR_ARG, "unknown mode");
+    LOAF_REQUIRE(precision == LOAF_PREC_FP64 || precision == LOAF_PREC_FP16X3 ||
+                     precision == LOAF_PREC_BF16X3,
+                 LOAF_ERR_ARG, "unknown precision");
+    LOAF_REQUIRE(mode != LOAF_MODE_LO || c->compressed, LOAF_ERR_NOT_READY,
+                 "LO mode needs lo_localize_compress");
+}
+
+// Theta for all walkers; returns 1 if any walker is singular or non-finite
+void stage_theta(loaf_ctx* c, int W, const double2* phi) {
+    run_theta_fp64(c, W, phi, c->w_theta.as<double2>(), c->w_logdet.as<double2>(),
+                   c->w_status.as<int>());
+}
+
+}  // namespace
+
+extern "C" {
+
+loaf_status loaf_create(loaf_ctx** out, int device, void* cuda_stream) {
+    if (!out) return LOAF_ERR_ARG;
+    *out = nullptr;
+    loaf_ctx* c = new (std::nothrow) loaf_ctx();
+    if (!c) return LOAF_ERR_OOM;
+    loaf_status st = guarded(c, [&] {
+        int n = 0;
+        LOAF_CUDA(cudaGetDeviceCount(&n));
+        LOAF_REQUIRE(device >= 0 && device < n, LOAF_ERR_ARG, "no such CUDA device");
+        c->device = device;
+        LOAF_CUDA(cudaSetDevice(device));
+        LOAF_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+        if (cuda_stream) {
+            c->stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            LOAF_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+            c->own_stream = true;
+        }
+        LOAF_CUBLAS(cublasCreate(&c->cublas));
+        LOAF_CUBLAS(cublasSetStream(c->cublas, c->stream));
+        LOAF_CUSOLVER(cusolverDnCreate(&c->cusolver));
+        LOAF_CUSOLVER(cusolverDnSetStream(c->cusolver, c->stream));
+    });
+    if (st != LOAF_OK) {
+        loaf_destroy(c);
+        return st;
+    }
+    *out = c;
+    return LOAF_OK;
+}
+
+loaf_status loaf_destroy(loaf_ctx* c) {
+    if (!c) return LOAF_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& s : c->sp) s.release();
+    c->d_h.release(); c->d_L.release();
+    for (loaf::DevBuf* b : {&c->w_phi, &c->w_theta, &c->w_z, &c->w_lu, &c->w_perm, &c->w_logdet,
+                            &c->w_status, &c->w_out, &c->w_part, &c->w_part2, &c->w_dhi,
+                            &c->w_dlo, &c->w_dscale, &c->w_host_stage})
+        b->release();
+    if (c->cublas) cublasDestroy(c->cublas);
+    if (c->cusolver) cusolverDnDestroy(c->cusolver);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return LOAF_OK;
+}
+
+const char* loaf_status_str(loaf_status s) {
+    switch (s) {
+        case LOAF_OK: return "ok";
+        case LOAF_ERR_ARG: return "invalid argument";
+        case LOAF_ERR_SHAPE: return "invalid or unsupported shape";
+        case LOAF_ERR_CUDA: return "CUDA error";
+        case LOAF_ERR_OOM: return "out of device memory";
+        case LOAF_ERR_SINGULAR: return "singular walker overlap";
+        case LOAF_ERR_NOT_READY: return "setup call missing";
+        case LOAF_ERR_TIMEOUT: return "bounded device wait gave up";
+        case LOAF_ERR_NAN: return "non-finite value";
+        case LOAF_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+const char* loaf_last_error(const loaf_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+loaf_status ao_load_cholesky(loaf_ctx* c, int M, int X, const double* h, const double* L,
+                             int n_alpha, int n_beta, const double* trial_a,
+                             const double* trial_b, double e0, int inputs_on_device) {
+    if (!c) return LOAF_ERR_ARG;
+    return guarded(c, [&] {
+        LOAF_CUDA(cudaSetDevice(c->device));
+        setup_load(c, M, X, h, L, n_alpha, n_beta, trial_a, trial_b, e0, inputs_on_device);
+    });
+}
+
+loaf_status lo_localize_compress(loaf_ctx* c, double t_svd, const double* r_ops, int n_ops,
+                                 int localize, double* compression_pct, int* m_svd_per_pair) {
+    if (!c) return LOAF_ERR_ARG;
+    return guarded(c, [&] {
+        LOAF_CUDA(cudaSetDevice(c->device));
+        setup_compress(c, t_svd, r_ops, n_ops, localize, compression_pct, m_svd_per_pair);
+    });
+}
+
+int loaf_num_pairs(const loaf_ctx* c) {
+    if (!c || !c->compressed) return 0;
+    int n = 0;
+    for (int s = 0; s < c->nspin; ++s) n += c->sp[s].pairs.npairs;
+    return n;
+}
+
+loaf_status lo_get_localized_trial(const loaf_ctx* c, int spin, double* out) {
+    if (!c || !out) return LOAF_ERR_ARG;
+    if (!c->loaded) return LOAF_ERR_NOT_READY;
+    if (spin < 0 || spin >= c->nspin) return LOAF_ERR_ARG;
+    std::memcpy(out, c->sp[spin].h_trial.data(), c->sp[spin].h_trial.size() * sizeof(double));
+    return LOAF_OK;
+}
+
+loaf_status walkers_theta(loaf_ctx* c, int W, const void* phi, void* theta_out, void* logdet_out,
+                          int* walker_status) {
+    if (!c) return LOAF_ERR_ARG;
+    int bad = 0;
+    loaf_status st = guarded(c, [&] {
+        LOAF_CUDA(cudaSetDevice(c->device));
+        check_ready(c, W, phi, LOAF_MODE_FULL, LOAF_PREC_FP64);
+        ensure_workspace(c, W, LOAF_MODE_FULL);
+        const double2* dphi = stage_walkers(c, W, phi);
+        stage_theta(c, W, dphi);
+        double2* dld = c->w_host_stage.as<double2>();
+        int* dst = reinterpret_cast<int*>(dld + W);
+        int* dbad = dst + W;
+        LOAF_CUDA(cudaMemsetAsync(dbad, 0, sizeof(int), c->stream));
+        finalize_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
+            W, c->nspin, c->sp[0].mult, c->nspin > 1 ? c->sp[1].mult : 0.0, 0.0,
+            c->w_logdet.as<double2>(), c->w_status.as<int>(), nullptr, nullptr, nullptr, nullptr,
+            dld, dst, dbad);
+        LOAF_LAUNCH_CHECK();
+        deliver(c, theta_out, c->w_theta.ptr, (size_t)W * c->ntot * c->M * sizeof(double2));
+        deliver(c, logdet_out, dld, (size_t)W * sizeof(double2));
+        deliver(c, walker_status, dst, (size_t)W * sizeof(int));
+        LOAF_CUDA(cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        LOAF_CUDA(cudaStreamSynchronize(c->stream));
+    });
+    if (st == LOAF_OK && bad) {
+        c->err = "at least one walker overlap is singular or non-finite";
+        return bad == LOAF_WALKER_SINGULAR ? LOAF_ERR_SINGULAR : LOAF_ERR_NAN;
+    }
+    return st;
+}
+
+loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int precision,
+                           void* e_out, void* logdet_out, int* walker_status) {
+    if (!c) return LOAF_ERR_ARG;
+    int bad = 0;
+    loaf_status st = guarded(c, [&] {
+        LOAF_CUDA(cudaSetDevice(c->device));
+        check_ready(c, W, phi, mode, precision);
+        LOAF_REQUIRE(e_out != nullptr, LOAF_ERR_ARG, "e_out is NULL");
+        ensure_workspace(c, W, mode);
+        const double2* dphi = stage_walkers(c, W, phi);
+        stage_theta(c, W, dphi);
+        double2* e1 = c->w_out.as<double2>();
+        double2* ej = e1 + W;
+        double2* ek = ej + W;
+        if (precision == LOAF_PREC_FP64) {
+            run_coulomb_fp64(c, W, c->w_theta.as<double2>(), e1);
+            if (mode == LOAF_MODE_FULL)
+                run_energy_fp64_full(c, W, c->w_theta.as<double2>(), ek);
+            else
+                run_energy_fp64_lo(c, W, c->w_theta.as<double2>(), ek, c->w_part.as<double2>());
+        } else {
+            run_energy_mixed(c, W, mode, precision, c->w_theta.as<double2>(), e1, nullptr);
+        }
+        double2* de = c->w_host_stage.as<double2>();
+        double2* dld = de + W;
+        int* dst = reinterpret_cast<int*>(dld + W);
+        int* dbad = dst + W;
+        LOAF_CUDA(cudaMemsetAsync(dbad, 0, sizeof(int), c->stream));
+        finalize_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
+            W, c->nspin, c->sp[0].mult, c->nspin > 1 ? c->sp[1].mult : 0.0, c->e0,
+            c->w_logdet.as<double2>(), c->w_status.as<int>(), e1, ej, ek, de, dld, dst, dbad);
+        LOAF_LAUNCH_CHECK();
+        deliver(c, e_out, de, (size_t)W * sizeof(double2));
+        deliver(c, logdet_out, dld, (size_t)W * sizeof(double2));
+        deliver(c, walker_status, dst, (size_t)W * sizeof(int));
+        LOAF_CUDA(cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        LOAF_CUDA(cudaStreamSynchronize(c->stream));
+    });
+    if (st == LOAF_OK && bad) {
+        c->err = "at least one walker overlap is singular or non-finite";
+        return bad == LOAF_WALKER_SINGULAR ? LOAF_ERR_SINGULAR : LOAF_ERR_NAN;
+    }
+    return st;
+}
+
+loaf_status walkers_pair_exchange(loaf_ctx* c, int W, const void* phi, int precision,
+                                  void* e_pairs_out) {
+    if (!c) return LOAF_ERR_ARG;
+    return guarded(c, [&] {
+        LOAF_CUDA(cudaSetDevice(c->device));
+        check_ready(c, W, phi, LOAF_MODE_LO, precision);
+        LOAF_REQUIRE(e_pairs_out != nullptr, LOAF_ERR_ARG, "e_pairs_out is NULL");
+        ensure_workspace(c, W, LOAF_MODE_LO);
+        const double2* dphi = stage_walkers(c, W, phi);
+        stage_theta(c, W, dphi);
+        if (precision == LOAF_PREC_FP64)
+            run_energy_fp64_lo(c, W, c->w_theta.as<double2>(), nullptr, c->w_part.as<double2>());
+        else
+            run_energy_mixed(c, W, LOAF_MODE_LO, precision, c->w_theta.as<double2>(), nullptr,
+                             c->w_part.as<double2>());
+        deliver(c, e_pairs_out, c->w_part.ptr, (size_t)loaf_num_pairs(c) * W * sizeof(double2));
+        LOAF_CUDA(cudaStreamSynchronize(c->stream));
+    });
+}
+
+}  // extern "C"

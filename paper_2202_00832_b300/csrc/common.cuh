@@ -1,0 +1,215 @@
+// Shared definitions of the LO-AFQMC CUDA library: the context, status
+// plumbing and small device helpers.  Every kernel and host routine of the
+// library includes this file; nothing here is visible through the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/lo_afqmc.h"
+
+namespace loaf {
+
+// ---------------------------------------------------------------------------
+// status plumbing
+// ---------------------------------------------------------------------------
+
+struct Error {
+    loaf_status code;
+    std::string msg;
+};
+
+#define LOAF_CUDA(call)                                                              \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            throw ::loaf::Error{e_ == cudaErrorMemoryAllocation ? LOAF_ERR_OOM       \
+                                                                : LOAF_ERR_CUDA,     \
+                                std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+        }                                                                            \
+    } while (0)
+
+#define LOAF_CUBLAS(call)                                                            \
+    do {                                                                             \
+        cublasStatus_t s_ = (call);                                                  \
+        if (s_ != CUBLAS_STATUS_SUCCESS)                                             \
+            throw ::loaf::Error{LOAF_ERR_CUDA,                                       \
+                                std::string(#call) + ": cublas status " +            \
+                                    std::to_string((int)s_)};                        \
+    } while (0)
+
+#define LOAF_CUSOLVER(call)                                                          \
+    do {                                                                             \
+        cusolverStatus_t s_ = (call);                                                \
+        if (s_ != CUSOLVER_STATUS_SUCCESS)                                           \
+            throw ::loaf::Error{LOAF_ERR_CUDA,                                       \
+                                std::string(#call) + ": cusolver status " +          \
+                                    std::to_string((int)s_)};                        \
+    } while (0)
+
+#define LOAF_REQUIRE(cond, code, text)                       \
+    do {                                                     \
+        if (!(cond)) throw ::loaf::Error{(code), (text)};    \
+    } while (0)
+
+#define LOAF_LAUNCH_CHECK() LOAF_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------------------
+// device buffers owned by the context
+// ---------------------------------------------------------------------------
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+    // grow (never shrink); contents are not preserved
+    void ensure(size_t nbytes) {
+        if (nbytes <= bytes) return;
+        release();
+        LOAF_CUDA(cudaMalloc(&ptr, nbytes));
+        bytes = nbytes;
+    }
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// ---------------------------------------------------------------------------
+// per-spin data
+// ---------------------------------------------------------------------------
+
+// Split-precision copy of a row-major FP64 matrix: rows x cols values in four
+// planes hi/lo (16-bit floats, FP16 or BF16 by `bf16`), each row scaled by a
+// power of two (value = (hi + lo) / scale[row]).  Rows are padded to `ld`
+// columns with zeros so every row starts on a 16-byte boundary.
+struct SplitMatrix {
+    int rows = 0, cols = 0, ld = 0;
+    bool bf16 = false;
+    DevBuf hi, lo, scale;  // hi/lo: rows x ld 16-bit; scale: rows doubles
+    void release() { hi.release(); lo.release(); scale.release(); rows = cols = ld = 0; }
+};
+
+struct PairTable {
+    int npairs = 0;
+    long rows = 0;                     // sum of K over pairs
+    std::vector<int> i, j, K;          // host copies
+    std::vector<long> off;             // first packed row of each pair
+    DevBuf d_i, d_j, d_K, d_off;       // device copies (int, int, int, long)
+    DevBuf d_U, d_V;                   // FP64: rows x M (row k of Ubar^T, row k of Vbar)
+    // mixed-precision operands (built lazily for FP16X3 / BF16X3)
+    SplitMatrix sU[2], sV[2];          // index 0: FP16, 1: BF16
+    DevBuf d_p, d_q;                   // FP64 rows: p = Ubar^T Phi_j, q = Vbar Phi_i
+    DevBuf d_e0;                       // FP64 per pair: p . q
+    void release() {
+        d_i.release(); d_j.release(); d_K.release(); d_off.release();
+        d_U.release(); d_V.release();
+        for (auto& s : sU) s.release();
+        for (auto& s : sV) s.release();
+        d_p.release(); d_q.release(); d_e0.release();
+        npairs = 0; rows = 0; i.clear(); j.clear(); K.clear(); off.clear();
+    }
+};
+
+struct SpinData {
+    int N = 0;             // occupied orbitals of this spin
+    int col0 = 0;          // first column of this spin inside a packed walker
+    double mult = 1.0;     // 2 for a restricted closed shell, else 1
+    std::vector<double> h_trial;  // M x N current trial (canonical or localized)
+    DevBuf d_trial;        // M x N FP64
+    DevBuf d_Lbar;         // X x N x M FP64
+    DevBuf d_hbar;         // N x M FP64
+    SplitMatrix sLbar[2];  // (X+1) x (N*M) rows gamma (last row hbar); FP16 / BF16
+    DevBuf d_J0;           // X doubles: tr(Lbar_g Phi) (trial Coulomb vector)
+    double E1_0 = 0.0;     // sum_ir hbar_ir Phi_ri
+    PairTable pairs;
+    void release() {
+        d_trial.release(); d_Lbar.release(); d_hbar.release();
+        for (auto& s : sLbar) s.release();
+        d_J0.release();
+        pairs.release();
+    }
+};
+
+}  // namespace loaf
+
+// ---------------------------------------------------------------------------
+// the context
+// ---------------------------------------------------------------------------
+
+struct loaf_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cublasHandle_t cublas = nullptr;
+    cusolverDnHandle_t cusolver = nullptr;
+    int sm_count = 0;
+
+    bool loaded = false;
+    bool compressed = false;
+    bool localized = false;
+    double t_svd = 0.0;
+    int M = 0, X = 0, na = 0, nb = 0, nspin = 0, ntot = 0;
+    bool closed = false;
+    double e0 = 0.0;
+    double trial_E_J = 0.0;  // walker-independent parts (mixed mode)
+    loaf::DevBuf d_h, d_L;
+    loaf::SpinData sp[2];
+    std::vector<double> canonical[2];  // trial orbitals as loaded (host)
+
+    // workspace for walkers_energy (grown to the largest W seen)
+    int ws_W = 0;
+    loaf::DevBuf w_phi, w_theta, w_z, w_lu, w_perm, w_logdet, w_status, w_out, w_part,
+        w_part2, w_dhi, w_dlo, w_dscale, w_host_stage;
+
+    std::string err;
+};
+
+namespace loaf {
+
+// complex helpers on double2
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ inline double2 cdiv(double2 a, double2 b) {
+    // Smith's algorithm keeps the intermediate in range
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, d = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    } else {
+        double r = b.x / b.y, d = b.x * r + b.y;
+        return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+    }
+}
+
+inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+// kernels and host stages (defined in the .cu files)
+void run_theta_fp64(loaf_ctx* c, int W, const double2* phi, double2* theta, double2* logdet,
+                    int* status);
+void run_energy_fp64_full(loaf_ctx* c, int W, const double2* theta, double2* e_out);
+void run_energy_fp64_lo(loaf_ctx* c, int W, const double2* theta, double2* e_out,
+                        double2* e_pairs);
+void run_coulomb_fp64(loaf_ctx* c, int W, const double2* theta, double2* e_part);
+void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2* theta,
+                      double2* e_out, double2* e_pairs);
+void setup_load(loaf_ctx* c, int M, int X, const double* h, const double* L, int na, int nb,
+                const double* ta, const double* tb, double e0, int on_device);
+void setup_compress(loaf_ctx* c, double t_svd, const double* r_ops, int n_ops, int localize,
+                    double* pct, int* m_svd);
+void setup_mixed_operands(loaf_ctx* c, int mode, bool bf16);
+void half_rotate(loaf_ctx* c, SpinData& s);
+
+}  // namespace loaf

@@ -1,0 +1,243 @@
+"""ctypes binding of liblo_afqmc.so (argument marshalling only).
+
+Every function here forwards to the C ABI declared in include/lo_afqmc.h.
+Arrays may be numpy arrays (host memory) or CUDA torch tensors (device
+memory on the context's device); their data pointers are passed as they are.
+No arithmetic of the method happens in Python.  The shared library must have
+been built (``python -m paper_2202_00832_b300.build``); loading fails loudly
+otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblo_afqmc.so")
+
+MODE_FULL, MODE_LO = 0, 1
+PREC_FP64, PREC_FP16X3, PREC_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp64": PREC_FP64, "fp16x3": PREC_FP16X3, "bf16x3": PREC_BF16X3}
+MODES = {"full": MODE_FULL, "lo": MODE_LO}
+
+STATUS = {0: "LOAF_OK", 1: "LOAF_ERR_ARG", 2: "LOAF_ERR_SHAPE", 3: "LOAF_ERR_CUDA",
+          4: "LOAF_ERR_OOM", 5: "LOAF_ERR_SINGULAR", 6: "LOAF_ERR_NOT_READY",
+          7: "LOAF_ERR_TIMEOUT", 8: "LOAF_ERR_NAN", 9: "LOAF_ERR_UNSUPPORTED"}
+
+# (name, restype, argtypes) of every exported entry point
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+SIGNATURES = [
+    ("loaf_create", _I, [ctypes.POINTER(_P), _I, _P]),
+    ("loaf_destroy", _I, [_P]),
+    ("loaf_status_str", ctypes.c_char_p, [_I]),
+    ("loaf_last_error", ctypes.c_char_p, [_P]),
+    ("ao_load_cholesky", _I, [_P, _I, _I, _P, _P, _I, _I, _P, _P, _D, _I]),
+    ("lo_localize_compress", _I, [_P, _D, _P, _I, _I, _P, _P]),
+    ("walkers_energy", _I, [_P, _I, _P, _I, _I, _P, _P, _P]),
+    ("walkers_theta", _I, [_P, _I, _P, _P, _P, _P]),
+    ("walkers_pair_exchange", _I, [_P, _I, _P, _I, _P]),
+    ("loaf_num_pairs", _I, [_P]),
+    ("lo_get_localized_trial", _I, [_P, _I, _P]),
+]
+
+_lib = None
+
+
+class LoafError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+
+
+def load_library(path: str = LIB_PATH):
+    """Load (once) and return the shared library; raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: build it with "
+                           "`python -m paper_2202_00832_b300.build` (there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a) -> Optional[int]:
+    """Data pointer of a numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)!r}")
+
+
+def _check_dtype(a, kind: str):
+    if a is None:
+        return
+    if isinstance(a, np.ndarray):
+        want = {"f8": np.float64, "c16": np.complex128, "i4": np.int32}[kind]
+        if a.dtype != want:
+            raise TypeError(f"expected {np.dtype(want)}, got {a.dtype}")
+    else:
+        import torch
+        want = {"f8": torch.float64, "c16": torch.complex128, "i4": torch.int32}[kind]
+        if a.dtype != want:
+            raise TypeError(f"expected {want}, got {a.dtype}")
+
+
+class Context:
+    """One loaf_ctx: a loaded system on one device and its workspace."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        lib = load_library()
+        self._lib = lib
+        h = _P()
+        self._check(lib.loaf_create(ctypes.byref(h), device, stream), "loaf_create", None)
+        self._h = h
+        self.M = self.X = self.n_alpha = self.n_beta = 0
+        self.closed = True
+
+    def _check(self, code: int, where: str, h=...):
+        if code != 0:
+            handle = self._h if h is ... else h
+            msg = self._lib.loaf_last_error(handle).decode() if handle else ""
+            raise LoafError(code, where, msg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.loaf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- setup ------------------------------------------------------------
+    def ao_load_cholesky(self, h, L, trial_a, trial_b=None, e0: float = 0.0,
+                         on_device: bool = False):
+        for a in (h, L, trial_a, trial_b):
+            _check_dtype(a, "f8")
+        M = int(h.shape[0])
+        X = int(L.shape[0])
+        na = int(trial_a.shape[1])
+        nb = int(trial_b.shape[1]) if trial_b is not None else na
+        self._check(self._lib.ao_load_cholesky(self._h, M, X, _ptr(h), _ptr(L), na, nb,
+                                               _ptr(trial_a), _ptr(trial_b), float(e0),
+                                               int(on_device)), "ao_load_cholesky")
+        self.M, self.X, self.n_alpha, self.n_beta = M, X, na, nb
+        self.closed = trial_b is None
+        return self
+
+    def load_molecule(self, mol, e0: float = 0.0):
+        """Load a synthetic molecule (closed shells use one restricted trial)."""
+        return self.ao_load_cholesky(mol.h, mol.L, mol.trial_a,
+                                     None if mol.closed_shell else mol.trial_b, e0)
+
+    def lo_localize_compress(self, t_svd: float, r_ops: Optional[np.ndarray] = None,
+                             localize: bool = True):
+        """Returns (compression_pct, m_svd_per_pair)."""
+        n_ops = 0
+        if r_ops is not None:
+            _check_dtype(r_ops, "f8")
+            n_ops = int(r_ops.shape[0])
+        npairs = self.n_alpha * (self.n_alpha + 1) // 2
+        if not self.closed:
+            npairs += self.n_beta * (self.n_beta + 1) // 2
+        pct = ctypes.c_double(0.0)
+        msvd = np.zeros(npairs, dtype=np.int32)
+        self._check(self._lib.lo_localize_compress(self._h, float(t_svd), _ptr(r_ops), n_ops,
+                                                   int(localize), ctypes.byref(pct), _ptr(msvd)),
+                    "lo_localize_compress")
+        return pct.value, msvd
+
+    def localized_trial(self, spin: int = 0) -> np.ndarray:
+        n = self.n_alpha if spin == 0 else self.n_beta
+        out = np.zeros((self.M, n))
+        self._check(self._lib.lo_get_localized_trial(self._h, spin, _ptr(out)),
+                    "lo_get_localized_trial")
+        return out
+
+    @property
+    def num_pairs(self) -> int:
+        return int(self._lib.loaf_num_pairs(self._h))
+
+    @property
+    def ntot(self) -> int:
+        return self.n_alpha if self.closed else self.n_alpha + self.n_beta
+
+    # -- hot path -----------------------------------------------------------
+    def walkers_energy(self, phi, mode="lo", precision="fp64", e_out=None, logdet_out=None,
+                       walker_status=None, raise_on_singular: bool = True):
+        """Energies of W walkers.  Host arrays in -> host arrays out by default."""
+        _check_dtype(phi, "c16")
+        W = int(phi.shape[0])
+        if e_out is None:
+            e_out = np.zeros(W, dtype=np.complex128)
+        if logdet_out is None and isinstance(phi, np.ndarray):
+            logdet_out = np.zeros(W, dtype=np.complex128)
+        if walker_status is None and isinstance(phi, np.ndarray):
+            walker_status = np.zeros(W, dtype=np.int32)
+        code = self._lib.walkers_energy(self._h, W, _ptr(phi), MODES.get(mode, mode),
+                                        PRECISIONS.get(precision, precision), _ptr(e_out),
+                                        _ptr(logdet_out), _ptr(walker_status))
+        if code == 5 and not raise_on_singular:
+            return e_out, logdet_out, walker_status
+        self._check(code, "walkers_energy")
+        return e_out, logdet_out, walker_status
+
+    def walkers_theta(self, phi, theta_out=None, logdet_out=None, walker_status=None,
+                      raise_on_singular: bool = True):
+        _check_dtype(phi, "c16")
+        W = int(phi.shape[0])
+        if theta_out is None:
+            theta_out = np.zeros((W, self.ntot, self.M), dtype=np.complex128)
+        if logdet_out is None:
+            logdet_out = np.zeros(W, dtype=np.complex128)
+        if walker_status is None:
+            walker_status = np.zeros(W, dtype=np.int32)
+        code = self._lib.walkers_theta(self._h, W, _ptr(phi), _ptr(theta_out), _ptr(logdet_out),
+                                       _ptr(walker_status))
+        if code == 5 and not raise_on_singular:
+            return theta_out, logdet_out, walker_status
+        self._check(code, "walkers_theta")
+        return theta_out, logdet_out, walker_status
+
+    def walkers_pair_exchange(self, phi, precision="fp64", out=None):
+        _check_dtype(phi, "c16")
+        W = int(phi.shape[0])
+        if out is None:
+            out = np.zeros((self.num_pairs, W), dtype=np.complex128)
+        self._check(self._lib.walkers_pair_exchange(self._h, W, _ptr(phi),
+                                                    PRECISIONS.get(precision, precision),
+                                                    _ptr(out)), "walkers_pair_exchange")
+        return out
+
+
+def position_operators(mol) -> np.ndarray:
+    """diag(x), diag(y), diag(z) of the orbital centres (orthonormal synthetic basis)."""
+    pos = mol.orbital_pos
+    return np.ascontiguousarray(np.stack([np.diag(pos[:, d]) for d in range(3)]))
