@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblo_afqmc.so")
 SOURCES = ["api.cu", "setup.cu", "k_theta.cu", "k_fp64.cu", "k_tc.cu"]
-HEADERS = ["common.cuh"]
+HEADERS = ["common.cuh", "tc_ptx.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

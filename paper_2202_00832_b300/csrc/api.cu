@@ -165,10 +165,12 @@ loaf_status loaf_destroy(loaf_ctx* c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& s : c->sp) s.release();
+    for (auto& m : c->mix) m.release();
     c->d_h.release(); c->d_L.release();
     for (loaf::DevBuf* b : {&c->w_phi, &c->w_theta, &c->w_z, &c->w_lu, &c->w_perm, &c->w_logdet,
                             &c->w_status, &c->w_out, &c->w_part, &c->w_part2, &c->w_dhi,
-                            &c->w_dlo, &c->w_dscale, &c->w_host_stage})
+                            &c->w_dlo, &c->w_dscale, &c->w_host_stage, &c->w_cpart,
+                            &c->w_lopart, &c->w_flag})
         b->release();
     if (c->cublas) cublasDestroy(c->cublas);
     if (c->cusolver) cusolverDnDestroy(c->cusolver);
@@ -264,7 +266,7 @@ loaf_status walkers_theta(loaf_ctx* c, int W, const void* phi, void* theta_out, 
 loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int precision,
                            void* e_out, void* logdet_out, int* walker_status) {
     if (!c) return LOAF_ERR_ARG;
-    int bad = 0;
+    int bad = 0, timeout = 0;
     loaf_status st = guarded(c, [&] {
         LOAF_CUDA(cudaSetDevice(c->device));
         check_ready(c, W, phi, mode, precision);
@@ -297,8 +299,15 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
         deliver(c, logdet_out, dld, (size_t)W * sizeof(double2));
         deliver(c, walker_status, dst, (size_t)W * sizeof(int));
         LOAF_CUDA(cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        if (precision != LOAF_PREC_FP64)
+            LOAF_CUDA(cudaMemcpyAsync(&timeout, c->w_flag.ptr, sizeof(int), cudaMemcpyDeviceToHost,
+                                      c->stream));
         LOAF_CUDA(cudaStreamSynchronize(c->stream));
     });
+    if (st == LOAF_OK && timeout) {
+        c->err = "a tensor-core kernel gave up waiting on a pipeline barrier";
+        return LOAF_ERR_TIMEOUT;
+    }
     if (st == LOAF_OK && bad) {
         c->err = "at least one walker overlap is singular or non-finite";
         return bad == LOAF_WALKER_SINGULAR ? LOAF_ERR_SINGULAR : LOAF_ERR_NAN;
@@ -322,7 +331,13 @@ loaf_status walkers_pair_exchange(loaf_ctx* c, int W, const void* phi, int preci
             run_energy_mixed(c, W, LOAF_MODE_LO, precision, c->w_theta.as<double2>(), nullptr,
                              c->w_part.as<double2>());
         deliver(c, e_pairs_out, c->w_part.ptr, (size_t)loaf_num_pairs(c) * W * sizeof(double2));
+        int timeout = 0;
+        if (precision != LOAF_PREC_FP64)
+            LOAF_CUDA(cudaMemcpyAsync(&timeout, c->w_flag.ptr, sizeof(int), cudaMemcpyDeviceToHost,
+                                      c->stream));
         LOAF_CUDA(cudaStreamSynchronize(c->stream));
+        LOAF_REQUIRE(!timeout, LOAF_ERR_TIMEOUT,
+                     "a tensor-core kernel gave up waiting on a pipeline barrier");
     });
 }
 

@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/lo_afqmc.h"
 
 namespace loaf {
@@ -140,6 +142,41 @@ struct SpinData {
     }
 };
 
+// Walker-independent operands of the split-precision path for one 16-bit
+// format.  Orbital index c runs over both spins (alpha first); rows of 16-bit
+// planes are padded to r_pad (a multiple of 8) basis functions with zeros.
+struct MixedOps {
+    bool coul_ready = false, lo_ready = false, bf16 = false;
+    int r_pad = 0;
+    long kflat = 0;            // ntot * r_pad
+    // Coulomb operand: rows g < X are mult_sigma * Lbar^sigma_g, row X is
+    // mult_sigma * hbar^sigma, flattened over (c, r)
+    DevBuf L_hi, L_lo, L_inv;  // (X+1) x kflat 16-bit; inverse row scale (float)
+    DevBuf J0;                 // X doubles: trial Coulomb vector
+    double E1_0 = 0.0;         // trial one-body energy
+    CUtensorMap mapL_hi, mapL_lo;
+    // LO operand: rows of Ubar^T and Vbar of both spins, concatenated
+    long R = 0;
+    DevBuf U_hi, U_lo, V_hi, V_lo;  // R x r_pad 16-bit
+    DevBuf row_c;              // R float4 {inv_su, inv_sv, p, q}
+    DevBuf pt;                 // pair tiles int4 {row0, nvalid, ci, cj}
+    int n_pt = 0;
+    int n_pairs = 0;           // pairs over both spins
+    DevBuf pair_pt0, pair_npt; // first pair tile and count per pair (int)
+    DevBuf pair_w;             // per pair: 0.5 * mult * (1 or 2) (double)
+    DevBuf e0;                 // per pair: trial value p . q (double)
+    double EK0 = 0.0;          // 1/2 sum_sigma mult sum_n wgt_n e0_n
+    CUtensorMap mapU_hi, mapU_lo, mapV_hi, mapV_lo;
+    void release() {
+        for (DevBuf* b : {&L_hi, &L_lo, &L_inv, &J0, &U_hi, &U_lo, &V_hi, &V_lo, &row_c, &pt,
+                          &pair_pt0, &pair_npt, &pair_w, &e0})
+            b->release();
+        coul_ready = lo_ready = false;
+        n_pt = n_pairs = 0;
+        R = 0;
+    }
+};
+
 }  // namespace loaf
 
 // ---------------------------------------------------------------------------
@@ -165,11 +202,12 @@ struct loaf_ctx {
     loaf::DevBuf d_h, d_L;
     loaf::SpinData sp[2];
     std::vector<double> canonical[2];  // trial orbitals as loaded (host)
+    loaf::MixedOps mix[2];             // split-precision operands: [0] FP16, [1] BF16
 
     // workspace for walkers_energy (grown to the largest W seen)
     int ws_W = 0;
     loaf::DevBuf w_phi, w_theta, w_z, w_lu, w_perm, w_logdet, w_status, w_out, w_part,
-        w_part2, w_dhi, w_dlo, w_dscale, w_host_stage;
+        w_part2, w_dhi, w_dlo, w_dscale, w_host_stage, w_cpart, w_lopart, w_flag;
 
     std::string err;
 };

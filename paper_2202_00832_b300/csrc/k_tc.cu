@@ -1,15 +1,1020 @@
-// Mixed-precision (tcgen05) stages: placeholder until the tensor-core
-// kernels land.
+// Split-precision tensor-core path (LOAF_PREC_FP16X3 / LOAF_PREC_BF16X3).
+//
+// Trial-delta form.  Theta = Phi_T + Delta with Phi_T^T Delta = 0 (eq. Q with
+// Phi_T^T Phi_T = 1).  Every walker-independent product with Phi_T is taken
+// once in FP64 (J0, E1_0, the pair vectors p = Ubar^T Phi_j, q = Vbar Phi_i and
+// their dot products e0); only the products with Delta, which is an order of
+// magnitude smaller than Theta, go through the 16-bit tensor cores:
+//   x = (x_hi + x_lo) / scale,  x_hi = rn16(x * scale), x_lo = rn16(x * scale - x_hi)
+//   A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi   (tcgen05.mma kind::f16, FP32 accumulate)
+// with power-of-two scales per operand row (weights) and per walker (Delta).
+//
+// Kernels (sm_103a, one CTA per SM, warp-specialised, 192 threads):
+//   coulomb_tc_kernel  dJ[g][w] = sum_(c,r) Lbar'[g][c][r] Delta[w][c][r]
+//                      (rows g < X: Cholesky vectors, row X: hbar -> dE1),
+//                      split over the (c, r) contraction; FP32 partial tiles.
+//   lo_exchange_tc_kernel  per pair tile (<= 128 ranks of one pair [ij]) and
+//                      128 walkers: a = Ubar^T Delta_j, b = Vbar Delta_i in two
+//                      TMEM accumulators, then the epilogue forms
+//                      p.db + q.da + da.db and reduces over the ranks.
+// Warp 0 issues TMA loads, warp 1 issues tcgen05.mma, warps 2-5 drain TMEM.
+// All mbarrier waits are bounded (tc_ptx.cuh); a timeout raises an error flag
+// the host turns into LOAF_ERR_TIMEOUT.
 #include "common.cuh"
+#include "tc_ptx.cuh"
+
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
 
 namespace loaf {
 
-void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2* theta,
-                      double2* e_out, double2* e_pairs) {
-    (void)c; (void)W; (void)mode; (void)precision; (void)theta; (void)e_out; (void)e_pairs;
-    throw Error{LOAF_ERR_UNSUPPORTED, "mixed-precision path not built yet"};
+namespace {
+
+constexpr int kBK = 32;              // basis functions per stage (64-byte rows)
+constexpr int kRowB = kBK * 2;       // bytes per tile row -> SWIZZLE_64B
+constexpr int kBM = 128;             // MMA rows
+constexpr int kBNW = 128;            // walkers per tile
+constexpr int kBN = 2 * kBNW;        // MMA columns: (walker, re/im) interleaved
+constexpr int kStages = 2;
+constexpr int kThreadsTC = 192;      // 6 warps
+constexpr uint32_t kTileA = kBM * kRowB;   // 8 KB
+constexpr uint32_t kTileB = kBN * kRowB;   // 16 KB
+
+// ---------------------------------------------------------------------------
+// host: TMA descriptors
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        LOAF_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                   cudaEnableDefault, &q));
+        LOAF_REQUIRE(p && q == cudaDriverEntryPointSuccess, LOAF_ERR_CUDA,
+                     "cuTensorMapEncodeTiled is unavailable");
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
 }
 
-void setup_mixed_operands(loaf_ctx* c, int mode, bool bf16) { (void)c; (void)mode; (void)bf16; }
+// 16-bit row-major matrix: `rows` rows of `inner` elements, rows `ld` apart
+void map_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t ld,
+            uint32_t box_inner, uint32_t box_rows) {
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {ld * 2};
+    cuuint32_t box[2] = {box_inner, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims,
+                             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    LOAF_REQUIRE(r == CUDA_SUCCESS, LOAF_ERR_CUDA, "cuTensorMapEncodeTiled (2d) failed");
+}
+
+// Delta planes [2W][ntot][r_pad]: x = r, y = orbital c, z = (walker, re/im)
+void map_delta_3d(CUtensorMap* m, const void* base, uint64_t r_pad, uint64_t ntot, uint64_t rows) {
+    cuuint64_t dims[3] = {r_pad, ntot, rows};
+    cuuint64_t strides[2] = {r_pad * 2, ntot * r_pad * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kBK, 1, (cuuint32_t)kBN};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(base), dims,
+                             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    LOAF_REQUIRE(r == CUDA_SUCCESS, LOAF_ERR_CUDA, "cuTensorMapEncodeTiled (3d) failed");
+}
+
+// ---------------------------------------------------------------------------
+// 16-bit split helpers
+// ---------------------------------------------------------------------------
+template <bool BF16> struct Half16;
+template <> struct Half16<false> {
+    __device__ static uint16_t from(double v, double& back) {
+        const __half h = __double2half(v);
+        back = (double)__half2float(h);
+        return __half_as_ushort(h);
+    }
+};
+template <> struct Half16<true> {
+    __device__ static uint16_t from(double v, double& back) {
+        const __nv_bfloat16 h = __double2bfloat16(v);
+        back = (double)__bfloat162float(h);
+        return __bfloat16_as_ushort(h);
+    }
+};
+
+template <bool BF16>
+__device__ inline void split16(double v, uint16_t& hi, uint16_t& lo) {
+    double b;
+    hi = Half16<BF16>::from(v, b);
+    double b2;
+    lo = Half16<BF16>::from(v - b, b2);
+}
+
+// power-of-two scale putting the largest |value| in [2^13, 2^14)
+__device__ inline double pow2_scale(double maxabs) {
+    if (!(maxabs > 0.0) || !isfinite(maxabs)) return 1.0;
+    int e;
+    frexp(maxabs, &e);  // maxabs = f * 2^e, f in [0.5, 1)
+    return ldexp(1.0, 14 - e);
+}
+
+__device__ inline double block_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double m = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, red[k]);
+    return m;
+}
+
+__device__ inline double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+    return s;
+}
+
+struct SpinRef {
+    const double* Lbar;   // X x N x M
+    const double* hbar;   // N x M
+    const double* trial;  // M x N
+    int N, col0;
+    double mult;
+};
+
+// ---------------------------------------------------------------------------
+// setup kernels of the split operands (FP64 in, 16-bit planes out)
+// ---------------------------------------------------------------------------
+
+// row g <= X of the Coulomb operand: mult * Lbar_g (g < X) or mult * hbar (g = X)
+template <bool BF16>
+__global__ void coul_split_kernel(int M, int X, int r_pad, int nspin, SpinRef s0, SpinRef s1,
+                                  uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
+                                  float* __restrict__ inv) {
+    __shared__ double red[32];
+    const int g = blockIdx.x;
+    const long kflat = (long)(s0.N + (nspin > 1 ? s1.N : 0)) * r_pad;
+    double m = 0.0;
+    for (int s = 0; s < nspin; ++s) {
+        const SpinRef sp = s == 0 ? s0 : s1;
+        const double* src = g < X ? sp.Lbar + (size_t)g * sp.N * M : sp.hbar;
+        for (long e = threadIdx.x; e < (long)sp.N * M; e += blockDim.x)
+            m = fmax(m, fabs(sp.mult * src[e]));
+    }
+    const double sc = pow2_scale(block_max(m, red));
+    for (int s = 0; s < nspin; ++s) {
+        const SpinRef sp = s == 0 ? s0 : s1;
+        const double* src = g < X ? sp.Lbar + (size_t)g * sp.N * M : sp.hbar;
+        for (long e = threadIdx.x; e < (long)sp.N * r_pad; e += blockDim.x) {
+            const int i = (int)(e / r_pad), r = (int)(e % r_pad);
+            const double v = r < M ? sp.mult * src[(size_t)i * M + r] * sc : 0.0;
+            uint16_t h, l;
+            split16<BF16>(v, h, l);
+            const size_t o = (size_t)g * kflat + (size_t)(sp.col0 + i) * r_pad + r;
+            hi[o] = h;
+            lo[o] = l;
+        }
+    }
+    if (threadIdx.x == 0) inv[g] = (float)(1.0 / sc);
+}
+
+// J0[g] = sum_sigma mult sum_ir Lbar_gir Phi_ri (g < X); E1_0 at g = X (FP64)
+__global__ void trial_coulomb_kernel(int M, int X, int nspin, SpinRef s0, SpinRef s1,
+                                     double* __restrict__ J0) {
+    __shared__ double red[32];
+    const int g = blockIdx.x;
+    double acc = 0.0;
+    for (int s = 0; s < nspin; ++s) {
+        const SpinRef sp = s == 0 ? s0 : s1;
+        const double* src = g < X ? sp.Lbar + (size_t)g * sp.N * M : sp.hbar;
+        double a = 0.0;
+        for (long e = threadIdx.x; e < (long)sp.N * M; e += blockDim.x) {
+            const int i = (int)(e / M), r = (int)(e % M);
+            a += src[e] * sp.trial[(size_t)r * sp.N + i];
+        }
+        acc += sp.mult * a;
+    }
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) J0[g] = t;
+}
+
+// one packed factor row (Ubar^T or Vbar) -> 16-bit planes, inverse scale
+template <bool BF16>
+__global__ void row_split_kernel(int M, int r_pad, const double* __restrict__ src,
+                                 uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
+                                 float* __restrict__ inv) {
+    __shared__ double red[32];
+    const long row = blockIdx.x;
+    const double* s = src + row * M;
+    double m = 0.0;
+    for (int r = threadIdx.x; r < M; r += blockDim.x) m = fmax(m, fabs(s[r]));
+    const double sc = pow2_scale(block_max(m, red));
+    for (int r = threadIdx.x; r < r_pad; r += blockDim.x) {
+        uint16_t h, l;
+        split16<BF16>(r < M ? s[r] * sc : 0.0, h, l);
+        hi[row * r_pad + r] = h;
+        lo[row * r_pad + r] = l;
+    }
+    if (threadIdx.x == 0) inv[row] = (float)(1.0 / sc);
+}
+
+// p = Ubar^T row . Phi_j, q = Vbar row . Phi_i (FP64), one warp per row
+__global__ void pq_kernel(int M, long rows, const double* __restrict__ U,
+                          const double* __restrict__ V, const int* __restrict__ row_pair,
+                          const int* __restrict__ pi, const int* __restrict__ pj,
+                          const double* __restrict__ trial, int N, double* __restrict__ p_out,
+                          double* __restrict__ q_out) {
+    const long row = (long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const int n = row_pair[row];
+    const int i = pi[n], j = pj[n];
+    double p = 0.0, q = 0.0;
+    for (int r = lane; r < M; r += 32) {
+        p += U[row * M + r] * trial[(size_t)r * N + j];
+        q += V[row * M + r] * trial[(size_t)r * N + i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        p += __shfl_xor_sync(0xffffffffu, p, o);
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if (lane == 0) { p_out[row] = p; q_out[row] = q; }
+}
+
+__global__ void row_consts_kernel(long rows, const float* __restrict__ inv_u,
+                                  const float* __restrict__ inv_v, const double* __restrict__ p,
+                                  const double* __restrict__ q, float4* __restrict__ out) {
+    const long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < rows) out[r] = make_float4(inv_u[r], inv_v[r], (float)p[r], (float)q[r]);
+}
+
+// e0[n] = sum_k p_k q_k over the pair's rows (FP64)
+__global__ void pair_e0_kernel(int npairs, const long* __restrict__ off, const int* __restrict__ K,
+                               const double* __restrict__ p, const double* __restrict__ q,
+                               double* __restrict__ e0) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= npairs) return;
+    double s = 0.0;
+    for (int k = 0; k < K[n]; ++k) s += p[off[n] + k] * q[off[n] + k];
+    e0[n] = s;
+}
+
+// ---------------------------------------------------------------------------
+// per-call: Delta = Theta - Phi_T -> scaled 16-bit planes
+// ---------------------------------------------------------------------------
+__global__ void delta_max_kernel(int M, int ntot, int nspin, SpinRef s0, SpinRef s1,
+                                 const double2* __restrict__ theta, float* __restrict__ inv_t,
+                                 double* __restrict__ scale) {
+    __shared__ double red[32];
+    const int w = blockIdx.x;
+    double m = 0.0;
+    for (int s = 0; s < nspin; ++s) {
+        const SpinRef sp = s == 0 ? s0 : s1;
+        const double2* th = theta + ((size_t)w * ntot + sp.col0) * M;
+        for (long e = threadIdx.x; e < (long)sp.N * M; e += blockDim.x) {
+            const int i = (int)(e / M), r = (int)(e % M);
+            const double2 t = th[e];
+            m = fmax(m, fmax(fabs(t.x - sp.trial[(size_t)r * sp.N + i]), fabs(t.y)));
+        }
+    }
+    const double sc = pow2_scale(block_max(m, red));
+    if (threadIdx.x == 0) { inv_t[w] = (float)(1.0 / sc); scale[w] = sc; }
+}
+
+template <bool BF16>
+__global__ void delta_split_kernel(int M, int ntot, int r_pad, int W, int nspin, SpinRef s0,
+                                   SpinRef s1, const double2* __restrict__ theta,
+                                   const double* __restrict__ scale, uint16_t* __restrict__ hi,
+                                   uint16_t* __restrict__ lo) {
+    const int w = blockIdx.x / ntot, c = blockIdx.x % ntot;
+    const SpinRef sp = (nspin > 1 && c >= s1.col0) ? s1 : s0;
+    const int i = c - sp.col0;
+    const double sc = scale[w];
+    const double2* th = theta + ((size_t)w * ntot + c) * M;
+    const size_t o_re = ((size_t)(2 * w) * ntot + c) * r_pad;
+    const size_t o_im = ((size_t)(2 * w + 1) * ntot + c) * r_pad;
+    for (int r = threadIdx.x; r < r_pad; r += blockDim.x) {
+        double vr = 0.0, vi = 0.0;
+        if (r < M) {
+            const double2 t = th[r];
+            vr = (t.x - sp.trial[(size_t)r * sp.N + i]) * sc;
+            vi = t.y * sc;
+        }
+        uint16_t h, l;
+        split16<BF16>(vr, h, l);
+        hi[o_re + r] = h;
+        lo[o_re + r] = l;
+        split16<BF16>(vi, h, l);
+        hi[o_im + r] = h;
+        lo[o_im + r] = l;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tensor-core kernels
+// ---------------------------------------------------------------------------
+struct TCShared {
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t tmem_full;
+    uint64_t tmem_empty;
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+    float red[4][kBN];
+};
+
+__device__ inline uint8_t* align1024(uint8_t* p) {
+    return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+struct CoulParams {
+    float* part;       // [split][rows][ldp] FP32 partial accumulators
+    int rows;          // X + 1
+    int n_mt, n_wt, n_split, nk, ldp;
+    uint32_t idesc;
+    int* err;
+};
+
+// dJ partial tile: rows g (128) x 256 columns (128 walkers, re/im), k-chunks
+// [split * nk / n_split, (split+1) * nk / n_split)
+__global__ void __launch_bounds__(kThreadsTC, 1)
+coulomb_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                  const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                  CoulParams P) {
+    extern __shared__ uint8_t dyn_smem[];
+    __shared__ TCShared sh;
+    uint8_t* base = align1024(dyn_smem);
+    constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kTileB;  // 48 KB
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_units = P.n_mt * P.n_wt * P.n_split;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) { tc::mbar_init(&sh.full[s], 1); tc::mbar_init(&sh.empty[s], 1); }
+        tc::mbar_init(&sh.tmem_full, 1);
+        tc::mbar_init(&sh.tmem_empty, 4);
+        tc::mbar_init(&sh.drain, 1);
+        sh.abort = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&sh.tmem_base, kBN);
+        tc::tmem_relinquish();
+    }
+    if (threadIdx.x == 32) {
+        tc::tma_prefetch(&mAhi); tc::tma_prefetch(&mAlo);
+        tc::tma_prefetch(&mBhi); tc::tma_prefetch(&mBlo);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = sh.tmem_base;
+    volatile int* abort = &sh.abort;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        int s = 0;
+        uint32_t ph = 0;
+        uint32_t filled = 0, last_par = 0;
+        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
+            const int mt = u % P.n_mt, wt = (u / P.n_mt) % P.n_wt, sp = u / (P.n_mt * P.n_wt);
+            const int k0 = (int)((long)sp * P.nk / P.n_split), k1 = (int)((long)(sp + 1) * P.nk / P.n_split);
+            for (int kc = k0; kc < k1; ++kc) {
+                if (!tc::mbar_wait(&sh.empty[s], ph ^ 1, abort)) break;
+                uint8_t* st = base + s * kStageBytes;
+                tc::mbar_arrive_expect_tx(&sh.full[s], kStageBytes);
+                tc::tma_load_2d(st, &mAhi, &sh.full[s], kc * kBK, mt * kBM);
+                tc::tma_load_2d(st + kTileA, &mAlo, &sh.full[s], kc * kBK, mt * kBM);
+                tc::tma_load_2d(st + 2 * kTileA, &mBhi, &sh.full[s], kc * kBK, wt * kBN);
+                tc::tma_load_2d(st + 2 * kTileA + kTileB, &mBlo, &sh.full[s], kc * kBK, wt * kBN);
+                filled |= 1u << s;
+                last_par = (last_par & ~(1u << s)) | (ph << s);
+                if (++s == kStages) { s = 0; ph ^= 1; }
+            }
+        }
+        // drain: every stage ever filled must have landed before the CTA exits
+        if (*abort) {
+            for (int q = 0; q < kStages; ++q)
+                if (filled & (1u << q)) {
+                    volatile int never = 0;
+                    tc::mbar_wait(&sh.full[q], (last_par >> q) & 1, &never);
+                }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        int s = 0;
+        uint32_t ph = 0, tph = 0;
+        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
+            const int sp = u / (P.n_mt * P.n_wt);
+            const int k0 = (int)((long)sp * P.nk / P.n_split), k1 = (int)((long)(sp + 1) * P.nk / P.n_split);
+            if (!tc::mbar_wait(&sh.tmem_empty, tph ^ 1, abort)) break;
+            tc::tc_fence_after();
+            bool ok = true;
+            for (int kc = k0; kc < k1; ++kc) {
+                if (!tc::mbar_wait(&sh.full[s], ph, abort)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint32_t st = tc::smem_u32(base + s * kStageBytes);
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk) {
+                    const uint32_t off = kk * 32;
+                    const uint64_t ahi = tc::smem_desc(st + off, kRowB);
+                    const uint64_t alo = tc::smem_desc(st + kTileA + off, kRowB);
+                    const uint64_t bhi = tc::smem_desc(st + 2 * kTileA + off, kRowB);
+                    const uint64_t blo = tc::smem_desc(st + 2 * kTileA + kTileB + off, kRowB);
+                    const uint32_t acc = (kc > k0 || kk > 0) ? 1u : 0u;
+                    tc::mma_f16(tmem, ahi, bhi, P.idesc, acc);
+                    tc::mma_f16(tmem, ahi, blo, P.idesc, 1u);
+                    tc::mma_f16(tmem, alo, bhi, P.idesc, 1u);
+                }
+                tc::mma_commit(&sh.empty[s]);
+                if (++s == kStages) { s = 0; ph ^= 1; }
+            }
+            if (!ok) break;
+            tc::mma_commit(&sh.tmem_full);
+            tph ^= 1;
+        }
+        tc::mma_commit(&sh.drain);
+        volatile int never = 0;
+        tc::mbar_wait(&sh.drain, 0, &never);
+    } else if (warp >= 2) {
+        // ---------------- epilogue: TMEM -> FP32 partial tile ----------------
+        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        uint32_t tph = 0;
+        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
+            const int mt = u % P.n_mt, wt = (u / P.n_mt) % P.n_wt, sp = u / (P.n_mt * P.n_wt);
+            if (!tc::mbar_wait(&sh.tmem_full, tph, abort)) break;
+            tc::tc_fence_after();
+            const int g = mt * kBM + q * 32 + lane;
+            float* dst = P.part + ((size_t)sp * P.rows + g) * P.ldp + (size_t)wt * kBN;
+#pragma unroll 1
+            for (int ch = 0; ch < kBN / 32; ++ch) {
+                float v[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + ch * 32, v);
+                tc::tmem_wait_ld();
+                if (g < P.rows) {
+                    float4* d4 = reinterpret_cast<float4*>(dst + ch * 32);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        d4[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                }
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&sh.tmem_empty);
+            tph ^= 1;
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, kBN);
+    if (threadIdx.x == 0 && sh.abort) atomicExch(P.err, 1);
+}
+
+struct LoParams {
+    const int4* pt;       // pair tiles {row0, nvalid, ci, cj}
+    const float4* rowc;   // per packed row {inv_su, inv_sv, p, q}
+    const float* inv_t;   // per walker inverse Delta scale
+    double2* part;        // [n_pt][ldp] per pair tile and walker
+    int n_pt, n_wt, W, ldp, nk;
+    uint32_t idesc;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kThreadsTC, 1)
+lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_constant__ CUtensorMap mUlo,
+                      const __grid_constant__ CUtensorMap mVhi, const __grid_constant__ CUtensorMap mVlo,
+                      const __grid_constant__ CUtensorMap mDhi, const __grid_constant__ CUtensorMap mDlo,
+                      LoParams P) {
+    extern __shared__ uint8_t dyn_smem[];
+    __shared__ TCShared sh;
+    uint8_t* base = align1024(dyn_smem);
+    // stage: U hi, U lo, V hi, V lo (8 KB each), Dj hi, Dj lo, Di hi, Di lo (16 KB each)
+    constexpr uint32_t kStageBytes = 4 * kTileA + 4 * kTileB;  // 96 KB
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_units = P.n_pt * P.n_wt;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) { tc::mbar_init(&sh.full[s], 1); tc::mbar_init(&sh.empty[s], 1); }
+        tc::mbar_init(&sh.tmem_full, 1);
+        tc::mbar_init(&sh.tmem_empty, 4);
+        tc::mbar_init(&sh.drain, 1);
+        sh.abort = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&sh.tmem_base, 2 * kBN);
+        tc::tmem_relinquish();
+    }
+    if (threadIdx.x == 32) {
+        tc::tma_prefetch(&mUhi); tc::tma_prefetch(&mUlo); tc::tma_prefetch(&mVhi);
+        tc::tma_prefetch(&mVlo); tc::tma_prefetch(&mDhi); tc::tma_prefetch(&mDlo);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = sh.tmem_base;
+    volatile int* abort = &sh.abort;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        int s = 0;
+        uint32_t ph = 0, filled = 0, last_par = 0;
+        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
+            const int4 t = P.pt[u / P.n_wt];
+            const int wt = u % P.n_wt;
+            for (int kc = 0; kc < P.nk; ++kc) {
+                if (!tc::mbar_wait(&sh.empty[s], ph ^ 1, abort)) break;
+                uint8_t* st = base + s * kStageBytes;
+                tc::mbar_arrive_expect_tx(&sh.full[s], kStageBytes);
+                const int x = kc * kBK;
+                tc::tma_load_2d(st, &mUhi, &sh.full[s], x, t.x);
+                tc::tma_load_2d(st + kTileA, &mUlo, &sh.full[s], x, t.x);
+                tc::tma_load_2d(st + 2 * kTileA, &mVhi, &sh.full[s], x, t.x);
+                tc::tma_load_2d(st + 3 * kTileA, &mVlo, &sh.full[s], x, t.x);
+                uint8_t* sb = st + 4 * kTileA;
+                tc::tma_load_3d(sb, &mDhi, &sh.full[s], x, t.w, wt * kBN);
+                tc::tma_load_3d(sb + kTileB, &mDlo, &sh.full[s], x, t.w, wt * kBN);
+                tc::tma_load_3d(sb + 2 * kTileB, &mDhi, &sh.full[s], x, t.z, wt * kBN);
+                tc::tma_load_3d(sb + 3 * kTileB, &mDlo, &sh.full[s], x, t.z, wt * kBN);
+                filled |= 1u << s;
+                last_par = (last_par & ~(1u << s)) | (ph << s);
+                if (++s == kStages) { s = 0; ph ^= 1; }
+            }
+        }
+        if (*abort) {
+            for (int q = 0; q < kStages; ++q)
+                if (filled & (1u << q)) {
+                    volatile int never = 0;
+                    tc::mbar_wait(&sh.full[q], (last_par >> q) & 1, &never);
+                }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        int s = 0;
+        uint32_t ph = 0, tph = 0;
+        const uint32_t tA = tmem, tB = tmem + kBN;  // accumulators a (U side), b (V side)
+        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
+            if (!tc::mbar_wait(&sh.tmem_empty, tph ^ 1, abort)) break;
+            tc::tc_fence_after();
+            bool ok = true;
+            for (int kc = 0; kc < P.nk; ++kc) {
+                if (!tc::mbar_wait(&sh.full[s], ph, abort)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint32_t st = tc::smem_u32(base + s * kStageBytes);
+                const uint32_t sb = st + 4 * kTileA;
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk) {
+                    const uint32_t off = kk * 32;
+                    const uint64_t uhi = tc::smem_desc(st + off, kRowB);
+                    const uint64_t ulo = tc::smem_desc(st + kTileA + off, kRowB);
+                    const uint64_t vhi = tc::smem_desc(st + 2 * kTileA + off, kRowB);
+                    const uint64_t vlo = tc::smem_desc(st + 3 * kTileA + off, kRowB);
+                    const uint64_t jhi = tc::smem_desc(sb + off, kRowB);
+                    const uint64_t jlo = tc::smem_desc(sb + kTileB + off, kRowB);
+                    const uint64_t ihi = tc::smem_desc(sb + 2 * kTileB + off, kRowB);
+                    const uint64_t ilo = tc::smem_desc(sb + 3 * kTileB + off, kRowB);
+                    const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+                    tc::mma_f16(tA, uhi, jhi, P.idesc, acc);
+                    tc::mma_f16(tA, uhi, jlo, P.idesc, 1u);
+                    tc::mma_f16(tA, ulo, jhi, P.idesc, 1u);
+                    tc::mma_f16(tB, vhi, ihi, P.idesc, acc);
+                    tc::mma_f16(tB, vhi, ilo, P.idesc, 1u);
+                    tc::mma_f16(tB, vlo, ihi, P.idesc, 1u);
+                }
+                tc::mma_commit(&sh.empty[s]);
+                if (++s == kStages) { s = 0; ph ^= 1; }
+            }
+            if (!ok) break;
+            tc::mma_commit(&sh.tmem_full);
+            tph ^= 1;
+        }
+        tc::mma_commit(&sh.drain);
+        volatile int never = 0;
+        tc::mbar_wait(&sh.drain, 0, &never);
+    } else if (warp >= 2) {
+        // ---------------- epilogue ----------------
+        // lane = rank within the tile; per walker m of a 16-walker chunk:
+        //   da = inv_su * inv_t * acc_a, db = inv_sv * inv_t * acc_b
+        //   val = p db + q da + da db   (complex; p, q real)
+        // then a butterfly reduction over the 32 ranks of the warp and a sum
+        // over the 4 warps in shared memory.
+        const int q = warp & 3;
+        const int ep_tid = threadIdx.x - 64;  // 0..127
+        uint32_t tph = 0;
+        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
+            const int pti = u / P.n_wt, wt = u % P.n_wt;
+            const int4 t = P.pt[pti];
+            const int rl = q * 32 + lane;
+            float4 rc = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rl < t.y) rc = P.rowc[t.x + rl];
+            const float cb = rc.z * rc.y;   // p * inv_sv
+            const float ca = rc.w * rc.x;   // q * inv_su
+            const float cq = rc.x * rc.y;   // inv_su * inv_sv
+            if (!tc::mbar_wait(&sh.tmem_full, tph, abort)) break;
+            tc::tc_fence_after();
+#pragma unroll 1
+            for (int ch = 0; ch < kBN / 32; ++ch) {
+                float va[32], vb[32];
+                const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+                tc::tmem_ld32(tmem + lane_off + ch * 32, va);
+                tc::tmem_ld32(tmem + lane_off + kBN + ch * 32, vb);
+                tc::tmem_wait_ld();
+                float v[32];
+#pragma unroll
+                for (int m = 0; m < 16; ++m) {
+                    const int w = wt * kBNW + ch * 16 + m;
+                    const float it = w < P.W ? __ldg(P.inv_t + w) : 0.f;
+                    const float ar = va[2 * m], ai = va[2 * m + 1];
+                    const float br = vb[2 * m], bi = vb[2 * m + 1];
+                    const float lr = fmaf(cb, br, ca * ar), li = fmaf(cb, bi, ca * ai);
+                    const float qr = cq * fmaf(ar, br, -ai * bi), qi = cq * fmaf(ar, bi, ai * br);
+                    v[2 * m] = it * fmaf(it, qr, lr);
+                    v[2 * m + 1] = it * fmaf(it, qi, li);
+                }
+                const float r = tc::warp_transpose_sum(v, lane);
+                sh.red[q][ch * 32 + lane] = r;
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&sh.tmem_empty);
+            tph ^= 1;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            {
+                const int w = wt * kBNW + ep_tid;
+                const double re = (double)sh.red[0][2 * ep_tid] + sh.red[1][2 * ep_tid] +
+                                  sh.red[2][2 * ep_tid] + sh.red[3][2 * ep_tid];
+                const double im = (double)sh.red[0][2 * ep_tid + 1] + sh.red[1][2 * ep_tid + 1] +
+                                  sh.red[2][2 * ep_tid + 1] + sh.red[3][2 * ep_tid + 1];
+                if (w < P.W) P.part[(size_t)pti * P.ldp + w] = make_double2(re, im);
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, 2 * kBN);
+    if (threadIdx.x == 0 && sh.abort) atomicExch(P.err, 1);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reductions of the tensor-core partials
+// ---------------------------------------------------------------------------
+
+// E1 = E1_0 + dE1,  E_J = 1/2 sum_g (J0_g + dJ_g)^2,  dJ from the split partials
+__global__ void coulomb_tc_reduce_kernel(int X, int W, int n_split, int ldp,
+                                         const float* __restrict__ part,
+                                         const float* __restrict__ inv_s,
+                                         const float* __restrict__ inv_t,
+                                         const double* __restrict__ J0, double E1_0,
+                                         double2* __restrict__ e1, double2* __restrict__ ej) {
+    // 32 walkers x 8 row groups
+    __shared__ double2 red[8][32];
+    const int wl = threadIdx.x & 31, gg = threadIdx.x >> 5;
+    const int w = blockIdx.x * 32 + wl;
+    double2 acc = make_double2(0.0, 0.0);
+    const size_t plane = (size_t)(X + 1) * ldp;
+    if (w < W) {
+        const double it = inv_t[w];
+        for (int g = gg; g < X; g += 8) {
+            double re = 0.0, im = 0.0;
+            for (int s = 0; s < n_split; ++s) {
+                const float2 v = *reinterpret_cast<const float2*>(part + s * plane + (size_t)g * ldp + 2 * w);
+                re += v.x;
+                im += v.y;
+            }
+            const double f = (double)inv_s[g] * it;
+            const double2 J = make_double2(J0[g] + re * f, im * f);
+            acc = cadd(acc, cmul(J, J));
+        }
+    }
+    red[gg][wl] = acc;
+    __syncthreads();
+    if (gg == 0 && w < W) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int k = 0; k < 8; ++k) t = cadd(t, red[k][wl]);
+        ej[w] = cscale(t, 0.5);
+        double re = 0.0, im = 0.0;
+        for (int s = 0; s < n_split; ++s) {
+            const float2 v = *reinterpret_cast<const float2*>(part + s * plane + (size_t)X * ldp + 2 * w);
+            re += v.x;
+            im += v.y;
+        }
+        const double f = (double)inv_s[X] * inv_t[w];
+        e1[w] = make_double2(E1_0 + re * f, im * f);
+    }
+}
+
+// per pair: e_n(w) = e0_n + sum over its tiles; E_K(w) = EK0 + sum_n pw_n de_n(w)
+__global__ void lo_tc_reduce_kernel(int n_pairs, int W, int ldp, const int* __restrict__ pt0,
+                                    const int* __restrict__ npt, const double* __restrict__ pw,
+                                    const double* __restrict__ e0, double EK0,
+                                    const double2* __restrict__ part, double2* __restrict__ ek,
+                                    double2* __restrict__ e_pairs) {
+    __shared__ double2 red[8][32];
+    const int wl = threadIdx.x & 31, gg = threadIdx.x >> 5;
+    const int w = blockIdx.x * 32 + wl;
+    double2 acc = make_double2(0.0, 0.0);
+    if (w < W) {
+        for (int n = gg; n < n_pairs; n += 8) {
+            double2 d = make_double2(0.0, 0.0);
+            for (int k = 0; k < npt[n]; ++k) d = cadd(d, part[(size_t)(pt0[n] + k) * ldp + w]);
+            if (e_pairs) e_pairs[(size_t)n * W + w] = make_double2(e0[n] + d.x, d.y);
+            acc = cadd(acc, cscale(d, pw[n]));
+        }
+    }
+    red[gg][wl] = acc;
+    __syncthreads();
+    if (gg == 0 && w < W && ek) {
+        double2 t = make_double2(EK0, 0.0);
+        for (int k = 0; k < 8; ++k) t = cadd(t, red[k][wl]);
+        ek[w] = t;
+    }
+}
+
+SpinRef spin_ref(const SpinData& s) {
+    return SpinRef{s.d_Lbar.as<double>(), s.d_hbar.as<double>(), s.d_trial.as<double>(), s.N,
+                   s.col0, s.mult};
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+void ensure_coulomb_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
+    if (mx.coul_ready) return;
+    mx.bf16 = bf16;
+    mx.r_pad = (c->M + 7) / 8 * 8;
+    mx.kflat = (long)c->ntot * mx.r_pad;
+    const int rows = c->X + 1;
+    mx.L_hi.ensure((size_t)rows * mx.kflat * 2);
+    mx.L_lo.ensure((size_t)rows * mx.kflat * 2);
+    mx.L_inv.ensure((size_t)rows * sizeof(float));
+    mx.J0.ensure((size_t)rows * sizeof(double));
+    SpinRef s0 = spin_ref(c->sp[0]), s1 = c->nspin > 1 ? spin_ref(c->sp[1]) : s0;
+    if (bf16)
+        coul_split_kernel<true><<<rows, 256, 0, c->stream>>>(c->M, c->X, mx.r_pad, c->nspin, s0, s1,
+                                                            mx.L_hi.as<uint16_t>(), mx.L_lo.as<uint16_t>(),
+                                                            mx.L_inv.as<float>());
+    else
+        coul_split_kernel<false><<<rows, 256, 0, c->stream>>>(c->M, c->X, mx.r_pad, c->nspin, s0, s1,
+                                                             mx.L_hi.as<uint16_t>(), mx.L_lo.as<uint16_t>(),
+                                                             mx.L_inv.as<float>());
+    LOAF_LAUNCH_CHECK();
+    trial_coulomb_kernel<<<rows, 256, 0, c->stream>>>(c->M, c->X, c->nspin, s0, s1, mx.J0.as<double>());
+    LOAF_LAUNCH_CHECK();
+    LOAF_CUDA(cudaMemcpyAsync(&mx.E1_0, mx.J0.as<double>() + c->X, sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+    LOAF_CUDA(cudaStreamSynchronize(c->stream));
+    map_2d(&mx.mapL_hi, mx.L_hi.ptr, mx.kflat, rows, mx.kflat, kBK, kBM);
+    map_2d(&mx.mapL_lo, mx.L_lo.ptr, mx.kflat, rows, mx.kflat, kBK, kBM);
+    mx.coul_ready = true;
+}
+
+void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
+    if (mx.lo_ready) return;
+    mx.bf16 = bf16;
+    mx.r_pad = (c->M + 7) / 8 * 8;
+    const int M = c->M;
+    long R = 0;
+    int npairs = 0;
+    for (int s = 0; s < c->nspin; ++s) { R += c->sp[s].pairs.rows; npairs += c->sp[s].pairs.npairs; }
+    mx.R = R;
+    mx.n_pairs = npairs;
+    const long Rb = std::max<long>(R, 1);
+    mx.U_hi.ensure((size_t)Rb * mx.r_pad * 2);
+    mx.U_lo.ensure((size_t)Rb * mx.r_pad * 2);
+    mx.V_hi.ensure((size_t)Rb * mx.r_pad * 2);
+    mx.V_lo.ensure((size_t)Rb * mx.r_pad * 2);
+    mx.row_c.ensure((size_t)Rb * sizeof(float4));
+    DevBuf inv_u, inv_v, pbuf, qbuf;
+    inv_u.ensure(Rb * sizeof(float));
+    inv_v.ensure(Rb * sizeof(float));
+    pbuf.ensure(Rb * sizeof(double));
+    qbuf.ensure(Rb * sizeof(double));
+    mx.e0.ensure(std::max(npairs, 1) * sizeof(double));
+    mx.pair_w.ensure(std::max(npairs, 1) * sizeof(double));
+
+    std::vector<double> pw;
+    std::vector<int4> tiles;
+    std::vector<int> pt0(npairs), npt(npairs);
+    long row_base = 0;
+    int pair_base = 0;
+    for (int s = 0; s < c->nspin; ++s) {
+        SpinData& sd = c->sp[s];
+        PairTable& pt = sd.pairs;
+        if (pt.rows > 0) {
+            const size_t o = (size_t)row_base * mx.r_pad;
+            if (bf16) {
+                row_split_kernel<true><<<pt.rows, 128, 0, c->stream>>>(M, mx.r_pad, pt.d_U.as<double>(),
+                    mx.U_hi.as<uint16_t>() + o, mx.U_lo.as<uint16_t>() + o, inv_u.as<float>() + row_base);
+                row_split_kernel<true><<<pt.rows, 128, 0, c->stream>>>(M, mx.r_pad, pt.d_V.as<double>(),
+                    mx.V_hi.as<uint16_t>() + o, mx.V_lo.as<uint16_t>() + o, inv_v.as<float>() + row_base);
+            } else {
+                row_split_kernel<false><<<pt.rows, 128, 0, c->stream>>>(M, mx.r_pad, pt.d_U.as<double>(),
+                    mx.U_hi.as<uint16_t>() + o, mx.U_lo.as<uint16_t>() + o, inv_u.as<float>() + row_base);
+                row_split_kernel<false><<<pt.rows, 128, 0, c->stream>>>(M, mx.r_pad, pt.d_V.as<double>(),
+                    mx.V_hi.as<uint16_t>() + o, mx.V_lo.as<uint16_t>() + o, inv_v.as<float>() + row_base);
+            }
+            LOAF_LAUNCH_CHECK();
+            // row -> pair map of this spin
+            std::vector<int> row_pair(pt.rows);
+            for (int n = 0; n < pt.npairs; ++n)
+                for (int k = 0; k < pt.K[n]; ++k) row_pair[pt.off[n] + k] = n;
+            DevBuf d_rp;
+            d_rp.ensure(row_pair.size() * sizeof(int));
+            LOAF_CUDA(cudaMemcpyAsync(d_rp.ptr, row_pair.data(), row_pair.size() * sizeof(int),
+                                      cudaMemcpyHostToDevice, c->stream));
+            pq_kernel<<<ceil_div(pt.rows, 8), 256, 0, c->stream>>>(
+                M, pt.rows, pt.d_U.as<double>(), pt.d_V.as<double>(), d_rp.as<int>(),
+                pt.d_i.as<int>(), pt.d_j.as<int>(), sd.d_trial.as<double>(), sd.N,
+                pbuf.as<double>() + row_base, qbuf.as<double>() + row_base);
+            LOAF_LAUNCH_CHECK();
+            LOAF_CUDA(cudaStreamSynchronize(c->stream));  // d_rp goes out of scope
+        }
+        // e0 per pair (pair offsets are spin-local rows)
+        {
+            DevBuf d_off;
+            d_off.ensure(std::max(pt.npairs, 1) * sizeof(long));
+            std::vector<long> goff(pt.npairs);
+            for (int n = 0; n < pt.npairs; ++n) goff[n] = pt.off[n] + row_base;
+            LOAF_CUDA(cudaMemcpyAsync(d_off.ptr, goff.data(), goff.size() * sizeof(long),
+                                      cudaMemcpyHostToDevice, c->stream));
+            pair_e0_kernel<<<ceil_div(std::max(pt.npairs, 1), 128), 128, 0, c->stream>>>(
+                pt.npairs, d_off.as<long>(), pt.d_K.as<int>(), pbuf.as<double>(),
+                qbuf.as<double>(), mx.e0.as<double>() + pair_base);
+            LOAF_LAUNCH_CHECK();
+            LOAF_CUDA(cudaStreamSynchronize(c->stream));
+        }
+        // pair tiles in 8 x 8 orbital blocks (pairs sharing orbitals run together)
+        std::vector<int> order(pt.npairs);
+        for (int n = 0; n < pt.npairs; ++n) order[n] = n;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            const int ba = (pt.i[a] / 8) * 1024 + pt.j[a] / 8, bb = (pt.i[b] / 8) * 1024 + pt.j[b] / 8;
+            return ba < bb;
+        });
+        for (int n : order) {
+            const int gpair = pair_base + n;
+            pt0[gpair] = (int)tiles.size();
+            int cnt = 0;
+            for (int k0 = 0; k0 < pt.K[n]; k0 += kBM) {
+                tiles.push_back(make_int4((int)(row_base + pt.off[n] + k0), std::min(kBM, pt.K[n] - k0),
+                                          sd.col0 + pt.i[n], sd.col0 + pt.j[n]));
+                ++cnt;
+            }
+            npt[gpair] = cnt;
+        }
+        for (int n = 0; n < pt.npairs; ++n)
+            pw.push_back(0.5 * sd.mult * (pt.i[n] == pt.j[n] ? 1.0 : 2.0));
+        row_base += pt.rows;
+        pair_base += pt.npairs;
+    }
+    if (R > 0) {
+        row_consts_kernel<<<ceil_div(R, 256), 256, 0, c->stream>>>(R, inv_u.as<float>(), inv_v.as<float>(),
+                                                                 pbuf.as<double>(), qbuf.as<double>(),
+                                                                 mx.row_c.as<float4>());
+        LOAF_LAUNCH_CHECK();
+    }
+    mx.n_pt = (int)tiles.size();
+    mx.pt.ensure(std::max<size_t>(tiles.size(), 1) * sizeof(int4));
+    mx.pair_pt0.ensure(std::max(npairs, 1) * sizeof(int));
+    mx.pair_npt.ensure(std::max(npairs, 1) * sizeof(int));
+    if (!tiles.empty())
+        LOAF_CUDA(cudaMemcpyAsync(mx.pt.ptr, tiles.data(), tiles.size() * sizeof(int4),
+                                  cudaMemcpyHostToDevice, c->stream));
+    LOAF_CUDA(cudaMemcpyAsync(mx.pair_pt0.ptr, pt0.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    LOAF_CUDA(cudaMemcpyAsync(mx.pair_npt.ptr, npt.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    LOAF_CUDA(cudaMemcpyAsync(mx.pair_w.ptr, pw.data(), npairs * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    std::vector<double> e0(npairs);
+    LOAF_CUDA(cudaMemcpyAsync(e0.data(), mx.e0.ptr, npairs * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LOAF_CUDA(cudaStreamSynchronize(c->stream));
+    double ek0 = 0.0;
+    for (int n = 0; n < npairs; ++n) ek0 += pw[n] * e0[n];
+    mx.EK0 = ek0;
+    map_2d(&mx.mapU_hi, mx.U_hi.ptr, mx.r_pad, Rb, mx.r_pad, kBK, kBM);
+    map_2d(&mx.mapU_lo, mx.U_lo.ptr, mx.r_pad, Rb, mx.r_pad, kBK, kBM);
+    map_2d(&mx.mapV_hi, mx.V_hi.ptr, mx.r_pad, Rb, mx.r_pad, kBK, kBM);
+    map_2d(&mx.mapV_lo, mx.V_lo.ptr, mx.r_pad, Rb, mx.r_pad, kBK, kBM);
+    mx.lo_ready = true;
+}
+
+constexpr size_t kCoulSmem = kStages * (2 * kTileA + 2 * kTileB) + 1024;
+constexpr size_t kLoSmem = kStages * (4 * kTileA + 4 * kTileB) + 1024;
+
+}  // namespace
+
+void setup_mixed_operands(loaf_ctx* c, int mode, bool bf16) {
+    MixedOps& mx = c->mix[bf16 ? 1 : 0];
+    ensure_coulomb_ops(c, mx, bf16);
+    if (mode == LOAF_MODE_LO) ensure_lo_ops(c, mx, bf16);
+}
+
+void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2* theta,
+                      double2* e_out, double2* e_pairs) {
+    const bool bf16 = precision == LOAF_PREC_BF16X3;
+    MixedOps& mx = c->mix[bf16 ? 1 : 0];
+    if (e_out) ensure_coulomb_ops(c, mx, bf16);
+    if (mode == LOAF_MODE_LO) ensure_lo_ops(c, mx, bf16);
+    mx.r_pad = (c->M + 7) / 8 * 8;
+    mx.kflat = (long)c->ntot * mx.r_pad;
+
+    // Delta planes for this batch
+    const int n_wt = ceil_div(W, kBNW);
+    const int Wpad = n_wt * kBNW;
+    const size_t plane = (size_t)2 * W * c->ntot * mx.r_pad;
+    c->w_dhi.ensure(plane * 2);
+    c->w_dlo.ensure(plane * 2);
+    c->w_dscale.ensure((size_t)W * (sizeof(float) + sizeof(double)) + 64);
+    float* inv_t = c->w_dscale.as<float>();
+    double* scale = reinterpret_cast<double*>(c->w_dscale.as<uint8_t>() + ((W * sizeof(float) + 15) / 16) * 16);
+    c->w_flag.ensure(16);
+    int* err = c->w_flag.as<int>();
+    LOAF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+    SpinRef s0 = spin_ref(c->sp[0]), s1 = c->nspin > 1 ? spin_ref(c->sp[1]) : s0;
+    delta_max_kernel<<<W, 256, 0, c->stream>>>(c->M, c->ntot, c->nspin, s0, s1, theta, inv_t, scale);
+    LOAF_LAUNCH_CHECK();
+    if (bf16)
+        delta_split_kernel<true><<<W * c->ntot, 128, 0, c->stream>>>(c->M, c->ntot, mx.r_pad, W, c->nspin,
+            s0, s1, theta, scale, c->w_dhi.as<uint16_t>(), c->w_dlo.as<uint16_t>());
+    else
+        delta_split_kernel<false><<<W * c->ntot, 128, 0, c->stream>>>(c->M, c->ntot, mx.r_pad, W, c->nspin,
+            s0, s1, theta, scale, c->w_dhi.as<uint16_t>(), c->w_dlo.as<uint16_t>());
+    LOAF_LAUNCH_CHECK();
+    const uint32_t idesc = tc::idesc_f16(kBM, kBN, bf16);
+
+    if (e_out) {
+        // ---- Coulomb + one-body on the tensor cores ----
+        CUtensorMap mBhi, mBlo;
+        map_2d(&mBhi, c->w_dhi.ptr, mx.kflat, 2L * W, mx.kflat, kBK, kBN);
+        map_2d(&mBlo, c->w_dlo.ptr, mx.kflat, 2L * W, mx.kflat, kBK, kBN);
+        CoulParams P;
+        P.rows = c->X + 1;
+        P.n_mt = ceil_div(P.rows, kBM);
+        P.n_wt = n_wt;
+        P.nk = (int)((mx.kflat + kBK - 1) / kBK);
+        const int tiles = P.n_mt * P.n_wt;
+        P.n_split = std::max(1, std::min(P.nk, (4 * c->sm_count + tiles - 1) / tiles));
+        P.ldp = n_wt * kBN;
+        P.idesc = idesc;
+        P.err = err;
+        c->w_cpart.ensure((size_t)P.n_split * P.rows * P.ldp * sizeof(float));
+        P.part = c->w_cpart.as<float>();
+        const int units = tiles * P.n_split;
+        LOAF_CUDA(cudaFuncSetAttribute(coulomb_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kCoulSmem));
+        coulomb_tc_kernel<<<std::min(units, c->sm_count), kThreadsTC, kCoulSmem, c->stream>>>(
+            mx.mapL_hi, mx.mapL_lo, mBhi, mBlo, P);
+        LOAF_LAUNCH_CHECK();
+        coulomb_tc_reduce_kernel<<<ceil_div(W, 32), 256, 0, c->stream>>>(
+            c->X, W, P.n_split, P.ldp, P.part, mx.L_inv.as<float>(), inv_t, mx.J0.as<double>(),
+            mx.E1_0, e_out, e_out + W);
+        LOAF_LAUNCH_CHECK();
+    }
+    if (mode == LOAF_MODE_LO) {
+        // ---- LO pair exchange on the tensor cores ----
+        double2* ek = e_out ? e_out + 2 * W : nullptr;
+        if (mx.n_pt > 0) {
+            CUtensorMap mDhi, mDlo;
+            map_delta_3d(&mDhi, c->w_dhi.ptr, mx.r_pad, c->ntot, 2L * W);
+            map_delta_3d(&mDlo, c->w_dlo.ptr, mx.r_pad, c->ntot, 2L * W);
+            LoParams P;
+            P.pt = mx.pt.as<int4>();
+            P.rowc = mx.row_c.as<float4>();
+            P.inv_t = inv_t;
+            P.n_pt = mx.n_pt;
+            P.n_wt = n_wt;
+            P.W = W;
+            P.ldp = Wpad;
+            P.nk = ceil_div(mx.r_pad, kBK);
+            P.idesc = idesc;
+            P.err = err;
+            c->w_lopart.ensure((size_t)mx.n_pt * Wpad * sizeof(double2));
+            P.part = c->w_lopart.as<double2>();
+            const int units = mx.n_pt * n_wt;
+            LOAF_CUDA(cudaFuncSetAttribute(lo_exchange_tc_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoSmem));
+            lo_exchange_tc_kernel<<<std::min(units, c->sm_count), kThreadsTC, kLoSmem, c->stream>>>(
+                mx.mapU_hi, mx.mapU_lo, mx.mapV_hi, mx.mapV_lo, mDhi, mDlo, P);
+            LOAF_LAUNCH_CHECK();
+        }
+        c->w_lopart.ensure(16);
+        lo_tc_reduce_kernel<<<ceil_div(W, 32), 256, 0, c->stream>>>(
+            mx.n_pairs, W, Wpad, mx.pair_pt0.as<int>(), mx.pair_npt.as<int>(), mx.pair_w.as<double>(),
+            mx.e0.as<double>(), mx.EK0, c->w_lopart.as<double2>(), ek, e_pairs);
+        LOAF_LAUNCH_CHECK();
+    } else if (e_out) {
+        // full mode: Coulomb on the tensor cores, exchange in FP64
+        run_energy_fp64_full(c, W, theta, e_out + 2 * W);
+    }
+}
 
 }  // namespace loaf

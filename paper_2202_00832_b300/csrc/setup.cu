@@ -50,6 +50,7 @@ void setup_load(loaf_ctx* c, int M, int X, const double* h, const double* L, int
     LOAF_REQUIRE(closed || nb >= 1, LOAF_ERR_SHAPE, "open shell needs n_beta >= 1");
 
     for (auto& s : c->sp) s.release();
+    for (auto& m : c->mix) m.release();
     c->loaded = c->compressed = c->localized = false;
     c->M = M; c->X = X; c->na = na; c->nb = nb; c->closed = closed; c->e0 = e0;
     c->nspin = closed ? 1 : 2;
@@ -407,6 +408,7 @@ void setup_compress(loaf_ctx* c, double t_svd, const double* r_ops, int n_ops, i
     LOAF_REQUIRE(!localize || (r_ops && n_ops >= 1), LOAF_ERR_ARG,
                  "localization needs the position operators");
     c->compressed = false;
+    for (auto& m : c->mix) m.release();
     for (int s = 0; s < c->nspin; ++s) {
         SpinData& sd = c->sp[s];
         std::vector<double> C = c->canonical[s];
