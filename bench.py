@@ -1,0 +1,377 @@
+"""Benchmark: walker local-energy evaluations per second at pentacene scale.
+
+One step = walkers_energy over one batch of W walkers through the C ABI: the
+whole hot path (overlap, LU, log-det, Theta, one-body + Coulomb, LO pair
+exchange, FP64 reductions).  Default workload: synthetic acene ribbon,
+M = 440 basis functions, N = 73 occupied orbitals (closed shell), X = 1800
+Cholesky vectors, W = 1024 walkers, T_SVD = 1e-4, FP16 hi+lo split products.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores instead (bounded sample of the same workload).  Under torchrun
+each rank evaluates its own W walkers (independent walker shards, no
+collective on the data path); the wall time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2202_00832_b300 import synth  # noqa: E402
+
+METRIC = "walker local-energy evals/sec at pentacene scale"
+UNIT = "walker-energies/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--walkers", type=int, default=None)
+    ap.add_argument("--threshold", type=float, default=1e-4)
+    ap.add_argument("--precision", default="fp16x3", choices=["fp16x3", "bf16x3", "fp64"])
+    ap.add_argument("--cpu-sample", type=int, default=3, help="walkers timed on the oracle")
+    ap.add_argument("--full-sample", type=int, default=64, help="walkers of the FP64 full GPU leg")
+    ap.add_argument("--no-extras", action="store_true", help="skip accuracy / FP64 / CPU legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for n, v in zip(names[1:], r[3][1:]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return {"bf16_tflops": p["bf16_tflops"], "bf16_tflops_sustained": p["bf16_tflops_sustained"],
+                "hbm_gbs": p["hbm_gbs"], "source": "measured"}
+    return {"bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "hbm_gbs": 6400.0,
+            "source": "fallback"}
+
+
+def blas_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max((i.get("num_threads", 1) for i in info), default=os.cpu_count())
+    except Exception:
+        return os.cpu_count()
+
+
+def time_oracle(mol, walkers):
+    """The FP64 oracle (exact Cholesky form) as it stands, per walker."""
+    from oracle import energy as E
+    t0 = time.perf_counter()
+    energies = [E.walker_energy(mol, w)["E"] for w in walkers]
+    dt = time.perf_counter() - t0
+    return np.array(energies), dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = synth.PENTACENE_440
+    mol = wl.molecule()
+    n = max(1, args.cpu_sample)
+    walkers = wl.walkers(mol, W=n)
+    cores = blas_threads()
+    for _ in range(min(args.warmup, 1)):
+        time_oracle(mol, walkers[:1])
+    total = 0.0
+    for s in range(args.steps):
+        _, dt = time_oracle(mol, walkers[:n])
+        total += dt
+    value = args.steps * n / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "walkers_per_step": n, "mode": "exact Cholesky form",
+                   "sample": f"{n} walkers per step of the {wl.W}-walker workload"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} walkers per step, oracle.energy.walker_energy"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2202_00832_b300.lo_afqmc import Context, position_operators
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+
+    wl = synth.PENTACENE_440
+    W = args.walkers or wl.W
+    t_gen = time.perf_counter()
+    mol = wl.molecule()
+    walk = wl.walkers(mol, W=W, first=rank * W, processes=min(16, os.cpu_count() or 1))
+    t_gen = time.perf_counter() - t_gen
+
+    stream = torch.cuda.current_stream()
+    ctx = Context(local, stream=stream.cuda_stream)
+    t_setup = time.perf_counter()
+    ctx.load_molecule(mol)
+    pct, msvd = ctx.lo_localize_compress(args.threshold, position_operators(mol), localize=True)
+    t_setup = time.perf_counter() - t_setup
+
+    phi_d = torch.from_numpy(walk).to(f"cuda:{local}")
+    e_d = torch.zeros(W, dtype=torch.complex128, device=phi_d.device)
+    ld_d = torch.zeros_like(e_d)
+    st_d = torch.zeros(W, dtype=torch.int32, device=phi_d.device)
+
+    def step():
+        ctx.walkers_energy(phi_d, mode="lo", precision=args.precision, e_out=e_d,
+                           logdet_out=ld_d, walker_status=st_d)
+
+    t_first = time.perf_counter()
+    step()  # builds the split operands once
+    t_first = time.perf_counter() - t_first
+    for _ in range(max(args.warmup, 3) - 1):
+        step()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    ctx.profile(True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * W * args.steps / (ms / 1e3)
+
+    # ---- end to end through the public API with pinned host buffers ----
+    phi_h = torch.from_numpy(walk).pin_memory()
+    e_h = torch.zeros(W, dtype=torch.complex128).pin_memory()
+    ld_h = torch.zeros_like(e_h).pin_memory()
+    st_h = torch.zeros(W, dtype=torch.int32).pin_memory()
+    ctx.walkers_energy(phi_h, mode="lo", precision=args.precision, e_out=e_h, logdet_out=ld_h,
+                       walker_status=st_h)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.walkers_energy(phi_h, mode="lo", precision=args.precision, e_out=e_h,
+                           logdet_out=ld_h, walker_status=st_h)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([t_e2e], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = world * W * args.steps / t_e2e
+    h2d = W * mol.M * mol.n_alpha * 16
+    d2h = W * (16 + 16 + 4)
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+        return
+
+    # ---- roofline of the dominant kernel (live stage timers) ----
+    peaks = load_peaks()
+    M, N, X = mol.M, mol.n_alpha, mol.X
+    sum_k = int(msvd.sum())
+    kernels = {k: v for k, v in prof.items() if k not in ("h2d_walkers", "finalize_d2h")}
+    dominant = max(kernels, key=lambda k: kernels[k][0])
+    per_launch_ms = {k: v[0] / max(v[1], 1) for k, v in kernels.items()}
+    # algorithmic work per launch (one launch covers the W-walker batch)
+    lo_flops = 8.0 * M * sum_k * W                      # a = Ubar^T Theta_j, b = Vbar Theta_i
+    n_tiles = sum((k + 127) // 128 for k in msvd)
+    lo_issued = 3 * 2 * 2 * 128 * 256 * (((M + 7) // 8 * 8 + 31) // 32 * 32) * n_tiles * ((W + 127) // 128)
+    coul_flops = 4.0 * (X + 1) * N * M * W            # dJ_g = sum_ir Lbar_gir Delta_ri (complex)
+    theta_flops = (4.0 * N * N * M + 8.0 / 3.0 * N ** 3 + 8.0 * M * N * N) * W
+    fp64_peak_tflops = 1.25  # nominal B300 FP64 (2 DFMA / clk / SM class figure)
+
+    def tc_roof(name, flops):
+        t = per_launch_ms[name] / 1e3
+        ach = flops / t / 1e12
+        pk = peaks["bf16_tflops_sustained"]
+        return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk, "traffic": None,
+                "peak_source": f"{peaks['source']} bf16 sustained (fp16 same rate)"}
+
+    rooflines = {}
+    if "lo_exchange_tc" in per_launch_ms:
+        r = tc_roof("lo_exchange_tc", lo_flops)
+        r["issued_tflops"] = lo_issued / (per_launch_ms["lo_exchange_tc"] / 1e3) / 1e12
+        rooflines["lo_exchange_tc"] = r
+    if "coulomb_tc" in per_launch_ms:
+        rooflines["coulomb_tc"] = tc_roof("coulomb_tc", coul_flops)
+    if "theta_fp64" in per_launch_ms:
+        t = per_launch_ms["theta_fp64"] / 1e3
+        ach = theta_flops / t / 1e12
+        rooflines["theta_fp64"] = {"kernel": "theta_fp64", "bound": "alu", "achieved": ach,
+                                   "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                                   "frac": ach / fp64_peak_tflops, "traffic": None,
+                                   "peak_source": "nominal FP64 ALU peak of B300"}
+    roof = rooflines.get(dominant) or next(iter(rooflines.values()))
+
+    extras = {}
+    cpu = None
+    if not args.no_extras:
+        # accuracy against the FP64 oracle and against the FP64 GPU LO path
+        n_acc = max(1, args.cpu_sample)
+        e_mixed = e_d[:n_acc].cpu().numpy()
+        sub = walk[:n_acc]
+        e_lo64, _, _ = ctx.walkers_energy(sub, mode="lo", precision="fp64")
+        ref, dt = time_oracle(mol, sub)
+        extras["accuracy_mha"] = {
+            "walkers": n_acc,
+            "mixed_vs_fp64_lo_max": float(np.abs(e_mixed - e_lo64).max() * 1e3),
+            "mixed_vs_oracle_full_max": float(np.abs(e_mixed - ref).max() * 1e3),
+            "lo_truncation_vs_oracle_full_max": float(np.abs(e_lo64 - ref).max() * 1e3),
+        }
+        cpu = {"value": n_acc / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": f"{n_acc} walkers of the workload through the FP64 oracle "
+                         f"(exact Cholesky form, {dt:.1f} s)"}
+        # the plain full-exchange FP64 path on the same GPU (subset of walkers)
+        nf = min(args.full_sample, W)
+        phi_f = phi_d[:nf].contiguous()
+        ef = torch.zeros(nf, dtype=torch.complex128, device=phi_d.device)
+        ctx.walkers_energy(phi_f, mode="full", precision="fp64", e_out=ef)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.walkers_energy(phi_f, mode="full", precision="fp64", e_out=ef)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        extras["full_fp64_gpu"] = {"value": nf / tf, "unit": UNIT, "walkers": nf}
+        extras["lo_vs_full_fp64_speedup"] = value / world / (nf / tf)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": f"{args.precision}: fp16 hi+lo x3 tcgen05 (fp32 acc) contractions; fp64 "
+                 f"overlap/LU/Theta/reductions" if args.precision != "fp64" else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{wl.name} (pentacene-scale acene ribbon)", "M": M, "N_occ": N,
+                   "X": X, "walkers_per_gpu": W, "t_svd": args.threshold, "mode": "lo",
+                   "compression_pct": pct, "mean_m_svd": float(msvd.mean()),
+                   "pairs": int(len(msvd)), "l2": "inputs larger than L2 (walkers "
+                   f"{walk.nbytes / 1e6:.0f} MB, LO factors, Delta planes)",
+                   "setup_s": t_setup, "first_call_s": t_first, "input_gen_s": t_gen},
+        "roofline": roof,
+        "rooflines": rooflines,
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "gpu_launches": int(sum(v[2] for k, v in prof.items())),
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clocks.summary(),
+        "cpu_baseline": cpu,
+        **extras,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -183,6 +183,20 @@ int loaf_num_pairs(const loaf_ctx *ctx);
  */
 loaf_status lo_get_localized_trial(const loaf_ctx *ctx, int spin, double *out);
 
+/*
+ * Stage timers.  loaf_profile(ctx, 1) resets and enables CUDA-event timers
+ * around every stage a call launches (events on the context stream, read
+ * after the call's final synchronisation); loaf_profile(ctx, 0) disables
+ * them.  loaf_profile_get returns, for stage idx < loaf_profile_count(ctx),
+ * its name (owned by the context, valid until the next loaf_profile call),
+ * the summed elapsed time in ms, the number of timed calls and the number of
+ * kernel launches those calls made.  Timers add two event records per stage.
+ */
+loaf_status loaf_profile(loaf_ctx *ctx, int enable);
+int loaf_profile_count(const loaf_ctx *ctx);
+loaf_status loaf_profile_get(const loaf_ctx *ctx, int idx, const char **name, double *total_ms,
+                             long *calls, long *launches);
+
 #ifdef __cplusplus
 }
 #endif

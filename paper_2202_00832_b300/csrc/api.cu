@@ -127,7 +127,79 @@ void stage_theta(loaf_ctx* c, int W, const double2* phi) {
 
 }  // namespace
 
+namespace loaf {
+
+static cudaEvent_t prof_event(loaf_ctx* c) {
+    if (!c->prof_pool.empty()) {
+        cudaEvent_t e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    LOAF_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+StageScope::StageScope(loaf_ctx* ctx, const char* name, int nlaunch) : c(ctx), launches(nlaunch) {
+    if (!c->prof_on) return;
+    for (size_t k = 0; k < c->prof.size(); ++k)
+        if (c->prof[k].name == name) idx = (int)k;
+    if (idx < 0) {
+        c->prof.push_back(loaf_ctx::ProfStage{name});
+        idx = (int)c->prof.size() - 1;
+    }
+    a = prof_event(c);
+    b = prof_event(c);
+    cudaEventRecord(a, c->stream);
+}
+
+void StageScope::end() {
+    if (idx < 0) return;
+    cudaEventRecord(b, c->stream);
+    c->prof_open.push_back(loaf_ctx::ProfMark{idx, a, b, launches});
+    idx = -1;
+}
+
+void prof_collect(loaf_ctx* c) {
+    for (auto& m : c->prof_open) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+            c->prof[m.stage].total_ms += ms;
+            c->prof[m.stage].calls += 1;
+            c->prof[m.stage].launches += m.launches;
+        }
+        c->prof_pool.push_back(m.a);
+        c->prof_pool.push_back(m.b);
+    }
+    c->prof_open.clear();
+}
+
+}  // namespace loaf
+
 extern "C" {
+
+loaf_status loaf_profile(loaf_ctx* c, int enable) {
+    if (!c) return LOAF_ERR_ARG;
+    return guarded(c, [&] {
+        LOAF_CUDA(cudaStreamSynchronize(c->stream));
+        prof_collect(c);
+        c->prof.clear();
+        c->prof_on = enable != 0;
+    });
+}
+
+int loaf_profile_count(const loaf_ctx* c) { return c ? (int)c->prof.size() : 0; }
+
+loaf_status loaf_profile_get(const loaf_ctx* c, int idx, const char** name, double* total_ms,
+                             long* calls, long* launches) {
+    if (!c || idx < 0 || idx >= (int)c->prof.size()) return LOAF_ERR_ARG;
+    if (name) *name = c->prof[idx].name.c_str();
+    if (total_ms) *total_ms = c->prof[idx].total_ms;
+    if (calls) *calls = c->prof[idx].calls;
+    if (launches) *launches = c->prof[idx].launches;
+    return LOAF_OK;
+}
+
 
 loaf_status loaf_create(loaf_ctx** out, int device, void* cuda_stream) {
     if (!out) return LOAF_ERR_ARG;
@@ -272,17 +344,30 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
         check_ready(c, W, phi, mode, precision);
         LOAF_REQUIRE(e_out != nullptr, LOAF_ERR_ARG, "e_out is NULL");
         ensure_workspace(c, W, mode);
-        const double2* dphi = stage_walkers(c, W, phi);
-        stage_theta(c, W, dphi);
+        const double2* dphi;
+        {
+            StageScope sc(c, "h2d_walkers", 0);
+            dphi = stage_walkers(c, W, phi);
+        }
+        {
+            StageScope sc(c, "theta_fp64", c->nspin);
+            stage_theta(c, W, dphi);
+        }
         double2* e1 = c->w_out.as<double2>();
         double2* ej = e1 + W;
         double2* ek = ej + W;
         if (precision == LOAF_PREC_FP64) {
-            run_coulomb_fp64(c, W, c->w_theta.as<double2>(), e1);
-            if (mode == LOAF_MODE_FULL)
+            {
+                StageScope sc(c, "coulomb_fp64", 2);
+                run_coulomb_fp64(c, W, c->w_theta.as<double2>(), e1);
+            }
+            if (mode == LOAF_MODE_FULL) {
+                StageScope sc(c, "exchange_full_fp64", c->nspin + 1);
                 run_energy_fp64_full(c, W, c->w_theta.as<double2>(), ek);
-            else
+            } else {
+                StageScope sc(c, "exchange_lo_fp64", 2 * c->nspin);
                 run_energy_fp64_lo(c, W, c->w_theta.as<double2>(), ek, c->w_part.as<double2>());
+            }
         } else {
             run_energy_mixed(c, W, mode, precision, c->w_theta.as<double2>(), e1, nullptr);
         }
@@ -290,19 +375,23 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
         double2* dld = de + W;
         int* dst = reinterpret_cast<int*>(dld + W);
         int* dbad = dst + W;
-        LOAF_CUDA(cudaMemsetAsync(dbad, 0, sizeof(int), c->stream));
-        finalize_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
-            W, c->nspin, c->sp[0].mult, c->nspin > 1 ? c->sp[1].mult : 0.0, c->e0,
-            c->w_logdet.as<double2>(), c->w_status.as<int>(), e1, ej, ek, de, dld, dst, dbad);
-        LOAF_LAUNCH_CHECK();
-        deliver(c, e_out, de, (size_t)W * sizeof(double2));
-        deliver(c, logdet_out, dld, (size_t)W * sizeof(double2));
-        deliver(c, walker_status, dst, (size_t)W * sizeof(int));
+        {
+            StageScope fsc(c, "finalize_d2h", 1);
+            LOAF_CUDA(cudaMemsetAsync(dbad, 0, sizeof(int), c->stream));
+            finalize_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
+                W, c->nspin, c->sp[0].mult, c->nspin > 1 ? c->sp[1].mult : 0.0, c->e0,
+                c->w_logdet.as<double2>(), c->w_status.as<int>(), e1, ej, ek, de, dld, dst, dbad);
+            LOAF_LAUNCH_CHECK();
+            deliver(c, e_out, de, (size_t)W * sizeof(double2));
+            deliver(c, logdet_out, dld, (size_t)W * sizeof(double2));
+            deliver(c, walker_status, dst, (size_t)W * sizeof(int));
+        }
         LOAF_CUDA(cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         if (precision != LOAF_PREC_FP64)
             LOAF_CUDA(cudaMemcpyAsync(&timeout, c->w_flag.ptr, sizeof(int), cudaMemcpyDeviceToHost,
                                       c->stream));
         LOAF_CUDA(cudaStreamSynchronize(c->stream));
+        prof_collect(c);
     });
     if (st == LOAF_OK && timeout) {
         c->err = "a tensor-core kernel gave up waiting on a pipeline barrier";
@@ -336,6 +425,7 @@ loaf_status walkers_pair_exchange(loaf_ctx* c, int W, const void* phi, int preci
             LOAF_CUDA(cudaMemcpyAsync(&timeout, c->w_flag.ptr, sizeof(int), cudaMemcpyDeviceToHost,
                                       c->stream));
         LOAF_CUDA(cudaStreamSynchronize(c->stream));
+        prof_collect(c);
         LOAF_REQUIRE(!timeout, LOAF_ERR_TIMEOUT,
                      "a tensor-core kernel gave up waiting on a pipeline barrier");
     });

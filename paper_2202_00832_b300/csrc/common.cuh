@@ -209,8 +209,33 @@ struct loaf_ctx {
     loaf::DevBuf w_phi, w_theta, w_z, w_lu, w_perm, w_logdet, w_status, w_out, w_part,
         w_part2, w_dhi, w_dlo, w_dscale, w_host_stage, w_cpart, w_lopart, w_flag;
 
+    // per-stage CUDA-event timers (loaf_profile); stage kernels are bracketed
+    // by events on the context stream while enabled
+    struct ProfStage { std::string name; double total_ms = 0.0; long calls = 0; long launches = 0; };
+    struct ProfMark { int stage; cudaEvent_t a, b; int launches; };
+    bool prof_on = false;
+    std::vector<ProfStage> prof;
+    std::vector<ProfMark> prof_open;
+    std::vector<cudaEvent_t> prof_pool;
+
     std::string err;
 };
+
+namespace loaf {
+// Brackets the kernels of one named stage with events on the context stream
+// (no-op while profiling is off).  Elapsed times are collected by
+// prof_collect() once the stream has been synchronized.
+struct StageScope {
+    loaf_ctx* c;
+    int idx = -1;
+    cudaEvent_t a = nullptr, b = nullptr;
+    int launches;
+    StageScope(loaf_ctx* ctx, const char* name, int nlaunch = 1);
+    void end();  // record the closing event now (idempotent)
+    ~StageScope() { end(); }
+};
+void prof_collect(loaf_ctx* c);
+}  // namespace loaf
 
 namespace loaf {
 

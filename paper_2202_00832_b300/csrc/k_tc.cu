@@ -940,6 +940,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
     int* err = c->w_flag.as<int>();
     LOAF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
     SpinRef s0 = spin_ref(c->sp[0]), s1 = c->nspin > 1 ? spin_ref(c->sp[1]) : s0;
+    StageScope dsc(c, "delta_split", 2);
     delta_max_kernel<<<W, 256, 0, c->stream>>>(c->M, c->ntot, c->nspin, s0, s1, theta, inv_t, scale);
     LOAF_LAUNCH_CHECK();
     if (bf16)
@@ -949,6 +950,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         delta_split_kernel<false><<<W * c->ntot, 128, 0, c->stream>>>(c->M, c->ntot, mx.r_pad, W, c->nspin,
             s0, s1, theta, scale, c->w_dhi.as<uint16_t>(), c->w_dlo.as<uint16_t>());
     LOAF_LAUNCH_CHECK();
+    dsc.end();
     const uint32_t idesc = tc::idesc_f16(kBM, kBN, bf16);
 
     if (e_out) {
@@ -971,9 +973,12 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         const int units = tiles * P.n_split;
         LOAF_CUDA(cudaFuncSetAttribute(coulomb_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kCoulSmem));
+        StageScope csc(c, "coulomb_tc", 1);
         coulomb_tc_kernel<<<std::min(units, c->sm_count), kThreadsTC, kCoulSmem, c->stream>>>(
             mx.mapL_hi, mx.mapL_lo, mBhi, mBlo, P);
         LOAF_LAUNCH_CHECK();
+        csc.end();
+        StageScope rsc(c, "coulomb_reduce", 1);
         coulomb_tc_reduce_kernel<<<ceil_div(W, 32), 256, 0, c->stream>>>(
             c->X, W, P.n_split, P.ldp, P.part, mx.L_inv.as<float>(), inv_t, mx.J0.as<double>(),
             mx.E1_0, e_out, e_out + W);
@@ -1002,17 +1007,20 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             const int units = mx.n_pt * n_wt;
             LOAF_CUDA(cudaFuncSetAttribute(lo_exchange_tc_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoSmem));
+            StageScope lsc(c, "lo_exchange_tc", 1);
             lo_exchange_tc_kernel<<<std::min(units, c->sm_count), kThreadsTC, kLoSmem, c->stream>>>(
                 mx.mapU_hi, mx.mapU_lo, mx.mapV_hi, mx.mapV_lo, mDhi, mDlo, P);
             LOAF_LAUNCH_CHECK();
         }
         c->w_lopart.ensure(16);
+        StageScope lrs(c, "lo_reduce", 1);
         lo_tc_reduce_kernel<<<ceil_div(W, 32), 256, 0, c->stream>>>(
             mx.n_pairs, W, Wpad, mx.pair_pt0.as<int>(), mx.pair_npt.as<int>(), mx.pair_w.as<double>(),
             mx.e0.as<double>(), mx.EK0, c->w_lopart.as<double2>(), ek, e_pairs);
         LOAF_LAUNCH_CHECK();
     } else if (e_out) {
         // full mode: Coulomb on the tensor cores, exchange in FP64
+        StageScope fsc(c, "exchange_full_fp64", c->nspin + 1);
         run_energy_fp64_full(c, W, theta, e_out + 2 * W);
     }
 }

@@ -43,6 +43,11 @@ SIGNATURES = [
     ("walkers_pair_exchange", _I, [_P, _I, _P, _I, _P]),
     ("loaf_num_pairs", _I, [_P]),
     ("lo_get_localized_trial", _I, [_P, _I, _P]),
+    ("loaf_profile", _I, [_P, _I]),
+    ("loaf_profile_count", _I, [_P]),
+    ("loaf_profile_get", _I, [_P, _I, ctypes.POINTER(ctypes.c_char_p),
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long),
+                              ctypes.POINTER(ctypes.c_long)]),
 ]
 
 _lib = None
@@ -188,6 +193,25 @@ class Context:
     @property
     def ntot(self) -> int:
         return self.n_alpha if self.closed else self.n_alpha + self.n_beta
+
+    # -- stage timers ---------------------------------------------------------
+    def profile(self, enable: bool = True):
+        """Enable (and reset) or disable the per-stage CUDA-event timers."""
+        self._check(self._lib.loaf_profile(self._h, int(enable)), "loaf_profile")
+
+    def profile_read(self) -> dict:
+        """{stage: (total_ms, calls, kernel_launches)} since profile(True)."""
+        out = {}
+        for k in range(self._lib.loaf_profile_count(self._h)):
+            name = ctypes.c_char_p()
+            ms = ctypes.c_double()
+            calls = ctypes.c_long()
+            launches = ctypes.c_long()
+            self._check(self._lib.loaf_profile_get(self._h, k, ctypes.byref(name),
+                                                   ctypes.byref(ms), ctypes.byref(calls),
+                                                   ctypes.byref(launches)), "loaf_profile_get")
+            out[name.value.decode()] = (ms.value, calls.value, launches.value)
+        return out
 
     # -- hot path -----------------------------------------------------------
     def walkers_energy(self, phi, mode="lo", precision="fp64", e_out=None, logdet_out=None,

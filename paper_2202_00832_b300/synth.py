@@ -237,9 +237,20 @@ def make_walkers(mol: Molecule, W: int, eps: float, seed0: int,
     jobs = [(trials, eps, seed0 + w, scale_sq) for w in range(first, first + W)]
     if processes and processes > 1 and W > 8:
         import multiprocessing as mp
+        import os
         ctx = mp.get_context("spawn")
-        with ctx.Pool(processes) as pool:
-            res = pool.map(_walker_job, jobs, chunksize=max(1, W // (4 * processes)))
+        saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS")}
+        os.environ["OPENBLAS_NUM_THREADS"] = "1"  # one BLAS thread per worker
+        os.environ["OMP_NUM_THREADS"] = "1"
+        try:
+            with ctx.Pool(processes) as pool:
+                res = pool.map(_walker_job, jobs, chunksize=max(1, W // (4 * processes)))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
     else:
         res = [_walker_job(j) for j in jobs]
     return np.stack([np.concatenate(r, axis=1) for r in res])
