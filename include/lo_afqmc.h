@@ -184,6 +184,35 @@ int loaf_num_pairs(const loaf_ctx *ctx);
 loaf_status lo_get_localized_trial(const loaf_ctx *ctx, int spin, double *out);
 
 /*
+ * walkers_theta_noalloc -- walkers_theta for callers that may not allocate
+ * device memory while they run: code that owns a fixed memory budget (an
+ * allocator that hands out one arena up front, a job that must not grow its
+ * footprint once it is running), or code that runs while allocation is off
+ * limits.  The paper has no counterpart; it is a deployment variant of the
+ * first stage only.
+ *
+ * Same result as walkers_theta (Theta = phi (Phi_T^T phi)^-1 per spin and
+ * log <Phi_T|phi>), but every buffer is the caller's and on the device, and
+ * the kernel's scratch lives in one fixed 32 MiB array compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  No cudaMalloc, cudaFree or allocating library routine is called.
+ *   phi            device, W x M x Ntot complex128
+ *   theta_out      device, W x Ntot x M complex128 (orbital-major)
+ *   logdet_out     device, W complex128, or NULL
+ *   walker_status  device, W ints, or NULL (singular walkers are reported
+ *                  here only; the call itself returns LOAF_OK)
+ * Limits: 1 <= W <= 4096 and W * Ntot * M <= 2,086,912; larger requests are
+ * rejected with LOAF_ERR_SHAPE before any work is queued.
+ * The call is asynchronous on the context stream.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * should come before any stream capture.  All calls share the one array:
+ * calls whose work overlaps on the GPU (other streams, other contexts on the
+ * same device, other threads) race on it and must be serialised by the caller.
+ */
+loaf_status walkers_theta_noalloc(loaf_ctx *ctx, int W, const void *phi, void *theta_out,
+                                  void *logdet_out, int *walker_status);
+
+/*
  * Stage timers.  loaf_profile(ctx, 1) resets and enables CUDA-event timers
  * around every stage a call launches (events on the context stream, read
  * after the call's final synchronisation); loaf_profile(ctx, 0) disables

@@ -8,6 +8,8 @@
 // FMAs per walker and spin.
 #include "common.cuh"
 
+#include <mutex>
+
 namespace loaf {
 
 namespace {
@@ -244,4 +246,128 @@ void run_theta_fp64(loaf_ctx* c, int W, const double2* phi, double2* theta, doub
     }
 }
 
+// ---------------------------------------------------------------------------
+// walkers_theta_noalloc: the Theta kernel above with its scratch (the forward-
+// solve rows Z and the per-spin log-det / status parts) in one fixed device
+// array, for callers that must not allocate device memory during a call.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = 32ull << 20;  // 32 MiB, held by every device that loads the library
+constexpr int kNoAllocMaxW = 4096;
+constexpr size_t kNoAllocLdBytes = 2ull * kNoAllocMaxW * sizeof(double2);
+constexpr size_t kNoAllocStBytes = 2ull * kNoAllocMaxW * sizeof(int);
+constexpr size_t kNoAllocZOffset = kNoAllocLdBytes + kNoAllocStBytes;  // multiple of 256
+constexpr size_t kNoAllocZEntries = (kNoAllocBytes - kNoAllocZOffset) / sizeof(double2);
+
+// layout: [2][kNoAllocMaxW] double2 log-det parts | [2][kNoAllocMaxW] int
+// status parts | Z rows (W x ntot x M complex) in the rest
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};  // device address of g_noalloc_scratch per device ordinal
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side symbol is only a stand-in for it).
+unsigned char* noalloc_scratch(int device) {
+    LOAF_REQUIRE(device >= 0 && device < 256, LOAF_ERR_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        LOAF_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[device] = p;
+    }
+    return static_cast<unsigned char*>(g_noalloc_addr[device]);
+}
+
+__global__ void theta_noalloc_combine_kernel(int W, int nspin, double mult0,
+                                             const double2* __restrict__ ld_part,
+                                             const int* __restrict__ st_part,
+                                             double2* __restrict__ ld_out,
+                                             int* __restrict__ st_out) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    double2 ld = cscale(ld_part[w], mult0 == 2.0 ? 2.0 : 1.0);
+    int st = st_part[w];
+    if (nspin > 1) {
+        ld = cadd(ld, ld_part[kNoAllocMaxW + w]);
+        st = max(st, st_part[kNoAllocMaxW + w]);
+    }
+    if (ld_out) ld_out[w] = ld;
+    if (st_out) st_out[w] = st;
+}
+
+bool on_device(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
 }  // namespace loaf
+
+extern "C" loaf_status walkers_theta_noalloc(loaf_ctx* c, int W, const void* phi, void* theta_out,
+                                             void* logdet_out, int* walker_status) {
+    using namespace loaf;
+    if (!c) return LOAF_ERR_ARG;
+    try {
+        LOAF_REQUIRE(c->loaded, LOAF_ERR_NOT_READY, "ao_load_cholesky has not been called");
+        LOAF_REQUIRE(phi && theta_out, LOAF_ERR_ARG, "phi and theta_out are required");
+        LOAF_REQUIRE(W >= 1 && W <= kNoAllocMaxW, LOAF_ERR_SHAPE,
+                     "walkers_theta_noalloc: W must be between 1 and 4096");
+        const size_t need = (size_t)W * c->ntot * c->M;
+        LOAF_REQUIRE(need <= kNoAllocZEntries, LOAF_ERR_SHAPE,
+                     "walkers_theta_noalloc: W * Ntot * M = " + std::to_string(need) +
+                         " exceeds the fixed scratch (" + std::to_string(kNoAllocZEntries) +
+                         " complex entries, 32 MiB); use walkers_theta or fewer walkers");
+        LOAF_CUDA(cudaSetDevice(c->device));
+        LOAF_REQUIRE(on_device(phi) && on_device(theta_out) &&
+                         (!logdet_out || on_device(logdet_out)) &&
+                         (!walker_status || on_device(walker_status)),
+                     LOAF_ERR_ARG, "walkers_theta_noalloc takes device buffers only");
+        unsigned char* scratch = noalloc_scratch(c->device);
+        double2* ld_part = reinterpret_cast<double2*>(scratch);
+        int* st_part = reinterpret_cast<int*>(scratch + kNoAllocLdBytes);
+        double2* zbuf = reinterpret_cast<double2*>(scratch + kNoAllocZOffset);
+        const double2* dphi = static_cast<const double2*>(phi);
+        double2* theta = static_cast<double2*>(theta_out);
+        for (int s = 0; s < c->nspin; ++s) {
+            const SpinData& sd = c->sp[s];
+            const int NI = (sd.N + kTile - 1) / kTile;
+            const size_t smem = (size_t)sd.N * sd.N * sizeof(double2) +
+                                (size_t)kChunk * sd.N * (sizeof(double2) + sizeof(double)) +
+                                (size_t)sd.N * sizeof(int) + 16;
+            auto launch = [&](auto kern) {
+                LOAF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+                kern<<<W, kThreads, smem, c->stream>>>(
+                    c->M, sd.N, c->ntot, sd.d_trial.as<double>(), dphi + sd.col0,
+                    theta + (size_t)sd.col0 * c->M, zbuf + (size_t)sd.col0 * c->M,
+                    ld_part + (size_t)s * kNoAllocMaxW, st_part + (size_t)s * kNoAllocMaxW);
+                LOAF_LAUNCH_CHECK();
+            };
+            switch (NI) {
+                case 1: launch(theta_fp64_kernel<1>); break;
+                case 2: launch(theta_fp64_kernel<2>); break;
+                case 3: launch(theta_fp64_kernel<3>); break;
+                case 4: launch(theta_fp64_kernel<4>); break;
+                case 5: launch(theta_fp64_kernel<5>); break;
+                case 6: launch(theta_fp64_kernel<6>); break;
+                default: throw Error{LOAF_ERR_SHAPE, "occupied orbitals beyond LOAF_MAX_NOCC"};
+            }
+        }
+        theta_noalloc_combine_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
+            W, c->nspin, c->sp[0].mult, ld_part, st_part, static_cast<double2*>(logdet_out),
+            walker_status);
+        LOAF_LAUNCH_CHECK();
+        c->err.clear();
+        return LOAF_OK;
+    } catch (const Error& e) {
+        c->err = e.msg;
+        return e.code;
+    }
+}

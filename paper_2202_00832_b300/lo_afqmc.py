@@ -43,6 +43,7 @@ SIGNATURES = [
     ("walkers_pair_exchange", _I, [_P, _I, _P, _I, _P]),
     ("loaf_num_pairs", _I, [_P]),
     ("lo_get_localized_trial", _I, [_P, _I, _P]),
+    ("walkers_theta_noalloc", _I, [_P, _I, _P, _P, _P, _P]),
     ("loaf_profile", _I, [_P, _I]),
     ("loaf_profile_count", _I, [_P]),
     ("loaf_profile_get", _I, [_P, _I, ctypes.POINTER(ctypes.c_char_p),
@@ -248,6 +249,21 @@ class Context:
         if code == 5 and not raise_on_singular:
             return theta_out, logdet_out, walker_status
         self._check(code, "walkers_theta")
+        return theta_out, logdet_out, walker_status
+
+    def walkers_theta_noalloc(self, phi, theta_out, logdet_out=None, walker_status=None):
+        """walkers_theta with device buffers only and no device allocation.
+
+        For callers that cannot allocate during the call; scratch comes from a
+        fixed 32 MiB array in the library (W * Ntot * M <= 2,086,912, W <= 4096).
+        Asynchronous on the context stream; singular walkers show up only in
+        walker_status.
+        """
+        _check_dtype(phi, "c16")
+        W = int(phi.shape[0])
+        self._check(self._lib.walkers_theta_noalloc(self._h, W, _ptr(phi), _ptr(theta_out),
+                                                    _ptr(logdet_out), _ptr(walker_status)),
+                    "walkers_theta_noalloc")
         return theta_out, logdet_out, walker_status
 
     def walkers_pair_exchange(self, phi, precision="fp64", out=None):
