@@ -11,8 +11,10 @@
 //
 // Kernels (sm_103a, one CTA per SM, warp-specialised, 192 threads):
 //   coulomb_tc_kernel  dJ[g][w] = sum_(c,r) Lbar'[g][c][r] Delta[w][c][r]
-//                      (rows g < X: Cholesky vectors, row X: hbar -> dE1),
-//                      split over the (c, r) contraction; FP32 partial tiles.
+//                      (rows g < X: Cholesky vectors, row X: hbar -> dE1):
+//                      128-term TMEM chains folded into double-float
+//                      registers, FP64 partials per split of the contraction
+//                      (576 threads: 16 epilogue warps).
 //   lo_exchange_tc_kernel  per pair tile (<= 128 ranks of one pair [ij]) and
 //                      128 walkers: a = Ubar^T Delta_j, b = Vbar Delta_i in two
 //                      TMEM accumulators, then the epilogue forms
@@ -337,37 +339,70 @@ __device__ inline uint8_t* align1024(uint8_t* p) {
     return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
 
+// ---- Coulomb kernel geometry ----
+// The tensor cores accumulate in FP32 with an error that grows with the
+// length of the accumulation chain (measured on B300: 0.235 / 0.151 / 0.038 /
+// 0.022 mHa in E_J at pentacene scale for 803 / 446 / 111 / 32-term chains).
+// Chains are therefore cut at kCGroup k-chunks (128 terms): each group
+// accumulates into one of four rotating TMEM buffers, and the epilogue folds
+// the finished buffer into a double-float (hi, lo) register accumulator with
+// an error-free TwoSum, so the long (c, r) contraction is summed to ~2^-44.
+constexpr int kCBN = 128;            // columns: 64 walkers, re/im interleaved
+constexpr int kCStages = 4;
+constexpr int kCGroup = 4;           // k-chunks per TMEM accumulation chain
+constexpr int kCBufs = 4;            // TMEM buffers of kCBN columns
+constexpr int kCEpiWarps = 16;       // 4 per TMEM lane quarter, 32 columns each
+constexpr int kCThreads = 64 + 32 * kCEpiWarps;
+constexpr uint32_t kCTileB = kCBN * kRowB;  // 8 KB
+
+struct CoulShared {
+    uint64_t full[kCStages];
+    uint64_t empty[kCStages];
+    uint64_t acc_full[kCBufs];
+    uint64_t acc_empty[kCBufs];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
 struct CoulParams {
-    float* part;       // [split][rows][ldp] FP32 partial accumulators
+    double* part;      // [split][rows][ldp] FP64 partial sums
     int rows;          // X + 1
     int n_mt, n_wt, n_split, nk, ldp;
     uint32_t idesc;
     int* err;
 };
 
-// dJ partial tile: rows g (128) x 256 columns (128 walkers, re/im), k-chunks
-// [split * nk / n_split, (split+1) * nk / n_split)
-__global__ void __launch_bounds__(kThreadsTC, 1)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += e;
+}
+
+// dJ partial tile: rows g (128) x 128 columns (64 walkers, re/im) over the
+// k-chunks [split * nk / n_split, (split+1) * nk / n_split)
+__global__ void __launch_bounds__(kCThreads, 1)
 coulomb_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                   const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
                   CoulParams P) {
     extern __shared__ uint8_t dyn_smem[];
-    __shared__ TCShared sh;
+    __shared__ CoulShared sh;
     uint8_t* base = align1024(dyn_smem);
-    constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kTileB;  // 48 KB
+    constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kCTileB;  // 32 KB
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_units = P.n_mt * P.n_wt * P.n_split;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) { tc::mbar_init(&sh.full[s], 1); tc::mbar_init(&sh.empty[s], 1); }
-        tc::mbar_init(&sh.tmem_full, 1);
-        tc::mbar_init(&sh.tmem_empty, 4);
+        for (int s = 0; s < kCStages; ++s) { tc::mbar_init(&sh.full[s], 1); tc::mbar_init(&sh.empty[s], 1); }
+        for (int b = 0; b < kCBufs; ++b) { tc::mbar_init(&sh.acc_full[b], 1); tc::mbar_init(&sh.acc_empty[b], kCEpiWarps); }
         tc::mbar_init(&sh.drain, 1);
         sh.abort = 0;
         tc::fence_barrier_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(&sh.tmem_base, kBN);
+        tc::tmem_alloc(&sh.tmem_base, kCBufs * kCBN);
         tc::tmem_relinquish();
     }
     if (threadIdx.x == 32) {
@@ -383,8 +418,7 @@ coulomb_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constan
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
         int s = 0;
-        uint32_t ph = 0;
-        uint32_t filled = 0, last_par = 0;
+        uint32_t ph = 0, filled = 0, last_par = 0;
         for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
             const int mt = u % P.n_mt, wt = (u / P.n_mt) % P.n_wt, sp = u / (P.n_mt * P.n_wt);
             const int k0 = (int)((long)sp * P.nk / P.n_split), k1 = (int)((long)(sp + 1) * P.nk / P.n_split);
@@ -394,16 +428,16 @@ coulomb_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constan
                 tc::mbar_arrive_expect_tx(&sh.full[s], kStageBytes);
                 tc::tma_load_2d(st, &mAhi, &sh.full[s], kc * kBK, mt * kBM);
                 tc::tma_load_2d(st + kTileA, &mAlo, &sh.full[s], kc * kBK, mt * kBM);
-                tc::tma_load_2d(st + 2 * kTileA, &mBhi, &sh.full[s], kc * kBK, wt * kBN);
-                tc::tma_load_2d(st + 2 * kTileA + kTileB, &mBlo, &sh.full[s], kc * kBK, wt * kBN);
+                tc::tma_load_2d(st + 2 * kTileA, &mBhi, &sh.full[s], kc * kBK, wt * kCBN);
+                tc::tma_load_2d(st + 2 * kTileA + kCTileB, &mBlo, &sh.full[s], kc * kBK, wt * kCBN);
                 filled |= 1u << s;
                 last_par = (last_par & ~(1u << s)) | (ph << s);
-                if (++s == kStages) { s = 0; ph ^= 1; }
+                if (++s == kCStages) { s = 0; ph ^= 1; }
             }
         }
         // drain: every stage ever filled must have landed before the CTA exits
         if (*abort) {
-            for (int q = 0; q < kStages; ++q)
+            for (int q = 0; q < kCStages; ++q)
                 if (filled & (1u << q)) {
                     volatile int never = 0;
                     tc::mbar_wait(&sh.full[q], (last_par >> q) & 1, &never);
@@ -412,71 +446,92 @@ coulomb_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constan
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         int s = 0;
-        uint32_t ph = 0, tph = 0;
-        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
+        uint32_t ph = 0, gcount = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < n_units && ok && !*abort; u += gridDim.x) {
             const int sp = u / (P.n_mt * P.n_wt);
             const int k0 = (int)((long)sp * P.nk / P.n_split), k1 = (int)((long)(sp + 1) * P.nk / P.n_split);
-            if (!tc::mbar_wait(&sh.tmem_empty, tph ^ 1, abort)) break;
-            tc::tc_fence_after();
-            bool ok = true;
-            for (int kc = k0; kc < k1; ++kc) {
-                if (!tc::mbar_wait(&sh.full[s], ph, abort)) { ok = false; break; }
+            for (int g0 = k0; g0 < k1 && ok; g0 += kCGroup, ++gcount) {
+                const uint32_t b = gcount % kCBufs, use = gcount / kCBufs;
+                if (!tc::mbar_wait(&sh.acc_empty[b], (use & 1) ^ 1, abort)) { ok = false; break; }
                 tc::tc_fence_after();
-                const uint32_t st = tc::smem_u32(base + s * kStageBytes);
+                const uint32_t d = tmem + b * kCBN;
+                const int g1 = min(g0 + kCGroup, k1);
+                for (int kc = g0; kc < g1; ++kc) {
+                    if (!tc::mbar_wait(&sh.full[s], ph, abort)) { ok = false; break; }
+                    tc::tc_fence_after();
+                    const uint32_t st = tc::smem_u32(base + s * kStageBytes);
 #pragma unroll
-                for (int kk = 0; kk < kBK / 16; ++kk) {
-                    const uint32_t off = kk * 32;
-                    const uint64_t ahi = tc::smem_desc(st + off, kRowB);
-                    const uint64_t alo = tc::smem_desc(st + kTileA + off, kRowB);
-                    const uint64_t bhi = tc::smem_desc(st + 2 * kTileA + off, kRowB);
-                    const uint64_t blo = tc::smem_desc(st + 2 * kTileA + kTileB + off, kRowB);
-                    const uint32_t acc = (kc > k0 || kk > 0) ? 1u : 0u;
-                    tc::mma_f16(tmem, ahi, bhi, P.idesc, acc);
-                    tc::mma_f16(tmem, ahi, blo, P.idesc, 1u);
-                    tc::mma_f16(tmem, alo, bhi, P.idesc, 1u);
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint32_t off = kk * 32;
+                        const uint64_t ahi = tc::smem_desc(st + off, kRowB);
+                        const uint64_t alo = tc::smem_desc(st + kTileA + off, kRowB);
+                        const uint64_t bhi = tc::smem_desc(st + 2 * kTileA + off, kRowB);
+                        const uint64_t blo = tc::smem_desc(st + 2 * kTileA + kCTileB + off, kRowB);
+                        const uint32_t acc = (kc > g0 || kk > 0) ? 1u : 0u;
+                        tc::mma_f16(d, ahi, bhi, P.idesc, acc);
+                        tc::mma_f16(d, ahi, blo, P.idesc, 1u);
+                        tc::mma_f16(d, alo, bhi, P.idesc, 1u);
+                    }
+                    tc::mma_commit(&sh.empty[s]);
+                    if (++s == kCStages) { s = 0; ph ^= 1; }
                 }
-                tc::mma_commit(&sh.empty[s]);
-                if (++s == kStages) { s = 0; ph ^= 1; }
+                if (!ok) break;
+                tc::mma_commit(&sh.acc_full[b]);
             }
-            if (!ok) break;
-            tc::mma_commit(&sh.tmem_full);
-            tph ^= 1;
         }
         tc::mma_commit(&sh.drain);
         volatile int never = 0;
         tc::mbar_wait(&sh.drain, 0, &never);
     } else if (warp >= 2) {
-        // ---------------- epilogue: TMEM -> FP32 partial tile ----------------
-        const int q = warp & 3;  // TMEM lane quarter this warp may access
-        uint32_t tph = 0;
-        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
+        // ---------------- epilogue: TMEM groups -> double-float -> FP64 ----------------
+        const int q = warp & 3;          // TMEM lane quarter this warp may access
+        const int h = (warp - 2) >> 2;   // column block: 32 columns per warp
+        uint32_t gcount = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < n_units && ok && !*abort; u += gridDim.x) {
             const int mt = u % P.n_mt, wt = (u / P.n_mt) % P.n_wt, sp = u / (P.n_mt * P.n_wt);
-            if (!tc::mbar_wait(&sh.tmem_full, tph, abort)) break;
-            tc::tc_fence_after();
-            const int g = mt * kBM + q * 32 + lane;
-            float* dst = P.part + ((size_t)sp * P.rows + g) * P.ldp + (size_t)wt * kBN;
-#pragma unroll 1
-            for (int ch = 0; ch < kBN / 32; ++ch) {
-                float v[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + ch * 32, v);
-                tc::tmem_wait_ld();
-                if (g < P.rows) {
-                    float4* d4 = reinterpret_cast<float4*>(dst + ch * 32);
+            const int k0 = (int)((long)sp * P.nk / P.n_split), k1 = (int)((long)(sp + 1) * P.nk / P.n_split);
+            // hi in registers, lo in shared memory ([column][epilogue thread])
+            float hi[32];
+            float* lo = reinterpret_cast<float*>(base + kCStages * kStageBytes) + (threadIdx.x - 64);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        d4[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            for (int k = 0; k < 32; ++k) { hi[k] = 0.f; lo[k * kCEpiWarps * 32] = 0.f; }
+            for (int g0 = k0; g0 < k1; g0 += kCGroup, ++gcount) {
+                const uint32_t b = gcount % kCBufs, use = gcount / kCBufs;
+                if (!tc::mbar_wait(&sh.acc_full[b], use & 1, abort)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + b * kCBN + h * 32;
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+                    float v[16];
+                    tc::tmem_ld16(taddr + part * 16, v);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        two_sum_acc(hi[part * 16 + k], lo[(part * 16 + k) * kCEpiWarps * 32], v[k]);
                 }
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&sh.acc_empty[b]);
             }
-            tc::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&sh.tmem_empty);
-            tph ^= 1;
+            if (!ok) break;
+            const int g = mt * kBM + q * 32 + lane;
+            if (g < P.rows) {
+                double2* dst = reinterpret_cast<double2*>(
+                    P.part + ((size_t)sp * P.rows + g) * P.ldp + (size_t)wt * kCBN + h * 32);
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    dst[k] = make_double2((double)hi[2 * k] + (double)lo[(2 * k) * kCEpiWarps * 32],
+                                          (double)hi[2 * k + 1] +
+                                              (double)lo[(2 * k + 1) * kCEpiWarps * 32]);
+            }
         }
     }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, kBN);
+    if (warp == 0) tc::tmem_dealloc(tmem, kCBufs * kCBN);
     if (threadIdx.x == 0 && sh.abort) atomicExch(P.err, 1);
 }
 
@@ -673,7 +728,7 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
 
 // E1 = E1_0 + dE1,  E_J = 1/2 sum_g (J0_g + dJ_g)^2,  dJ from the split partials
 __global__ void coulomb_tc_reduce_kernel(int X, int W, int n_split, int ldp,
-                                         const float* __restrict__ part,
+                                         const double* __restrict__ part,
                                          const float* __restrict__ inv_s,
                                          const float* __restrict__ inv_t,
                                          const double* __restrict__ J0, double E1_0,
@@ -689,7 +744,7 @@ __global__ void coulomb_tc_reduce_kernel(int X, int W, int n_split, int ldp,
         for (int g = gg; g < X; g += 8) {
             double re = 0.0, im = 0.0;
             for (int s = 0; s < n_split; ++s) {
-                const float2 v = *reinterpret_cast<const float2*>(part + s * plane + (size_t)g * ldp + 2 * w);
+                const double2 v = *reinterpret_cast<const double2*>(part + s * plane + (size_t)g * ldp + 2 * w);
                 re += v.x;
                 im += v.y;
             }
@@ -706,7 +761,7 @@ __global__ void coulomb_tc_reduce_kernel(int X, int W, int n_split, int ldp,
         ej[w] = cscale(t, 0.5);
         double re = 0.0, im = 0.0;
         for (int s = 0; s < n_split; ++s) {
-            const float2 v = *reinterpret_cast<const float2*>(part + s * plane + (size_t)X * ldp + 2 * w);
+            const double2 v = *reinterpret_cast<const double2*>(part + s * plane + (size_t)X * ldp + 2 * w);
             re += v.x;
             im += v.y;
         }
@@ -907,7 +962,8 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     mx.lo_ready = true;
 }
 
-constexpr size_t kCoulSmem = kStages * (2 * kTileA + 2 * kTileB) + 1024;
+constexpr size_t kCoulSmem =
+    kCStages * (2 * kTileA + 2 * kCTileB) + 32 * kCEpiWarps * 32 * sizeof(float) + 1024;
 constexpr size_t kLoSmem = kStages * (4 * kTileA + 4 * kTileB) + 1024;
 
 }  // namespace
@@ -956,25 +1012,25 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
     if (e_out) {
         // ---- Coulomb + one-body on the tensor cores ----
         CUtensorMap mBhi, mBlo;
-        map_2d(&mBhi, c->w_dhi.ptr, mx.kflat, 2L * W, mx.kflat, kBK, kBN);
-        map_2d(&mBlo, c->w_dlo.ptr, mx.kflat, 2L * W, mx.kflat, kBK, kBN);
+        map_2d(&mBhi, c->w_dhi.ptr, mx.kflat, 2L * W, mx.kflat, kBK, kCBN);
+        map_2d(&mBlo, c->w_dlo.ptr, mx.kflat, 2L * W, mx.kflat, kBK, kCBN);
         CoulParams P;
         P.rows = c->X + 1;
         P.n_mt = ceil_div(P.rows, kBM);
-        P.n_wt = n_wt;
+        P.n_wt = ceil_div(2L * W, kCBN);
         P.nk = (int)((mx.kflat + kBK - 1) / kBK);
         const int tiles = P.n_mt * P.n_wt;
-        P.n_split = std::max(1, std::min(P.nk, (4 * c->sm_count + tiles - 1) / tiles));
-        P.ldp = n_wt * kBN;
-        P.idesc = idesc;
+        P.n_split = std::max(1, std::min(ceil_div(P.nk, kCGroup), (3 * c->sm_count + tiles - 1) / tiles));
+        P.ldp = P.n_wt * kCBN;
+        P.idesc = tc::idesc_f16(kBM, kCBN, bf16);
         P.err = err;
-        c->w_cpart.ensure((size_t)P.n_split * P.rows * P.ldp * sizeof(float));
-        P.part = c->w_cpart.as<float>();
+        c->w_cpart.ensure((size_t)P.n_split * P.rows * P.ldp * sizeof(double));
+        P.part = c->w_cpart.as<double>();
         const int units = tiles * P.n_split;
         LOAF_CUDA(cudaFuncSetAttribute(coulomb_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kCoulSmem));
         StageScope csc(c, "coulomb_tc", 1);
-        coulomb_tc_kernel<<<std::min(units, c->sm_count), kThreadsTC, kCoulSmem, c->stream>>>(
+        coulomb_tc_kernel<<<std::min(units, c->sm_count), kCThreads, kCoulSmem, c->stream>>>(
             mx.mapL_hi, mx.mapL_lo, mBhi, mBlo, P);
         LOAF_LAUNCH_CHECK();
         csc.end();

@@ -100,3 +100,24 @@ def test_repeat_calls_are_deterministic(chain_lo):
     a, _, _ = ctx.walkers_energy(walk, mode="lo", precision="fp16x3")
     b, _, _ = ctx.walkers_energy(walk, mode="lo", precision="fp16x3")
     assert np.array_equal(a, b)
+
+
+def test_naphthalene_scale_long_contractions():
+    """M = 250, N = 34, X = 1000 (honeycomb patch): the Coulomb contraction runs
+    over N*M = 8500 terms, far beyond one tensor-core accumulation chain.  Mixed
+    LO energies stay within 0.1 mHa of the FP64 LO path on the same factors,
+    and the FP64 full path matches the oracle."""
+    wl = synth.NAPHTHALENE_250
+    mol = wl.molecule()
+    walk = wl.walkers(mol, W=48)
+    ctx = Context(0)
+    ctx.load_molecule(mol)
+    e64f, _, _ = ctx.walkers_energy(walk[:3], mode="full", precision="fp64")
+    ref = oracle_energies(mol, walk[:3])
+    assert np.max(np.abs(e64f - ref) / np.abs(ref)) < 1e-10
+    ctx.lo_localize_compress(1e-4, position_operators(mol), localize=True)
+    e64, _, _ = ctx.walkers_energy(walk, mode="lo", precision="fp64")
+    e16, _, _ = ctx.walkers_energy(walk, mode="lo", precision="fp16x3")
+    err = np.abs(e16 - e64).max()
+    print("naphthalene fp16x3 vs fp64 LO max |dE| (Ha):", err)
+    assert err < TOL_MIXED
