@@ -32,6 +32,8 @@ sys.path.insert(0, ROOT)
 from paper_2202_00832_b300 import synth  # noqa: E402
 
 METRIC = "walker local-energy evals/sec at pentacene scale"
+WORKLOADS = {"pentacene": synth.PENTACENE_440, "naphthalene": synth.NAPHTHALENE_250,
+             "chain": synth.CHAIN_60}
 UNIT = "walker-energies/s"
 
 
@@ -42,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--walkers", type=int, default=None)
+    ap.add_argument("--workload", default="pentacene", choices=sorted(WORKLOADS),
+                    help="pentacene (the benchmark) or a smaller system for profiling")
     ap.add_argument("--threshold", type=float, default=1e-4)
     ap.add_argument("--precision", default="fp16x3", choices=["fp16x3", "bf16x3", "fp64"])
     ap.add_argument("--cpu-sample", type=int, default=3, help="walkers timed on the oracle")
@@ -149,7 +153,7 @@ def time_oracle(mol, walkers):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    wl = synth.PENTACENE_440
+    wl = WORKLOADS[args.workload]
     mol = wl.molecule()
     n = max(1, args.cpu_sample)
     walkers = wl.walkers(mol, W=n)
@@ -185,7 +189,7 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("gloo", rank=rank, world_size=world)
 
-    wl = synth.PENTACENE_440
+    wl = WORKLOADS[args.workload]
     W = args.walkers or wl.W
     t_gen = time.perf_counter()
     mol = wl.molecule()
@@ -276,8 +280,9 @@ def run_ours(args, rank, world, local):
     per_launch_ms = {k: v[0] / max(v[1], 1) for k, v in kernels.items()}
     # algorithmic work per launch (one launch covers the W-walker batch)
     lo_flops = 8.0 * M * sum_k * W                      # a = Ubar^T Theta_j, b = Vbar Theta_i
-    n_tiles = sum((k + 127) // 128 for k in msvd)
-    lo_issued = 3 * 2 * 2 * 128 * 256 * (((M + 7) // 8 * 8 + 31) // 32 * 32) * n_tiles * ((W + 127) // 128)
+    n_tiles = sum((int(k) + 127) // 128 for k in msvd)
+    lo_issued = (3 * 2 * 2 * 128 * 256 * int(((M + 7) // 8 * 8 + 31) // 32 * 32) * int(n_tiles)
+                 * int((W + 127) // 128))
     coul_flops = 4.0 * (X + 1) * N * M * W            # dJ_g = sum_ir Lbar_gir Delta_ri (complex)
     theta_flops = (4.0 * N * N * M + 8.0 / 3.0 * N ** 3 + 8.0 * M * N * N) * W
     fp64_peak_tflops = 1.25  # nominal B300 FP64 (2 DFMA / clk / SM class figure)
@@ -344,7 +349,8 @@ def run_ours(args, rank, world, local):
         "dtype": f"{args.precision}: fp16 hi+lo x3 tcgen05 (fp32 acc) contractions; fp64 "
                  f"overlap/LU/Theta/reductions" if args.precision != "fp64" else "f64",
         "data": "synthetic",
-        "config": {"workload": f"{wl.name} (pentacene-scale acene ribbon)", "M": M, "N_occ": N,
+        "config": {"workload": wl.name + (" (pentacene-scale acene ribbon)" if wl is synth.PENTACENE_440
+                                          else ""), "M": M, "N_occ": N,
                    "X": X, "walkers_per_gpu": W, "t_svd": args.threshold, "mode": "lo",
                    "compression_pct": pct, "mean_m_svd": float(msvd.mean()),
                    "pairs": int(len(msvd)), "l2": "inputs larger than L2 (walkers "
