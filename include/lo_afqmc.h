@@ -184,6 +184,44 @@ int loaf_num_pairs(const loaf_ctx *ctx);
 loaf_status lo_get_localized_trial(const loaf_ctx *ctx, int spin, double *out);
 
 /*
+ * Learned pair screen.  The paper's conclusions (Sec. 5) propose screening
+ * electron pairs and keeping only those that contribute meaningfully; they
+ * give no algorithm.  Here a network 8 -> 64 -> 64 -> 1 (tanh hidden layers,
+ * FP16 weights and activations, FP32 accumulation) predicts log10 of the
+ * largest |e_ij| of each pair [ij] from eight walker-independent descriptors
+ * (centroid distance d, 1/(1+d), spread sum and difference of the two
+ * localized orbitals, log s_1, log s_2, M_SVD/M, log |Y^[ij]|_F); pairs
+ * predicted below a cutoff are left out of the LO exchange (their trial part
+ * e0 included).  The unscreened evaluation stays available.
+ *
+ * pair_screen_train: computes the training labels with the FP16X3 LO path on
+ *   W_train walkers (phi as in walkers_energy, host or device), standardises
+ *   descriptors and labels, and runs `epochs` full-batch Adam steps (beta1 0.9,
+ *   beta2 0.999, eps 1e-8, learning rate lr) from init_params (host,
+ *   loaf_screen_num_params() floats in the order W1[64][8], b1[64], W2[64][64],
+ *   b2[64], W3[64], b3).  loss_history (host, `epochs` floats, may be NULL)
+ *   receives the mean squared error before each step.  Clears any screen.
+ * pair_screen_set: cutoff_ha >= 0 keeps pairs with predicted |e_ij| >= cutoff;
+ *   cutoff_ha < 0 removes the screen.  kept_pairs (may be NULL) gets the count.
+ * pair_screen_query: copies (each may be NULL) the trained parameters, the
+ *   8 descriptors of every pair (double, pair-major), the predicted and the
+ *   label log10 |e_ij|, and the keep mask (1 = evaluated).
+ * mlp_loss_grad: the network's mean squared error and its gradient with
+ *   respect to the parameters on n standardised samples x (n x 8) and
+ *   targets t (host arrays), on CUDA device `device` -- the kernels training
+ *   uses, exposed for gradient checks.
+ */
+int loaf_screen_num_params(void);
+loaf_status pair_screen_train(loaf_ctx *ctx, int W_train, const void *phi, int epochs, float lr,
+                              const float *init_params, float *loss_history);
+loaf_status pair_screen_set(loaf_ctx *ctx, double cutoff_ha, int *kept_pairs);
+loaf_status pair_screen_query(const loaf_ctx *ctx, float *params_out, double *features_out,
+                              double *pred_log10_out, double *target_log10_out,
+                              unsigned char *keep_out);
+loaf_status mlp_loss_grad(int device, int n, const float *x, const float *t, const float *params,
+                          float *loss_out, float *grad_out);
+
+/*
  * walkers_theta_noalloc -- walkers_theta for callers that may not allocate
  * device memory while they run: code that owns a fixed memory budget (an
  * allocator that hands out one arena up front, a job that must not grow its

@@ -106,6 +106,7 @@ struct PairTable {
     long rows = 0;                     // sum of K over pairs
     std::vector<int> i, j, K;          // host copies
     std::vector<long> off;             // first packed row of each pair
+    std::vector<double> sig;           // per pair: s_1, s_2, sum s^2 of Y^[ij]
     DevBuf d_i, d_j, d_K, d_off;       // device copies (int, int, int, long)
     DevBuf d_U, d_V;                   // FP64: rows x M (row k of Ubar^T, row k of Vbar)
     // mixed-precision operands (built lazily for FP16X3 / BF16X3)
@@ -118,7 +119,7 @@ struct PairTable {
         for (auto& s : sU) s.release();
         for (auto& s : sV) s.release();
         d_p.release(); d_q.release(); d_e0.release();
-        npairs = 0; rows = 0; i.clear(); j.clear(); K.clear(); off.clear();
+        npairs = 0; rows = 0; i.clear(); j.clear(); K.clear(); off.clear(); sig.clear();
     }
 };
 
@@ -167,11 +168,20 @@ struct MixedOps {
     DevBuf e0;                 // per pair: trial value p . q (double)
     double EK0 = 0.0;          // 1/2 sum_sigma mult sum_n wgt_n e0_n
     CUtensorMap mapU_hi, mapU_lo, mapV_hi, mapV_lo;
+    // host copies of the unscreened tile list, and the screened list
+    std::vector<int4> h_tiles;
+    std::vector<int> h_pt0, h_npt, h_order;
+    std::vector<double> h_pw, h_e0;
+    DevBuf s_pt, s_pt0, s_npt, s_pw;
+    int s_n_pt = 0, screen_built = -1;
+    double s_EK0 = 0.0;
     void release() {
         for (DevBuf* b : {&L_hi, &L_lo, &L_inv, &J0, &U_hi, &U_lo, &V_hi, &V_lo, &row_c, &pt,
-                          &pair_pt0, &pair_npt, &pair_w, &e0})
+                          &pair_pt0, &pair_npt, &pair_w, &e0, &s_pt, &s_pt0, &s_npt, &s_pw})
             b->release();
         coul_ready = lo_ready = false;
+        screen_built = -1;
+        h_tiles.clear(); h_pt0.clear(); h_npt.clear(); h_order.clear(); h_pw.clear(); h_e0.clear();
         n_pt = n_pairs = 0;
         R = 0;
     }
@@ -203,6 +213,17 @@ struct loaf_ctx {
     loaf::SpinData sp[2];
     std::vector<double> canonical[2];  // trial orbitals as loaded (host)
     loaf::MixedOps mix[2];             // split-precision operands: [0] FP16, [1] BF16
+
+    // learned pair screen
+    std::vector<double> features;      // 8 descriptors per pair (spins concatenated)
+    std::vector<unsigned char> keep;   // 1 = evaluate the pair; empty = no screen
+    int screen_version = 0;            // bumped whenever keep changes
+    std::vector<float> mlp_params;     // trained network (FP32 master copy)
+    std::vector<double> mlp_target;    // training targets (log10 max |e_ij|)
+    std::vector<double> mlp_pred;      // predicted log10 |e_ij| of every pair
+    loaf::DevBuf d_keep;               // device copy of keep
+    int d_keep_version = -1;
+    double feat_mu[8] = {0}, feat_sd[8] = {1, 1, 1, 1, 1, 1, 1, 1}, tgt_mu = 0.0, tgt_sd = 1.0;
 
     // workspace for walkers_energy (grown to the largest W seen)
     int ws_W = 0;

@@ -287,11 +287,13 @@ pair_exchange_fp64_kernel(int M, int W, int ntot, int col0, const int* __restric
 // E_K[w] = 1/2 sum_sigma mult_sigma sum_n wgt_n e[n][w], wgt = 1 (i == j) or 2
 __global__ void pair_reduce_kernel(int npairs, int W, const int* __restrict__ pi,
                                    const int* __restrict__ pj, const double2* __restrict__ e,
-                                   double scale, double2* __restrict__ out, int accumulate) {
+                                   const unsigned char* __restrict__ keep, double scale,
+                                   double2* __restrict__ out, int accumulate) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= W) return;
     double2 s = make_double2(0.0, 0.0);
     for (int n = 0; n < npairs; ++n) {
+        if (keep && !keep[n]) continue;  // pair dropped by the screen
         const double wg = pi[n] == pj[n] ? 1.0 : 2.0;
         s = cadd(s, cscale(e[(size_t)n * W + w], wg));
     }
@@ -352,6 +354,13 @@ void run_energy_fp64_full(loaf_ctx* c, int W, const double2* theta, double2* ek_
 
 void run_energy_fp64_lo(loaf_ctx* c, int W, const double2* theta, double2* ek_out,
                         double2* e_pairs) {
+    if (!c->keep.empty() && c->d_keep_version != c->screen_version) {
+        c->d_keep.ensure(c->keep.size());
+        LOAF_CUDA(cudaMemcpyAsync(c->d_keep.ptr, c->keep.data(), c->keep.size(),
+                                  cudaMemcpyHostToDevice, c->stream));
+        LOAF_CUDA(cudaStreamSynchronize(c->stream));
+        c->d_keep_version = c->screen_version;
+    }
     // e_pairs: [total pairs][W]; spin blocks consecutive
     long base = 0;
     for (int s = 0; s < c->nspin; ++s) {
@@ -368,8 +377,10 @@ void run_energy_fp64_lo(loaf_ctx* c, int W, const double2* theta, double2* ek_ou
             e_pairs + base * W);
         LOAF_LAUNCH_CHECK();
         if (ek_out) {
+            const unsigned char* keep =
+                c->keep.empty() ? nullptr : c->d_keep.as<unsigned char>() + base;
             pair_reduce_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
-                pt.npairs, W, pt.d_i.as<int>(), pt.d_j.as<int>(), e_pairs + base * W,
+                pt.npairs, W, pt.d_i.as<int>(), pt.d_j.as<int>(), e_pairs + base * W, keep,
                 0.5 * sd.mult, ek_out, s > 0);
             LOAF_LAUNCH_CHECK();
         }

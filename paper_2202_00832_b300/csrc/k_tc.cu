@@ -919,6 +919,7 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
         });
         for (int n : order) {
             const int gpair = pair_base + n;
+            mx.h_order.push_back(gpair);
             pt0[gpair] = (int)tiles.size();
             int cnt = 0;
             for (int k0 = 0; k0 < pt.K[n]; k0 += kBM) {
@@ -955,11 +956,51 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     double ek0 = 0.0;
     for (int n = 0; n < npairs; ++n) ek0 += pw[n] * e0[n];
     mx.EK0 = ek0;
+    mx.h_tiles = tiles;
+    mx.h_pt0 = pt0;
+    mx.h_npt = npt;
+    mx.h_pw = pw;
+    mx.h_e0 = e0;
+    mx.screen_built = -1;
     map_2d(&mx.mapU_hi, mx.U_hi.ptr, mx.r_pad, Rb, mx.r_pad, kBK, kBM);
     map_2d(&mx.mapU_lo, mx.U_lo.ptr, mx.r_pad, Rb, mx.r_pad, kBK, kBM);
     map_2d(&mx.mapV_hi, mx.V_hi.ptr, mx.r_pad, Rb, mx.r_pad, kBK, kBM);
     map_2d(&mx.mapV_lo, mx.V_lo.ptr, mx.r_pad, Rb, mx.r_pad, kBK, kBM);
     mx.lo_ready = true;
+}
+
+// Tile list restricted to the pairs the screen keeps (same order as the full
+// list); a dropped pair loses both its walker part and its trial part e0.
+void ensure_screened_tiles(loaf_ctx* c, MixedOps& mx) {
+    if (mx.screen_built == c->screen_version) return;
+    const int npairs = mx.n_pairs;
+    std::vector<int4> tiles;
+    std::vector<int> pt0(npairs, 0), npt(npairs, 0);
+    std::vector<double> pw(npairs, 0.0);
+    double ek0 = 0.0;
+    for (int g : mx.h_order) {
+        const bool k = c->keep.empty() || c->keep[g];
+        pt0[g] = (int)tiles.size();
+        if (!k) continue;
+        for (int t = 0; t < mx.h_npt[g]; ++t) tiles.push_back(mx.h_tiles[mx.h_pt0[g] + t]);
+        npt[g] = mx.h_npt[g];
+        pw[g] = mx.h_pw[g];
+    }
+    for (int g = 0; g < npairs; ++g) ek0 += pw[g] * mx.h_e0[g];  // same order as the full list
+    mx.s_n_pt = (int)tiles.size();
+    mx.s_pt.ensure(std::max<size_t>(tiles.size(), 1) * sizeof(int4));
+    mx.s_pt0.ensure(std::max(npairs, 1) * sizeof(int));
+    mx.s_npt.ensure(std::max(npairs, 1) * sizeof(int));
+    mx.s_pw.ensure(std::max(npairs, 1) * sizeof(double));
+    if (!tiles.empty())
+        LOAF_CUDA(cudaMemcpyAsync(mx.s_pt.ptr, tiles.data(), tiles.size() * sizeof(int4),
+                                  cudaMemcpyHostToDevice, c->stream));
+    LOAF_CUDA(cudaMemcpyAsync(mx.s_pt0.ptr, pt0.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    LOAF_CUDA(cudaMemcpyAsync(mx.s_npt.ptr, npt.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    LOAF_CUDA(cudaMemcpyAsync(mx.s_pw.ptr, pw.data(), npairs * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    LOAF_CUDA(cudaStreamSynchronize(c->stream));
+    mx.s_EK0 = ek0;
+    mx.screen_built = c->screen_version;
 }
 
 constexpr size_t kCoulSmem =
@@ -1043,24 +1084,33 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
     if (mode == LOAF_MODE_LO) {
         // ---- LO pair exchange on the tensor cores ----
         double2* ek = e_out ? e_out + 2 * W : nullptr;
-        if (mx.n_pt > 0) {
+        // energies honour the pair screen; pair values are always for every pair
+        const bool screened = !c->keep.empty() && e_pairs == nullptr;
+        if (screened) ensure_screened_tiles(c, mx);
+        const int n_pt = screened ? mx.s_n_pt : mx.n_pt;
+        const int4* tile_list = screened ? mx.s_pt.as<int4>() : mx.pt.as<int4>();
+        const int* list_pt0 = screened ? mx.s_pt0.as<int>() : mx.pair_pt0.as<int>();
+        const int* list_npt = screened ? mx.s_npt.as<int>() : mx.pair_npt.as<int>();
+        const double* list_pw = screened ? mx.s_pw.as<double>() : mx.pair_w.as<double>();
+        const double list_ek0 = screened ? mx.s_EK0 : mx.EK0;
+        if (n_pt > 0) {
             CUtensorMap mDhi, mDlo;
             map_delta_3d(&mDhi, c->w_dhi.ptr, mx.r_pad, c->ntot, 2L * W);
             map_delta_3d(&mDlo, c->w_dlo.ptr, mx.r_pad, c->ntot, 2L * W);
             LoParams P;
-            P.pt = mx.pt.as<int4>();
+            P.pt = tile_list;
             P.rowc = mx.row_c.as<float4>();
             P.inv_t = inv_t;
-            P.n_pt = mx.n_pt;
+            P.n_pt = n_pt;
             P.n_wt = n_wt;
             P.W = W;
             P.ldp = Wpad;
             P.nk = ceil_div(mx.r_pad, kBK);
             P.idesc = idesc;
             P.err = err;
-            c->w_lopart.ensure((size_t)mx.n_pt * Wpad * sizeof(double2));
+            c->w_lopart.ensure((size_t)n_pt * Wpad * sizeof(double2));
             P.part = c->w_lopart.as<double2>();
-            const int units = mx.n_pt * n_wt;
+            const int units = n_pt * n_wt;
             LOAF_CUDA(cudaFuncSetAttribute(lo_exchange_tc_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoSmem));
             StageScope lsc(c, "lo_exchange_tc", 1);
@@ -1071,8 +1121,8 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         c->w_lopart.ensure(16);
         StageScope lrs(c, "lo_reduce", 1);
         lo_tc_reduce_kernel<<<ceil_div(W, 32), 256, 0, c->stream>>>(
-            mx.n_pairs, W, Wpad, mx.pair_pt0.as<int>(), mx.pair_npt.as<int>(), mx.pair_w.as<double>(),
-            mx.e0.as<double>(), mx.EK0, c->w_lopart.as<double2>(), ek, e_pairs);
+            mx.n_pairs, W, Wpad, list_pt0, list_npt, list_pw, mx.e0.as<double>(), list_ek0,
+            c->w_lopart.as<double2>(), ek, e_pairs);
         LOAF_LAUNCH_CHECK();
     } else if (e_out) {
         // full mode: Coulomb on the tensor cores, exchange in FP64

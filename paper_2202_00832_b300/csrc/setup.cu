@@ -191,7 +191,7 @@ __global__ void copy_block_kernel(int M, const double* __restrict__ Y, long ldy,
 __global__ void extract_factors_kernel(int M, int jw, double thr, const double* __restrict__ Z,
                                        const double* __restrict__ lam, const int* __restrict__ slot,
                                        double* __restrict__ Uslots, double* __restrict__ Vslots,
-                                       int* __restrict__ Kout) {
+                                       int* __restrict__ Kout, double* __restrict__ sig3) {
     const int b = blockIdx.x;
     const long n = jw ? 2L * M : (long)M;
     const double* zb = Z + (size_t)b * n * n;
@@ -207,6 +207,16 @@ __global__ void extract_factors_kernel(int M, int jw, double thr, const double* 
         }
         sK = k;
         Kout[slot[b]] = k;
+        // pair descriptors: the two largest singular values and sum s^2
+        double s1 = 0.0, s2 = 0.0, ss = 0.0;
+        for (int t = 0; t < M; ++t) {
+            const double sv = jw ? fmax(lb[n - 1 - t], 0.0) : fabs(lb[t]);
+            ss += sv * sv;
+            if (sv > s1) { s2 = s1; s1 = sv; } else if (sv > s2) { s2 = sv; }
+        }
+        sig3[3 * slot[b]] = s1;
+        sig3[3 * slot[b] + 1] = s2;
+        sig3[3 * slot[b] + 2] = ss;
     }
     __syncthreads();
     const int K = sK;
@@ -273,7 +283,7 @@ struct EigBatch {
 }  // namespace
 
 static void run_eig_batch(loaf_ctx* c, cusolverDnParams_t prm, EigBatch& eb, int M, bool jw,
-                          double thr, double* Uslots, double* Vslots, int* dK) {
+                          double thr, double* Uslots, double* Vslots, int* dK, double* dSig) {
     const int cnt = (int)eb.pending_slots.size();
     if (cnt == 0) return;
     LOAF_CUDA(cudaMemcpyAsync(eb.slots.ptr, eb.pending_slots.data(), cnt * sizeof(int),
@@ -285,7 +295,7 @@ static void run_eig_batch(loaf_ctx* c, cusolverDnParams_t prm, EigBatch& eb, int
     const size_t smem = jw ? 0 : (size_t)M * sizeof(int);
     extract_factors_kernel<<<cnt, 256, smem, c->stream>>>(M, jw ? 1 : 0, thr, eb.A.as<double>(),
                                                          eb.lam.as<double>(), eb.slots.as<int>(),
-                                                         Uslots, Vslots, dK);
+                                                         Uslots, Vslots, dK, dSig);
     LOAF_LAUNCH_CHECK();
     // the host-side slot list is reused by the next batch: wait for the copy
     LOAF_CUDA(cudaStreamSynchronize(c->stream));
@@ -316,7 +326,8 @@ static void compress_spin(loaf_ctx* c, SpinData& s, double thr) {
     for (int i = 0; i < N; ++i)
         for (int j = i; j < N; ++j) { pt.i.push_back(i); pt.j.push_back(j); }
 
-    DevBuf Uslots, Vslots, dK, G;
+    DevBuf Uslots, Vslots, dK, G, dSig;
+    dSig.ensure((size_t)npairs * 3 * sizeof(double));
     Uslots.ensure((size_t)npairs * M * M * sizeof(double));
     Vslots.ensure((size_t)npairs * M * M * sizeof(double));
     dK.ensure((size_t)npairs * sizeof(int));
@@ -351,7 +362,7 @@ static void compress_spin(loaf_ctx* c, SpinData& s, double thr) {
                     diag_b.pending_slots.push_back(slot);
                     if ((int)diag_b.pending_slots.size() == diag_b.cap)
                         run_eig_batch(c, prm, diag_b, M, false, thr, Uslots.as<double>(),
-                                      Vslots.as<double>(), dK.as<int>());
+                                      Vslots.as<double>(), dK.as<int>(), dSig.as<double>());
                 } else {
                     double* H = off_b.A.as<double>() +
                                 (size_t)off_b.pending_slots.size() * 4 * M * M;
@@ -361,14 +372,14 @@ static void compress_spin(loaf_ctx* c, SpinData& s, double thr) {
                     off_b.pending_slots.push_back(slot);
                     if ((int)off_b.pending_slots.size() == off_b.cap)
                         run_eig_batch(c, prm, off_b, M, true, thr, Uslots.as<double>(),
-                                      Vslots.as<double>(), dK.as<int>());
+                                      Vslots.as<double>(), dK.as<int>(), dSig.as<double>());
                 }
             }
             // G is overwritten by the next row: flush what still points into it
             run_eig_batch(c, prm, diag_b, M, false, thr, Uslots.as<double>(), Vslots.as<double>(),
-                          dK.as<int>());
+                          dK.as<int>(), dSig.as<double>());
             run_eig_batch(c, prm, off_b, M, true, thr, Uslots.as<double>(), Vslots.as<double>(),
-                          dK.as<int>());
+                          dK.as<int>(), dSig.as<double>());
         }
     } catch (...) {
         cusolverDnDestroyParams(prm);
@@ -377,8 +388,11 @@ static void compress_spin(loaf_ctx* c, SpinData& s, double thr) {
     cusolverDnDestroyParams(prm);
 
     pt.K.resize(npairs);
+    pt.sig.resize((size_t)npairs * 3);
     LOAF_CUDA(cudaMemcpyAsync(pt.K.data(), dK.ptr, npairs * sizeof(int), cudaMemcpyDeviceToHost,
                               c->stream));
+    LOAF_CUDA(cudaMemcpyAsync(pt.sig.data(), dSig.ptr, pt.sig.size() * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
     LOAF_CUDA(cudaStreamSynchronize(c->stream));
     pt.off.resize(npairs);
     long rows = 0;
@@ -399,6 +413,51 @@ static void compress_spin(loaf_ctx* c, SpinData& s, double thr) {
                                                        pt.d_U.as<double>(), pt.d_V.as<double>());
     LOAF_LAUNCH_CHECK();
     LOAF_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+// Eight walker-independent descriptors per pair [ij] for the pair screen:
+// centroid distance d, 1/(1+d), s_i + s_j, |s_i - s_j|, log s_1, log s_2,
+// M_SVD/M and log |Y^[ij]|_F, with centroid c_i = <i|r_d|i> and spread
+// s_i = sqrt(sum_d |r_d i|^2 - c_id^2) of the (localized) trial orbitals.
+static void pair_features_host(loaf_ctx* c, const double* r_ops, int n_ops) {
+    const int M = c->M;
+    c->features.clear();
+    auto lg = [](double v) { return std::log(std::max(v, 1e-300)); };
+    for (int s = 0; s < c->nspin; ++s) {
+        const SpinData& sd = c->sp[s];
+        const int N = sd.N;
+        std::vector<double> cen((size_t)N * 3, 0.0), sq((size_t)N * 3, 0.0), spread(N, 0.0);
+        for (int d = 0; d < std::min(n_ops, 3) && r_ops; ++d) {
+            const double* r = r_ops + (size_t)d * M * M;
+            for (int i = 0; i < N; ++i) {
+                double cc = 0.0, nn = 0.0;
+                for (int p = 0; p < M; ++p) {
+                    double rc = 0.0;
+                    for (int q = 0; q < M; ++q) rc += r[(size_t)p * M + q] * sd.h_trial[(size_t)q * N + i];
+                    cc += sd.h_trial[(size_t)p * N + i] * rc;
+                    nn += rc * rc;
+                }
+                cen[i * 3 + d] = cc;
+                sq[i * 3 + d] = nn;
+            }
+        }
+        for (int i = 0; i < N; ++i) {
+            double v = 0.0;
+            for (int d = 0; d < 3; ++d) v += sq[i * 3 + d] - cen[i * 3 + d] * cen[i * 3 + d];
+            spread[i] = std::sqrt(std::max(v, 0.0));
+        }
+        const PairTable& pt = sd.pairs;
+        for (int n = 0; n < pt.npairs; ++n) {
+            const int i = pt.i[n], j = pt.j[n];
+            double dd = 0.0;
+            for (int d = 0; d < 3; ++d) dd += (cen[i * 3 + d] - cen[j * 3 + d]) * (cen[i * 3 + d] - cen[j * 3 + d]);
+            dd = std::sqrt(dd);
+            const double f[8] = {dd, 1.0 / (1.0 + dd), spread[i] + spread[j],
+                                 std::fabs(spread[i] - spread[j]), lg(pt.sig[3 * n]),
+                                 lg(pt.sig[3 * n + 1]), (double)pt.K[n] / M, 0.5 * lg(pt.sig[3 * n + 2])};
+            c->features.insert(c->features.end(), f, f + 8);
+        }
+    }
 }
 
 void setup_compress(loaf_ctx* c, double t_svd, const double* r_ops, int n_ops, int localize,
@@ -423,6 +482,9 @@ void setup_compress(loaf_ctx* c, double t_svd, const double* r_ops, int n_ops, i
     c->localized = localize != 0;
     c->t_svd = t_svd;
     c->compressed = true;
+    pair_features_host(c, r_ops, n_ops);
+    c->keep.clear();
+    c->screen_version++;
     long tot = 0, cnt = 0;
     int k = 0;
     for (int s = 0; s < c->nspin; ++s)

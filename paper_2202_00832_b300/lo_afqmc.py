@@ -44,6 +44,11 @@ SIGNATURES = [
     ("loaf_num_pairs", _I, [_P]),
     ("lo_get_localized_trial", _I, [_P, _I, _P]),
     ("walkers_theta_noalloc", _I, [_P, _I, _P, _P, _P, _P]),
+    ("loaf_screen_num_params", _I, []),
+    ("pair_screen_train", _I, [_P, _I, _P, _I, ctypes.c_float, _P, _P]),
+    ("pair_screen_set", _I, [_P, _D, _P]),
+    ("pair_screen_query", _I, [_P, _P, _P, _P, _P, _P]),
+    ("mlp_loss_grad", _I, [_I, _I, _P, _P, _P, _P, _P]),
     ("loaf_profile", _I, [_P, _I]),
     ("loaf_profile_count", _I, [_P]),
     ("loaf_profile_get", _I, [_P, _I, ctypes.POINTER(ctypes.c_char_p),
@@ -266,6 +271,34 @@ class Context:
                     "walkers_theta_noalloc")
         return theta_out, logdet_out, walker_status
 
+    # -- learned pair screen ------------------------------------------------
+    def pair_screen_train(self, phi, init_params, epochs=500, lr=3e-3):
+        """Train the screen on walkers phi; returns the loss history."""
+        _check_dtype(phi, "c16")
+        init = np.ascontiguousarray(init_params, dtype=np.float32)
+        hist = np.zeros(epochs, dtype=np.float32)
+        self._check(self._lib.pair_screen_train(self._h, int(phi.shape[0]), _ptr(phi), int(epochs),
+                                                float(lr), _ptr(init), _ptr(hist)),
+                    "pair_screen_train")
+        return hist
+
+    def pair_screen_set(self, cutoff_ha: float) -> int:
+        kept = ctypes.c_int(0)
+        self._check(self._lib.pair_screen_set(self._h, float(cutoff_ha), ctypes.byref(kept)),
+                    "pair_screen_set")
+        return kept.value
+
+    def pair_screen_query(self, trained: bool = True) -> dict:
+        n = self.num_pairs
+        out = {"features": np.zeros((n, 8)), "keep": np.zeros(n, dtype=np.uint8)}
+        if trained:
+            out.update(params=np.zeros(self._lib.loaf_screen_num_params(), dtype=np.float32),
+                       pred=np.zeros(n), target=np.zeros(n))
+        self._check(self._lib.pair_screen_query(
+            self._h, _ptr(out.get("params")), _ptr(out["features"]), _ptr(out.get("pred")),
+            _ptr(out.get("target")), _ptr(out["keep"])), "pair_screen_query")
+        return out
+
     def walkers_pair_exchange(self, phi, precision="fp64", out=None):
         _check_dtype(phi, "c16")
         W = int(phi.shape[0])
@@ -275,6 +308,32 @@ class Context:
                                                     PRECISIONS.get(precision, precision),
                                                     _ptr(out)), "walkers_pair_exchange")
         return out
+
+
+def mlp_loss_grad(x, t, params, device: int = 0):
+    """(loss, gradient) of the screening network on the GPU (float32 in/out)."""
+    lib = load_library()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    g = np.zeros(lib.loaf_screen_num_params(), dtype=np.float32)
+    loss = ctypes.c_float(0.0)
+    code = lib.mlp_loss_grad(device, int(len(t)), _ptr(x), _ptr(t), _ptr(params),
+                             ctypes.byref(loss), _ptr(g))
+    if code != 0:
+        raise LoafError(code, "mlp_loss_grad", "")
+    return float(loss.value), g
+
+
+def init_screen_params(seed: int = 0) -> np.ndarray:
+    """Seeded Glorot-uniform initial weights (zero biases) for the screen."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in [(64, 8), (64, 64), (1, 64)]:
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        parts.append(rng.uniform(-lim, lim, fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
 
 
 def position_operators(mol) -> np.ndarray:
