@@ -242,7 +242,8 @@ loaf_status loaf_destroy(loaf_ctx* c) {
     for (loaf::DevBuf* b : {&c->w_phi, &c->w_theta, &c->w_z, &c->w_lu, &c->w_perm, &c->w_logdet,
                             &c->w_status, &c->w_out, &c->w_part, &c->w_part2, &c->w_dhi,
                             &c->w_dlo, &c->w_dscale, &c->w_host_stage, &c->w_cpart,
-                            &c->w_lopart, &c->w_flag, &c->d_keep})
+                            &c->w_lopart, &c->w_flag, &c->d_keep, &c->w_oz_at, &c->w_oz_bs,
+                            &c->w_oz_bt, &c->w_oz_S, &c->w_oz_int})
         b->release();
     if (c->cublas) cublasDestroy(c->cublas);
     if (c->cusolver) cusolverDnDestroy(c->cusolver);
@@ -349,7 +350,12 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
             StageScope sc(c, "h2d_walkers", 0);
             dphi = stage_walkers(c, W, phi);
         }
-        {
+        // the LO split-precision path forms Delta on the tensor cores; the FP64
+        // path and the full mode use the FP64 Theta kernel
+        const bool tc_theta = precision != LOAF_PREC_FP64 && mode == LOAF_MODE_LO;
+        if (tc_theta) {
+            run_theta_tc(c, W, dphi, precision);
+        } else {
             StageScope sc(c, "theta_fp64", c->nspin);
             stage_theta(c, W, dphi);
         }
@@ -369,7 +375,8 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
                 run_energy_fp64_lo(c, W, c->w_theta.as<double2>(), ek, c->w_part.as<double2>());
             }
         } else {
-            run_energy_mixed(c, W, mode, precision, c->w_theta.as<double2>(), e1, nullptr);
+            run_energy_mixed(c, W, mode, precision, tc_theta ? nullptr : c->w_theta.as<double2>(),
+                             e1, nullptr);
         }
         double2* de = c->w_host_stage.as<double2>();
         double2* dld = de + W;
@@ -413,12 +420,14 @@ loaf_status walkers_pair_exchange(loaf_ctx* c, int W, const void* phi, int preci
         LOAF_REQUIRE(e_pairs_out != nullptr, LOAF_ERR_ARG, "e_pairs_out is NULL");
         ensure_workspace(c, W, LOAF_MODE_LO);
         const double2* dphi = stage_walkers(c, W, phi);
-        stage_theta(c, W, dphi);
-        if (precision == LOAF_PREC_FP64)
+        if (precision == LOAF_PREC_FP64) {
+            stage_theta(c, W, dphi);
             run_energy_fp64_lo(c, W, c->w_theta.as<double2>(), nullptr, c->w_part.as<double2>());
-        else
-            run_energy_mixed(c, W, LOAF_MODE_LO, precision, c->w_theta.as<double2>(), nullptr,
+        } else {
+            run_theta_tc(c, W, dphi, precision);
+            run_energy_mixed(c, W, LOAF_MODE_LO, precision, nullptr, nullptr,
                              c->w_part.as<double2>());
+        }
         deliver(c, e_pairs_out, c->w_part.ptr, (size_t)loaf_num_pairs(c) * W * sizeof(double2));
         int timeout = 0;
         if (precision != LOAF_PREC_FP64)

@@ -135,7 +135,10 @@ struct SpinData {
     DevBuf d_J0;           // X doubles: tr(Lbar_g Phi) (trial Coulomb vector)
     double E1_0 = 0.0;     // sum_ir hbar_ir Phi_ri
     PairTable pairs;
+    DevBuf oz_trialT, oz_rowexp;   // digit slices of Phi_T^T (tensor-core Theta)
+    int oz_trial_version = -1;
     void release() {
+        oz_trialT.release(); oz_rowexp.release(); oz_trial_version = -1;
         d_trial.release(); d_Lbar.release(); d_hbar.release();
         for (auto& s : sLbar) s.release();
         d_J0.release();
@@ -228,7 +231,9 @@ struct loaf_ctx {
     // workspace for walkers_energy (grown to the largest W seen)
     int ws_W = 0;
     loaf::DevBuf w_phi, w_theta, w_z, w_lu, w_perm, w_logdet, w_status, w_out, w_part,
-        w_part2, w_dhi, w_dlo, w_dscale, w_host_stage, w_cpart, w_lopart, w_flag;
+        w_part2, w_dhi, w_dlo, w_dscale, w_host_stage, w_cpart, w_lopart, w_flag, w_oz_at, w_oz_bs,
+        w_oz_bt, w_oz_S, w_oz_int;
+    int trial_version = 0;  // bumped whenever a trial (canonical or localized) is loaded
 
     // per-stage CUDA-event timers (loaf_profile); stage kernels are bracketed
     // by events on the context stream while enabled
@@ -289,6 +294,7 @@ void run_energy_fp64_lo(loaf_ctx* c, int W, const double2* theta, double2* e_out
 void run_coulomb_fp64(loaf_ctx* c, int W, const double2* theta, double2* e_part);
 void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2* theta,
                       double2* e_out, double2* e_pairs);
+void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision);
 void setup_load(loaf_ctx* c, int M, int X, const double* h, const double* L, int na, int nb,
                 const double* ta, const double* tb, double e0, int on_device);
 void setup_compress(loaf_ctx* c, double t_svd, const double* r_ops, int n_ops, int localize,

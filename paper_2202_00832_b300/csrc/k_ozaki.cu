@@ -1,0 +1,674 @@
+// Theta on the tensor cores with exact integer slices (split-precision path).
+//
+// The overlap S = Phi_T^T phi and Theta = phi S^-1 (eq. Q) need close to FP64
+// accuracy: Delta = Theta - Phi_T is a small difference of O(1) numbers.  B300
+// runs FP64 at ~1 TFLOP/s, so the two M N^2-sized products run on the FP16
+// tensor cores instead, error-free:
+//   every operand row (or column) is scaled by a power of two into [-1/4, 1/4]
+//   and written as six balanced base-128 digits d_s in [-64, 63]
+//   (x = sum_s d_s 2^-7s, 42 bits); digits are exact in FP16;
+//   a digit product is at most 2^12 and the sums below stay under 2^24, so the
+//   FP32 tensor-core accumulation is exact;
+//   products with s + t = D (D = 2..7, 21 products per k-step) accumulate into
+//   one of six TMEM accumulators and are combined exactly in int64:
+//   value = 2^(e_row + e_col - 49) * sum_D acc_D * 2^(7 (7 - D)).
+// Omitting s + t >= 8 leaves an error near 2^-49 of the operands' scale.
+// Only the O(N^3) part -- Gauss-Jordan inversion of S with partial pivoting
+// and the log-determinant -- stays FP64 (one CTA per walker and spin).
+//
+// Stages per spin: slice phi (two layouts) -> S GEMM (A = Phi_T^T slices,
+// B = phi slices) -> Gauss-Jordan (Z = S^-1, log det, Z slices) -> Delta scale
+// -> Theta GEMM (A = phi slices, B = Z slices) whose epilogue writes
+// Delta = Theta - Phi_T as the 16-bit hi/lo planes the Coulomb and LO kernels read.
+#include "common.cuh"
+#include "tc_ptx.cuh"
+
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+
+namespace loaf {
+
+namespace {
+
+constexpr int kNS = 6;          // digit slices
+constexpr int kND = 6;          // accumulated diagonals D = s + t = 2..7
+constexpr int kOBK = 32;        // K per stage (64-byte rows, SWIZZLE_64B)
+constexpr int kOBM = 128;
+constexpr int kOBN = 80;
+constexpr int kOStages = 2;
+constexpr uint32_t kOTileA = kOBM * 64;              // 8 KB
+constexpr uint32_t kOTileB = kOBN * 64;              // 5 KB
+constexpr uint32_t kOStage = kNS * (kOTileA + kOTileB);  // 78 KB
+constexpr size_t kOSmem = kOStages * kOStage + 1024;
+
+PFN_cuTensorMapEncodeTiled_v12000 encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        LOAF_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                   cudaEnableDefault, &q));
+        LOAF_REQUIRE(p && q == cudaDriverEntryPointSuccess, LOAF_ERR_CUDA,
+                     "cuTensorMapEncodeTiled is unavailable");
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 16-bit slices [slice][batch][rows][ld]: x = K (extent k), y = row, z = batch, w = slice
+void map_slices(CUtensorMap* m, const void* base, uint64_t k, uint64_t ld, uint64_t rows,
+                uint64_t batch, uint32_t box_rows) {
+    cuuint64_t dims[4] = {k, rows, batch, (cuuint64_t)kNS};
+    cuuint64_t strides[3] = {ld * 2, ld * rows * 2, ld * rows * batch * 2};
+    cuuint32_t box[4] = {(cuuint32_t)kOBK, box_rows, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = encode()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void*>(base), dims,
+                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    LOAF_REQUIRE(r == CUDA_SUCCESS, LOAF_ERR_CUDA, "cuTensorMapEncodeTiled (slices) failed");
+}
+
+// smallest E with max|v| <= 2^(E-2)  (0 for an all-zero set)
+__device__ inline int slice_exponent(double maxabs) {
+    if (!(maxabs > 0.0)) return 0;
+    int e;
+    frexp(maxabs, &e);  // maxabs < 2^e
+    return e + 2;
+}
+
+// six balanced base-128 digits of x = v 2^-E (|x| <= 1/4), most significant first
+__device__ inline void digits6(double v, int E, int (&d)[kNS]) {
+    long long X = __double2ll_rn(ldexp(v, 42 - E));
+#pragma unroll
+    for (int s = kNS - 1; s >= 0; --s) {
+        const int r = (int)((X + 64) & 127) - 64;
+        d[s] = r;
+        X = (X - r) >> 7;
+    }
+}
+
+__device__ inline uint16_t h16(int d) { return __half_as_ushort(__int2half_rn(d)); }
+
+__device__ inline double block_max_d(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double m = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, red[k]);
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// slicing
+// ---------------------------------------------------------------------------
+
+// Phi_T^T rows i (per-row exponent), K = basis p: A_S[s][i][p_pad]
+__global__ void slice_trial_kernel(int M, int N, int p_pad, const double* __restrict__ trial,
+                                   uint16_t* __restrict__ out, int* __restrict__ row_exp) {
+    __shared__ double red[32];
+    const int i = blockIdx.x;
+    double m = 0.0;
+    for (int p = threadIdx.x; p < M; p += blockDim.x) m = fmax(m, fabs(trial[(size_t)p * N + i]));
+    const int E = slice_exponent(block_max_d(m, red));
+    for (int p = threadIdx.x; p < p_pad; p += blockDim.x) {
+        int d[kNS];
+        digits6(p < M ? trial[(size_t)p * N + i] : 0.0, E, d);
+#pragma unroll
+        for (int s = 0; s < kNS; ++s) out[((size_t)s * N + i) * p_pad + p] = h16(d[s]);
+    }
+    if (threadIdx.x == 0) row_exp[i] = E;
+}
+
+// One walker's spin block of phi (M x N complex) -> digits in two layouts:
+//   At[s][w][p][kpad]        K = 2j + ri  (A operand of the Theta GEMM)
+//   Bs[s][(2w + ri) N + j][p_pad]          (B operand of the S GEMM)
+// with one exponent per walker and spin.  64 basis rows per step through
+// shared memory (transpose for Bs).
+constexpr int kSliceRows = 64;
+__global__ void __launch_bounds__(256)
+slice_phi_kernel(int M, int N, int ntot, int col0, int p_pad, int kpad, int W,
+                 const double2* __restrict__ phi, uint16_t* __restrict__ At, uint16_t* __restrict__ Bs,
+                 int* __restrict__ wexp) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    signed char* dg = reinterpret_cast<signed char*>(sm);  // [kNS][2N][kSliceRows]
+    __shared__ double red[32];
+    const int w = blockIdx.x;
+    const double2* pw = phi + (size_t)w * M * ntot + col0;
+    double m = 0.0;
+    for (long e = threadIdx.x; e < (long)M * N; e += blockDim.x) {
+        const double2 v = pw[(e / N) * ntot + e % N];
+        m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    }
+    const int E = slice_exponent(block_max_d(m, red));
+    if (threadIdx.x == 0) wexp[w] = E;
+    const int twoN = 2 * N;
+    for (int p0 = 0; p0 < p_pad; p0 += kSliceRows) {
+        const int np = min(kSliceRows, p_pad - p0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < np * twoN; e += blockDim.x) {
+            const int pp = e / twoN, K = e % twoN;
+            const int p = p0 + pp, j = K >> 1, ri = K & 1;
+            double v = 0.0;
+            if (p < M) {
+                const double2 z = pw[(size_t)p * ntot + j];
+                v = ri ? z.y : z.x;
+            }
+            int d[kNS];
+            digits6(v, E, d);
+#pragma unroll
+            for (int s = 0; s < kNS; ++s) {
+                dg[((size_t)s * twoN + (ri * N + j)) * kSliceRows + pp] = (signed char)d[s];
+                if (p < M) At[(((size_t)s * W + w) * M + p) * kpad + K] = h16(d[s]);
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kNS * twoN * np; e += blockDim.x) {
+            const int s = e / (twoN * np), rem = e % (twoN * np);
+            const int col = rem / np, pp = rem % np;  // col = ri * N + j
+            const int ri = col / N, j = col % N;
+            Bs[((size_t)s * 2 * N * W + (size_t)(2 * w + ri) * N + j) * p_pad + p0 + pp] =
+                h16(dg[((size_t)s * twoN + col) * kSliceRows + pp]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the slice GEMM (tcgen05, 21 products into six diagonal accumulators)
+// ---------------------------------------------------------------------------
+struct OzParams {
+    int n_rt, n_ct, n_b, nk, a_batched;
+    uint32_t idesc;
+    int* err;
+    int mode;  // 0: overlap S, 1: Theta -> Delta planes
+    int M, N, ntot, col0, r_pad, W, rows_valid, cols_valid;
+    const int* row_exp;   // mode 0: exponent of each Phi_T^T row
+    const int* wexp;      // exponent of each walker's phi block
+    const int* col_exp;   // mode 1: [W][N] exponent of each column of S^-1
+    double* S_out;        // mode 0: [W][N][N] complex as (re, im) doubles
+    const double* trial;  // mode 1: M x N
+    const double* tscale; // mode 1: per-walker Delta scale
+    uint16_t* dhi;
+    uint16_t* dlo;
+    int bf16;
+};
+
+struct OzShared {
+    uint64_t full[kOStages];
+    uint64_t empty[kOStages];
+    uint64_t tmem_full;
+    uint64_t tmem_empty;
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ inline uint8_t* align1k(uint8_t* p) {
+    return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+__device__ inline void store_delta(const OzParams& P, int w, int r, int cc, double theta) {
+    // cc = 2k + ro of this spin; Delta = Theta - Phi_T (real part only)
+    const int k = cc >> 1, ro = cc & 1;
+    const double delta = ro ? theta : theta - P.trial[(size_t)r * P.N + k];
+    const float f = (float)(delta * P.tscale[w]);
+    uint16_t h, l;
+    if (P.bf16) {
+        const __nv_bfloat16 a = __float2bfloat16(f);
+        h = __bfloat16_as_ushort(a);
+        l = __bfloat16_as_ushort(__float2bfloat16(f - __bfloat162float(a)));
+    } else {
+        const __half a = __float2half(f);
+        h = __half_as_ushort(a);
+        l = __half_as_ushort(__float2half(f - __half2float(a)));
+    }
+    const size_t o = ((size_t)(2 * w + ro) * P.ntot + P.col0 + k) * P.r_pad + r;
+    P.dhi[o] = h;
+    P.dlo[o] = l;
+}
+
+__global__ void __launch_bounds__(192, 1)
+ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+                  OzParams P) {
+    extern __shared__ uint8_t dyn[];
+    __shared__ OzShared sh;
+    uint8_t* base = align1k(dyn);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_units = P.n_b * P.n_rt * P.n_ct;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kOStages; ++s) { tc::mbar_init(&sh.full[s], 1); tc::mbar_init(&sh.empty[s], 1); }
+        tc::mbar_init(&sh.tmem_full, 1);
+        tc::mbar_init(&sh.tmem_empty, 4);
+        tc::mbar_init(&sh.drain, 1);
+        sh.abort = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&sh.tmem_base, 512);
+        tc::tmem_relinquish();
+    }
+    if (threadIdx.x == 32) { tc::tma_prefetch(&mA); tc::tma_prefetch(&mB); }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = sh.tmem_base;
+    volatile int* abort = &sh.abort;
+
+    if (warp == 0 && lane == 0) {
+        int s = 0;
+        uint32_t ph = 0, filled = 0, last_par = 0;
+        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
+            const int ct = u % P.n_ct, rt = (u / P.n_ct) % P.n_rt, b = u / (P.n_ct * P.n_rt);
+            for (int kc = 0; kc < P.nk; ++kc) {
+                if (!tc::mbar_wait(&sh.empty[s], ph ^ 1, abort)) break;
+                uint8_t* st = base + s * kOStage;
+                tc::mbar_arrive_expect_tx(&sh.full[s], kOStage);
+                for (int q = 0; q < kNS; ++q) {
+                    tc::tma_load_4d(st + q * kOTileA, &mA, &sh.full[s], kc * kOBK, rt * kOBM,
+                                    P.a_batched ? b : 0, q);
+                    tc::tma_load_4d(st + kNS * kOTileA + q * kOTileB, &mB, &sh.full[s], kc * kOBK,
+                                    ct * kOBN, b, q);
+                }
+                filled |= 1u << s;
+                last_par = (last_par & ~(1u << s)) | (ph << s);
+                if (++s == kOStages) { s = 0; ph ^= 1; }
+            }
+        }
+        if (*abort) {
+            for (int q = 0; q < kOStages; ++q)
+                if (filled & (1u << q)) {
+                    volatile int never = 0;
+                    tc::mbar_wait(&sh.full[q], (last_par >> q) & 1, &never);
+                }
+        }
+    } else if (warp == 1 && lane == 0) {
+        int s = 0;
+        uint32_t ph = 0, tph = 0;
+        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
+            if (!tc::mbar_wait(&sh.tmem_empty, tph ^ 1, abort)) break;
+            tc::tc_fence_after();
+            bool ok = true;
+            uint32_t started = 0;  // bit D-2: diagonal D already has a product this unit
+            for (int kc = 0; kc < P.nk; ++kc) {
+                if (!tc::mbar_wait(&sh.full[s], ph, abort)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint32_t st = tc::smem_u32(base + s * kOStage);
+#pragma unroll
+                for (int kk = 0; kk < kOBK / 16; ++kk) {
+#pragma unroll
+                    for (int a = 0; a < kNS; ++a)
+#pragma unroll
+                        for (int bq = 0; bq < kNS; ++bq) {
+                            const int D = a + bq;  // (s-1) + (t-1): diagonal index 0..5 kept
+                            if (D >= kND) continue;
+                            const uint64_t da = tc::smem_desc(st + a * kOTileA + kk * 32, 64);
+                            const uint64_t db = tc::smem_desc(st + kNS * kOTileA + bq * kOTileB + kk * 32, 64);
+                            const uint32_t acc = (started >> D) & 1u;
+                            tc::mma_f16(tmem + D * kOBN, da, db, P.idesc, acc);
+                            started |= 1u << D;
+                        }
+                }
+                tc::mma_commit(&sh.empty[s]);
+                if (++s == kOStages) { s = 0; ph ^= 1; }
+            }
+            if (!ok) break;
+            tc::mma_commit(&sh.tmem_full);
+            tph ^= 1;
+        }
+        tc::mma_commit(&sh.drain);
+        volatile int never = 0;
+        tc::mbar_wait(&sh.drain, 0, &never);
+    } else if (warp >= 2) {
+        const int q = warp & 3;
+        uint32_t tph = 0;
+        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
+            const int ct = u % P.n_ct, rt = (u / P.n_ct) % P.n_rt, b = u / (P.n_ct * P.n_rt);
+            if (!tc::mbar_wait(&sh.tmem_full, tph, abort)) break;
+            tc::tc_fence_after();
+            const int row = rt * kOBM + q * 32 + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < kOBN; c0 += 16) {
+                float v[kND][16];
+#pragma unroll
+                for (int D = 0; D < kND; ++D)
+                    tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + D * kOBN + c0, v[D]);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    long long z = 0;
+#pragma unroll
+                    for (int D = 0; D < kND; ++D)
+                        z += (long long)__float2ll_rn(v[D][c]) * (1LL << (7 * (kND - 1 - D)));
+                    const int col = ct * kOBN + c0 + c;
+                    if (row >= P.rows_valid || col >= P.cols_valid) continue;
+                    if (P.mode == 0) {
+                        // S_w[i][j], column col = (2w + ri) N + j
+                        const int w = col / (2 * P.N), rem = col % (2 * P.N);
+                        const int ri = rem / P.N, j = rem % P.N;
+                        const double val = ldexp((double)z, P.row_exp[row] + P.wexp[w] - 49);
+                        P.S_out[(((size_t)w * P.N + row) * P.N + j) * 2 + ri] = val;
+                    } else {
+                        const int w = b, k = col >> 1;
+                        const double val = ldexp((double)z, P.wexp[w] + P.col_exp[(size_t)w * P.N + k] - 49);
+                        store_delta(P, w, row, col, val);
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&sh.tmem_empty);
+            tph ^= 1;
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (threadIdx.x == 0 && sh.abort) atomicExch(P.err, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Jordan inversion with partial pivoting (FP64), log-det, S^-1 slices
+// ---------------------------------------------------------------------------
+__device__ inline double mag2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// Z = S^-1 of one walker and spin.  Writes the log-det part, the status, the
+// per-column exponents g_k and the digits of the real block form of Z:
+//   Bt[s][w][2k + ro][2j + ri] = {Zr, -Zi, Zi, Zr}[ri][ro] (j, k) / 2^g_k,
+// the B operand of the Theta GEMM (Theta = [phi_re phi_im] B, column pairs).
+__global__ void __launch_bounds__(256)
+gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint16_t* __restrict__ Bt,
+                    int* __restrict__ col_exp, int* __restrict__ gmax, double2* __restrict__ ld_part,
+                    int* __restrict__ st_part) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    double2* A = reinterpret_cast<double2*>(sm);  // N x N
+    double2* colk = A + N * N;                     // N
+    int* piv = reinterpret_cast<int*>(colk + N);   // N
+    int* gk = piv + N;                             // N
+    __shared__ double red_v[32];
+    __shared__ int s_p, s_flag, s_swaps;
+    __shared__ double s_tol;
+    __shared__ double2 s_ld;
+    const int w = blockIdx.x, tid = threadIdx.x;
+    for (int e = tid; e < N * N; e += blockDim.x) A[e] = S[(size_t)w * N * N + e];
+    double m = 0.0;
+    for (int e = tid; e < N * N; e += blockDim.x) m = fmax(m, mag2(A[e]));
+    m = block_max_d(m, red_v);
+    if (tid == 0) {
+        const double tol = (double)N * 2.220446049250313e-16 * sqrt(m);
+        s_tol = tol * tol;
+        s_flag = (m == m && !isinf(m)) ? 0 : 2;
+        s_swaps = 0;
+        s_ld = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int k = 0; k < N && s_flag == 0; ++k) {
+        if (tid < 32) {
+            double best = -1.0;
+            int bi = k;
+            for (int i = k + tid; i < N; i += 32) {
+                const double v = mag2(A[i * N + k]);
+                if (v > best) { best = v; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (tid == 0) {
+                s_p = bi;
+                piv[k] = bi;
+                if (!(best > s_tol)) s_flag = 1;
+            }
+        }
+        __syncthreads();
+        if (s_flag) break;
+        const int p = s_p;
+        if (p != k) {
+            for (int c = tid; c < N; c += blockDim.x) {
+                const double2 t = A[k * N + c];
+                A[k * N + c] = A[p * N + c];
+                A[p * N + c] = t;
+            }
+            if (tid == 0) s_swaps += 1;
+        }
+        __syncthreads();
+        const double2 pv = A[k * N + k];
+        if (tid == 0) {
+            s_ld.x += log(hypot(pv.x, pv.y));
+            s_ld.y += atan2(pv.y, pv.x);
+        }
+        const double2 inv = cdiv(make_double2(1.0, 0.0), pv);
+        for (int i = tid; i < N; i += blockDim.x) colk[i] = A[i * N + k];
+        __syncthreads();
+        // pivot row: A[k][j] *= 1/pv, with A[k][k] = 1/pv
+        for (int j = tid; j < N; j += blockDim.x)
+            A[k * N + j] = j == k ? inv : cmul(A[k * N + j], inv);
+        __syncthreads();
+        // other rows: A[i][j] -= A[i][k] (old) * A[k][j] (new), A[i][k] starts from 0
+        for (int e = tid; e < N * N; e += blockDim.x) {
+            const int i = e / N, j = e % N;
+            if (i == k) continue;
+            const double2 base = j == k ? make_double2(0.0, 0.0) : A[e];
+            A[e] = csub(base, cmul(colk[i], A[k * N + j]));
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    const int flag = s_flag;
+    // undo the row interchanges on the columns, in reverse order
+    if (flag == 0) {
+        for (int k = N - 1; k >= 0; --k) {
+            const int p = piv[k];
+            if (p != k)
+                for (int i = tid; i < N; i += blockDim.x) {
+                    const double2 t = A[i * N + k];
+                    A[i * N + k] = A[i * N + p];
+                    A[i * N + p] = t;
+                }
+            __syncthreads();
+        }
+    }
+    if (tid == 0) {
+        st_part[w] = flag == 0 ? LOAF_WALKER_OK : (flag == 1 ? LOAF_WALKER_SINGULAR : LOAF_WALKER_NAN);
+        double2 ld = s_ld;
+        if (flag == 0) {
+            if (s_swaps & 1) ld.y += 3.141592653589793;
+            ld.y = remainder(ld.y, 6.283185307179586);
+        } else {
+            ld = make_double2(-INFINITY, 0.0);
+        }
+        ld_part[w] = ld;
+    }
+    // per-column exponents of Z (one warp per column)
+    const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    for (int k = wid; k < N; k += nw) {
+        double mm = 0.0;
+        if (flag == 0)
+            for (int j = lane; j < N; j += 32) mm = fmax(mm, fmax(fabs(A[j * N + k].x), fabs(A[j * N + k].y)));
+        for (int o = 16; o > 0; o >>= 1) mm = fmax(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+        if (lane == 0) {
+            const int g = slice_exponent(mm);
+            gk[k] = g;
+            col_exp[(size_t)w * N + k] = g;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int g = -1 << 30;
+        for (int k = 0; k < N; ++k) g = max(g, gk[k]);
+        gmax[w] = g;
+    }
+    const int twoN = 2 * N;
+    for (int e = tid; e < twoN * twoN; e += blockDim.x) {
+        const int cc = e / twoN, K = e % twoN;  // cc = 2k + ro, K = 2j + ri
+        const int k = cc >> 1, ro = cc & 1, j = K >> 1, ri = K & 1;
+        double v = 0.0;
+        if (flag == 0) {
+            const double2 z = A[j * N + k];
+            v = (ri == ro) ? z.x : (ri ? -z.y : z.y);
+        }
+        int d[kNS];
+        digits6(v, gk[k], d);
+#pragma unroll
+        for (int s = 0; s < kNS; ++s) Bt[(((size_t)s * W + w) * twoN + cc) * kpad + K] = h16(d[s]);
+    }
+}
+
+// Delta scale per walker from the slice exponents: |Theta| <= 2N 2^(E + G - 4)
+// < 2^(E + G + 4) and |Phi_T| <= 1, so t = 2^(12 - max(E + G + 4, 0)) keeps
+// |Delta t| <= 2^13 for fp16.
+__global__ void delta_scale_kernel(int W, int nspin, const int* __restrict__ wexp0,
+                                   const int* __restrict__ gmax0, const int* __restrict__ wexp1,
+                                   const int* __restrict__ gmax1, float* __restrict__ inv_t,
+                                   double* __restrict__ scale) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    int b = max(wexp0[w] + gmax0[w] + 4, 0);
+    if (nspin > 1) b = max(b, wexp1[w] + gmax1[w] + 4);
+    b = min(b, 900);
+    scale[w] = ldexp(1.0, 12 - b);
+    inv_t[w] = (float)ldexp(1.0, b - 12);
+}
+
+}  // namespace
+
+void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
+    const int M = c->M;
+    const int p_pad = (M + 7) / 8 * 8;
+    const int r_pad = p_pad;
+    const bool bf16 = precision == LOAF_PREC_BF16X3;
+    int nmax = 0;
+    for (int s = 0; s < c->nspin; ++s) nmax = std::max(nmax, c->sp[s].N);
+    const int kpad_max = (2 * nmax + 7) / 8 * 8;
+    const size_t at_spin = (size_t)kNS * W * M * kpad_max;        // 16-bit entries per spin
+    const size_t bt_spin = (size_t)kNS * W * 2 * nmax * kpad_max;
+    c->w_oz_at.ensure(at_spin * c->nspin * 2);
+    c->w_oz_bt.ensure(bt_spin * c->nspin * 2);
+    c->w_oz_bs.ensure((size_t)kNS * 2 * nmax * W * p_pad * 2);
+    c->w_oz_S.ensure((size_t)W * nmax * nmax * sizeof(double2));
+    c->w_oz_int.ensure((size_t)2 * W * (2 + nmax) * sizeof(int) + 256);
+    const size_t plane = (size_t)2 * W * c->ntot * r_pad;
+    c->w_dhi.ensure(plane * 2);
+    c->w_dlo.ensure(plane * 2);
+    c->w_dscale.ensure((size_t)W * (sizeof(float) + sizeof(double)) + 64);
+    float* inv_t = c->w_dscale.as<float>();
+    double* tscale =
+        reinterpret_cast<double*>(c->w_dscale.as<uint8_t>() + ((W * sizeof(float) + 15) / 16) * 16);
+    c->w_flag.ensure(16);
+    int* err = c->w_flag.as<int>();
+    LOAF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+    // int scratch per spin: [wexp W][gmax W][col_exp W * nmax]
+    int* ib = c->w_oz_int.as<int>();
+    auto wexp = [&](int s) { return ib + (size_t)s * W * (2 + nmax); };
+    auto gmx = [&](int s) { return ib + (size_t)s * W * (2 + nmax) + W; };
+    auto cexp = [&](int s) { return ib + (size_t)s * W * (2 + nmax) + 2 * W; };
+    uint16_t* At = c->w_oz_at.as<uint16_t>();
+    uint16_t* Bt = c->w_oz_bt.as<uint16_t>();
+    if (r_pad != M) {  // basis padding of the Delta planes is never written below
+        LOAF_CUDA(cudaMemsetAsync(c->w_dhi.ptr, 0, plane * 2, c->stream));
+        LOAF_CUDA(cudaMemsetAsync(c->w_dlo.ptr, 0, plane * 2, c->stream));
+    }
+    LOAF_CUDA(cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kOSmem));
+
+    // phase 1, per spin: slices of phi, S = Phi_T^T phi, Z = S^-1 (FP64) and its slices
+    for (int s = 0; s < c->nspin; ++s) {
+        SpinData& sd = c->sp[s];
+        const int N = sd.N, twoN = 2 * N, kpad = (twoN + 7) / 8 * 8;
+        if (sd.oz_trial_version != c->trial_version) {
+            sd.oz_trialT.ensure((size_t)kNS * N * p_pad * 2);
+            sd.oz_rowexp.ensure((size_t)N * sizeof(int));
+            slice_trial_kernel<<<N, 128, 0, c->stream>>>(M, N, p_pad, sd.d_trial.as<double>(),
+                                                       sd.oz_trialT.as<uint16_t>(),
+                                                       sd.oz_rowexp.as<int>());
+            LOAF_LAUNCH_CHECK();
+            sd.oz_trial_version = c->trial_version;
+        }
+        {
+            StageScope sc(c, "theta_slice", 1);
+            const size_t smem = (size_t)kNS * twoN * kSliceRows;
+            LOAF_CUDA(cudaFuncSetAttribute(slice_phi_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            slice_phi_kernel<<<W, 256, smem, c->stream>>>(M, N, c->ntot, sd.col0, p_pad, kpad, W, phi,
+                                                         At + at_spin * s, c->w_oz_bs.as<uint16_t>(),
+                                                         wexp(s));
+            LOAF_LAUNCH_CHECK();
+        }
+        {
+            // S = Phi_T^T phi: rows i, columns (2w + ri) N + j, K = basis
+            StageScope sc(c, "overlap_tc", 1);
+            CUtensorMap mA, mB;
+            map_slices(&mA, sd.oz_trialT.ptr, p_pad, p_pad, N, 1, kOBM);
+            map_slices(&mB, c->w_oz_bs.ptr, p_pad, p_pad, (uint64_t)twoN * W, 1, kOBN);
+            OzParams P{};
+            P.n_rt = ceil_div(N, kOBM);
+            P.n_ct = ceil_div((long)twoN * W, kOBN);
+            P.n_b = 1;
+            P.nk = ceil_div(p_pad, kOBK);
+            P.a_batched = 0;
+            P.idesc = tc::idesc_f16(kOBM, kOBN, false);
+            P.err = err;
+            P.mode = 0;
+            P.M = M; P.N = N; P.ntot = c->ntot; P.col0 = sd.col0; P.r_pad = r_pad; P.W = W;
+            P.rows_valid = N;
+            P.cols_valid = twoN * W;
+            P.row_exp = sd.oz_rowexp.as<int>();
+            P.wexp = wexp(s);
+            P.S_out = c->w_oz_S.as<double>();
+            const int units = P.n_rt * P.n_ct * P.n_b;
+            ozaki_gemm_kernel<<<std::min(units, c->sm_count), 192, kOSmem, c->stream>>>(mA, mB, P);
+            LOAF_LAUNCH_CHECK();
+        }
+        {
+            StageScope sc(c, "inverse_fp64", 1);
+            const size_t smem = (size_t)N * N * sizeof(double2) + (size_t)N * sizeof(double2) +
+                                2 * N * sizeof(int) + 16;
+            LOAF_CUDA(cudaFuncSetAttribute(gauss_jordan_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            gauss_jordan_kernel<<<W, 256, smem, c->stream>>>(
+                N, kpad, W, c->w_oz_S.as<double2>(), Bt + bt_spin * s, cexp(s), gmx(s),
+                c->w_logdet.as<double2>() + (size_t)s * W, c->w_status.as<int>() + (size_t)s * W);
+            LOAF_LAUNCH_CHECK();
+        }
+    }
+    // phase 2: one Delta scale per walker over both spins
+    delta_scale_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
+        W, c->nspin, wexp(0), gmx(0), wexp(c->nspin - 1), gmx(c->nspin - 1), inv_t, tscale);
+    LOAF_LAUNCH_CHECK();
+    // phase 3, per spin: Theta = phi Z on the tensor cores -> Delta planes
+    for (int s = 0; s < c->nspin; ++s) {
+        SpinData& sd = c->sp[s];
+        const int N = sd.N, twoN = 2 * N, kpad = (twoN + 7) / 8 * 8;
+        StageScope sc(c, "theta_tc", 1);
+        CUtensorMap mA, mB;
+        map_slices(&mA, At + at_spin * s, twoN, kpad, M, W, kOBM);
+        map_slices(&mB, Bt + bt_spin * s, twoN, kpad, twoN, W, kOBN);
+        OzParams P{};
+        P.n_rt = ceil_div(M, kOBM);
+        P.n_ct = ceil_div(twoN, kOBN);
+        P.n_b = W;
+        P.nk = ceil_div(twoN, kOBK);
+        P.a_batched = 1;
+        P.idesc = tc::idesc_f16(kOBM, kOBN, false);
+        P.err = err;
+        P.mode = 1;
+        P.M = M; P.N = N; P.ntot = c->ntot; P.col0 = sd.col0; P.r_pad = r_pad; P.W = W;
+        P.rows_valid = M;
+        P.cols_valid = twoN;
+        P.wexp = wexp(s);
+        P.col_exp = cexp(s);
+        P.trial = sd.d_trial.as<double>();
+        P.tscale = tscale;
+        P.dhi = c->w_dhi.as<uint16_t>();
+        P.dlo = c->w_dlo.as<uint16_t>();
+        P.bf16 = bf16 ? 1 : 0;
+        const int units = P.n_rt * P.n_ct * P.n_b;
+        ozaki_gemm_kernel<<<std::min(units, c->sm_count), 192, kOSmem, c->stream>>>(mA, mB, P);
+        LOAF_LAUNCH_CHECK();
+    }
+}
+
+}  // namespace loaf

@@ -1024,30 +1024,32 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
     mx.r_pad = (c->M + 7) / 8 * 8;
     mx.kflat = (long)c->ntot * mx.r_pad;
 
-    // Delta planes for this batch
+    // Delta planes for this batch: formed here from an FP64 Theta, or already
+    // written by the tensor-core Theta stage when theta is NULL
     const int n_wt = ceil_div(W, kBNW);
     const int Wpad = n_wt * kBNW;
     const size_t plane = (size_t)2 * W * c->ntot * mx.r_pad;
-    c->w_dhi.ensure(plane * 2);
-    c->w_dlo.ensure(plane * 2);
     c->w_dscale.ensure((size_t)W * (sizeof(float) + sizeof(double)) + 64);
     float* inv_t = c->w_dscale.as<float>();
     double* scale = reinterpret_cast<double*>(c->w_dscale.as<uint8_t>() + ((W * sizeof(float) + 15) / 16) * 16);
     c->w_flag.ensure(16);
     int* err = c->w_flag.as<int>();
-    LOAF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
-    SpinRef s0 = spin_ref(c->sp[0]), s1 = c->nspin > 1 ? spin_ref(c->sp[1]) : s0;
-    StageScope dsc(c, "delta_split", 2);
-    delta_max_kernel<<<W, 256, 0, c->stream>>>(c->M, c->ntot, c->nspin, s0, s1, theta, inv_t, scale);
-    LOAF_LAUNCH_CHECK();
-    if (bf16)
-        delta_split_kernel<true><<<W * c->ntot, 128, 0, c->stream>>>(c->M, c->ntot, mx.r_pad, W, c->nspin,
-            s0, s1, theta, scale, c->w_dhi.as<uint16_t>(), c->w_dlo.as<uint16_t>());
-    else
-        delta_split_kernel<false><<<W * c->ntot, 128, 0, c->stream>>>(c->M, c->ntot, mx.r_pad, W, c->nspin,
-            s0, s1, theta, scale, c->w_dhi.as<uint16_t>(), c->w_dlo.as<uint16_t>());
-    LOAF_LAUNCH_CHECK();
-    dsc.end();
+    if (theta) {
+        c->w_dhi.ensure(plane * 2);
+        c->w_dlo.ensure(plane * 2);
+        LOAF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+        SpinRef s0 = spin_ref(c->sp[0]), s1 = c->nspin > 1 ? spin_ref(c->sp[1]) : s0;
+        StageScope dsc(c, "delta_split", 2);
+        delta_max_kernel<<<W, 256, 0, c->stream>>>(c->M, c->ntot, c->nspin, s0, s1, theta, inv_t, scale);
+        LOAF_LAUNCH_CHECK();
+        if (bf16)
+            delta_split_kernel<true><<<W * c->ntot, 128, 0, c->stream>>>(c->M, c->ntot, mx.r_pad, W, c->nspin,
+                s0, s1, theta, scale, c->w_dhi.as<uint16_t>(), c->w_dlo.as<uint16_t>());
+        else
+            delta_split_kernel<false><<<W * c->ntot, 128, 0, c->stream>>>(c->M, c->ntot, mx.r_pad, W, c->nspin,
+                s0, s1, theta, scale, c->w_dhi.as<uint16_t>(), c->w_dlo.as<uint16_t>());
+        LOAF_LAUNCH_CHECK();
+    }
     const uint32_t idesc = tc::idesc_f16(kBM, kBN, bf16);
 
     if (e_out) {

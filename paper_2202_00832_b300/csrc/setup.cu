@@ -81,6 +81,7 @@ void setup_load(loaf_ctx* c, int M, int X, const double* h, const double* L, int
     c->canonical[1] = c->nspin > 1 ? c->sp[1].h_trial : std::vector<double>();
     for (int s = 0; s < c->nspin; ++s) half_rotate(c, c->sp[s]);
     LOAF_CUDA(cudaStreamSynchronize(c->stream));
+    c->trial_version++;
     c->loaded = true;
 }
 
@@ -476,6 +477,7 @@ void setup_compress(loaf_ctx* c, double t_svd, const double* r_ops, int n_ops, i
         LOAF_CUDA(cudaMemcpyAsync(sd.d_trial.ptr, C.data(), C.size() * sizeof(double),
                                   cudaMemcpyHostToDevice, c->stream));
         for (auto& m : sd.sLbar) m.release();
+        c->trial_version++;
         half_rotate(c, sd);
         compress_spin(c, sd, t_svd);
     }
