@@ -78,9 +78,12 @@ __device__ inline int slice_exponent(double maxabs) {
     return e + 2;
 }
 
+// 2^e as a double from its bit pattern (|e| < 1000)
+__device__ inline double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
 // six balanced base-128 digits of x = v 2^-E (|x| <= 1/4), most significant first
 __device__ inline void digits6(double v, int E, int (&d)[kNS]) {
-    long long X = __double2ll_rn(ldexp(v, 42 - E));
+    long long X = __double2ll_rn(v * pow2d(42 - E));
 #pragma unroll
     for (int s = kNS - 1; s >= 0; --s) {
         const int r = (int)((X + 64) & 127) - 64;
@@ -133,7 +136,7 @@ slice_phi_kernel(int M, int N, int ntot, int col0, int p_pad, int kpad, int W,
                  const double2* __restrict__ phi, uint16_t* __restrict__ At, uint16_t* __restrict__ Bs,
                  int* __restrict__ wexp) {
     extern __shared__ __align__(16) unsigned char sm[];
-    signed char* dg = reinterpret_cast<signed char*>(sm);  // [kNS][2N][kSliceRows]
+    signed char* dg = reinterpret_cast<signed char*>(sm);  // [kNS][kSliceRows][2N]
     __shared__ double red[32];
     const int w = blockIdx.x;
     const double2* pw = phi + (size_t)w * M * ntot + col0;
@@ -160,7 +163,7 @@ slice_phi_kernel(int M, int N, int ntot, int col0, int p_pad, int kpad, int W,
             digits6(v, E, d);
 #pragma unroll
             for (int s = 0; s < kNS; ++s) {
-                dg[((size_t)s * twoN + (ri * N + j)) * kSliceRows + pp] = (signed char)d[s];
+                dg[((size_t)s * kSliceRows + pp) * twoN + K] = (signed char)d[s];
                 if (p < M) At[(((size_t)s * W + w) * M + p) * kpad + K] = h16(d[s]);
             }
         }
@@ -170,7 +173,7 @@ slice_phi_kernel(int M, int N, int ntot, int col0, int p_pad, int kpad, int W,
             const int col = rem / np, pp = rem % np;  // col = ri * N + j
             const int ri = col / N, j = col % N;
             Bs[((size_t)s * 2 * N * W + (size_t)(2 * w + ri) * N + j) * p_pad + p0 + pp] =
-                h16(dg[((size_t)s * twoN + col) * kSliceRows + pp]);
+                h16(dg[((size_t)s * kSliceRows + pp) * twoN + 2 * j + ri]);
         }
     }
 }
@@ -189,7 +192,7 @@ struct OzParams {
     const int* col_exp;   // mode 1: [W][N] exponent of each column of S^-1
     double* S_out;        // mode 0: [W][N][N] complex as (re, im) doubles
     const double* trial;  // mode 1: M x N
-    const double* tscale; // mode 1: per-walker Delta scale
+    const int* texp;      // mode 1: per-walker Delta scale exponent (scale = 2^texp)
     uint16_t* dhi;
     uint16_t* dlo;
     int bf16;
@@ -209,11 +212,13 @@ __device__ inline uint8_t* align1k(uint8_t* p) {
     return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
 
-__device__ inline void store_delta(const OzParams& P, int w, int r, int cc, double theta) {
-    // cc = 2k + ro of this spin; Delta = Theta - Phi_T (real part only)
+// z 2^e - Phi_T (real part only), times the walker's Delta scale 2^te, as the
+// 16-bit hi/lo pair of the Delta planes; cc = 2k + ro of this spin
+__device__ inline void store_delta(const OzParams& P, int w, int r, int cc, long long z, int e, int te) {
     const int k = cc >> 1, ro = cc & 1;
-    const double delta = ro ? theta : theta - P.trial[(size_t)r * P.N + k];
-    const float f = (float)(delta * P.tscale[w]);
+    const double zt = (double)z * pow2d(e + te);
+    const double dl = ro ? zt : fma(-P.trial[(size_t)r * P.N + k], pow2d(te), zt);
+    const float f = (float)dl;
     uint16_t h, l;
     if (P.bf16) {
         const __nv_bfloat16 a = __float2bfloat16(f);
@@ -229,7 +234,10 @@ __device__ inline void store_delta(const OzParams& P, int w, int r, int cc, doub
     P.dlo[o] = l;
 }
 
-__global__ void __launch_bounds__(192, 1)
+constexpr int kOEpiWarps = 8;  // two per TMEM lane quarter, 40 columns each
+constexpr int kOThreads = 64 + 32 * kOEpiWarps;
+
+__global__ void __launch_bounds__(kOThreads, 1)
 ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                   OzParams P) {
     extern __shared__ uint8_t dyn[];
@@ -240,7 +248,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
     if (threadIdx.x == 0) {
         for (int s = 0; s < kOStages; ++s) { tc::mbar_init(&sh.full[s], 1); tc::mbar_init(&sh.empty[s], 1); }
         tc::mbar_init(&sh.tmem_full, 1);
-        tc::mbar_init(&sh.tmem_empty, 4);
+        tc::mbar_init(&sh.tmem_empty, kOEpiWarps);
         tc::mbar_init(&sh.drain, 1);
         sh.abort = 0;
         tc::fence_barrier_init();
@@ -322,6 +330,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
         tc::mbar_wait(&sh.drain, 0, &never);
     } else if (warp >= 2) {
         const int q = warp & 3;
+        const int h = (warp - 2) >> 2;  // columns [40 h, 40 h + 40)
         uint32_t tph = 0;
         for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
             const int ct = u % P.n_ct, rt = (u / P.n_ct) % P.n_rt, b = u / (P.n_ct * P.n_rt);
@@ -329,14 +338,14 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
             tc::tc_fence_after();
             const int row = rt * kOBM + q * 32 + lane;
 #pragma unroll 1
-            for (int c0 = 0; c0 < kOBN; c0 += 16) {
-                float v[kND][16];
+            for (int c0 = h * 40; c0 < h * 40 + 40; c0 += 8) {
+                float v[kND][8];
 #pragma unroll
                 for (int D = 0; D < kND; ++D)
-                    tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + D * kOBN + c0, v[D]);
+                    tc::tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + D * kOBN + c0, v[D]);
                 tc::tmem_wait_ld();
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
+                for (int c = 0; c < 8; ++c) {
                     long long z = 0;
 #pragma unroll
                     for (int D = 0; D < kND; ++D)
@@ -347,12 +356,12 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
                         // S_w[i][j], column col = (2w + ri) N + j
                         const int w = col / (2 * P.N), rem = col % (2 * P.N);
                         const int ri = rem / P.N, j = rem % P.N;
-                        const double val = ldexp((double)z, P.row_exp[row] + P.wexp[w] - 49);
-                        P.S_out[(((size_t)w * P.N + row) * P.N + j) * 2 + ri] = val;
+                        P.S_out[(((size_t)w * P.N + row) * P.N + j) * 2 + ri] =
+                            (double)z * pow2d(P.row_exp[row] + P.wexp[w] - 49);
                     } else {
                         const int w = b, k = col >> 1;
-                        const double val = ldexp((double)z, P.wexp[w] + P.col_exp[(size_t)w * P.N + k] - 49);
-                        store_delta(P, w, row, col, val);
+                        store_delta(P, w, row, col, z, P.wexp[w] + P.col_exp[(size_t)w * P.N + k] - 49,
+                                    P.texp[w]);
                     }
                 }
             }
@@ -385,13 +394,15 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
     extern __shared__ __align__(16) unsigned char sm[];
     double2* A = reinterpret_cast<double2*>(sm);  // N x N
     double2* colk = A + N * N;                     // N
-    int* piv = reinterpret_cast<int*>(colk + N);   // N
+    double2* pivv = colk + N;                      // N pivots
+    int* piv = reinterpret_cast<int*>(pivv + N);   // N
     int* gk = piv + N;                             // N
     __shared__ double red_v[32];
+    __shared__ double2 red_c[32];
     __shared__ int s_p, s_flag, s_swaps;
     __shared__ double s_tol;
-    __shared__ double2 s_ld;
     const int w = blockIdx.x, tid = threadIdx.x;
+    const int ti = tid >> 4, tj = tid & 15;  // 16 x 16 grid over the matrix
     for (int e = tid; e < N * N; e += blockDim.x) A[e] = S[(size_t)w * N * N + e];
     double m = 0.0;
     for (int e = tid; e < N * N; e += blockDim.x) m = fmax(m, mag2(A[e]));
@@ -401,7 +412,6 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
         s_tol = tol * tol;
         s_flag = (m == m && !isinf(m)) ? 0 : 2;
         s_swaps = 0;
-        s_ld = make_double2(0.0, 0.0);
     }
     __syncthreads();
     for (int k = 0; k < N && s_flag == 0; ++k) {
@@ -421,38 +431,39 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
                 s_p = bi;
                 piv[k] = bi;
                 if (!(best > s_tol)) s_flag = 1;
+                if (bi != k) s_swaps += 1;
             }
         }
         __syncthreads();
         if (s_flag) break;
         const int p = s_p;
-        if (p != k) {
+        if (p != k)
             for (int c = tid; c < N; c += blockDim.x) {
                 const double2 t = A[k * N + c];
                 A[k * N + c] = A[p * N + c];
                 A[p * N + c] = t;
             }
-            if (tid == 0) s_swaps += 1;
-        }
         __syncthreads();
         const double2 pv = A[k * N + k];
-        if (tid == 0) {
-            s_ld.x += log(hypot(pv.x, pv.y));
-            s_ld.y += atan2(pv.y, pv.x);
-        }
         const double2 inv = cdiv(make_double2(1.0, 0.0), pv);
+        if (tid == 0) pivv[k] = pv;
         for (int i = tid; i < N; i += blockDim.x) colk[i] = A[i * N + k];
         __syncthreads();
         // pivot row: A[k][j] *= 1/pv, with A[k][k] = 1/pv
         for (int j = tid; j < N; j += blockDim.x)
             A[k * N + j] = j == k ? inv : cmul(A[k * N + j], inv);
         __syncthreads();
-        // other rows: A[i][j] -= A[i][k] (old) * A[k][j] (new), A[i][k] starts from 0
-        for (int e = tid; e < N * N; e += blockDim.x) {
-            const int i = e / N, j = e % N;
+        // other rows: A[i][j] -= A[i][k] (old) * A[k][j] (new); A[i][k] starts from 0
+        for (int i = ti; i < N; i += 16) {
             if (i == k) continue;
-            const double2 base = j == k ? make_double2(0.0, 0.0) : A[e];
-            A[e] = csub(base, cmul(colk[i], A[k * N + j]));
+            const double2 f = colk[i];
+            for (int j = tj; j < N; j += 16) {
+                const double2 u = A[k * N + j];
+                double2 v = j == k ? make_double2(0.0, 0.0) : A[i * N + j];
+                v.x = fma(-f.x, u.x, fma(f.y, u.y, v.x));
+                v.y = fma(-f.x, u.y, fma(-f.y, u.x, v.y));
+                A[i * N + j] = v;
+            }
         }
         __syncthreads();
     }
@@ -471,9 +482,24 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
             __syncthreads();
         }
     }
+    // log det = sum_k log(pivot_k) + i pi (row exchanges mod 2)
+    double2 lp = make_double2(0.0, 0.0);
+    if (flag == 0)
+        for (int k = tid; k < N; k += blockDim.x) {
+            const double2 d = pivv[k];
+            lp.x += log(hypot(d.x, d.y));
+            lp.y += atan2(d.y, d.x);
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        lp.x += __shfl_xor_sync(0xffffffffu, lp.x, o);
+        lp.y += __shfl_xor_sync(0xffffffffu, lp.y, o);
+    }
+    if ((tid & 31) == 0) red_c[tid >> 5] = lp;
+    __syncthreads();
     if (tid == 0) {
         st_part[w] = flag == 0 ? LOAF_WALKER_OK : (flag == 1 ? LOAF_WALKER_SINGULAR : LOAF_WALKER_NAN);
-        double2 ld = s_ld;
+        double2 ld = make_double2(0.0, 0.0);
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) ld = cadd(ld, red_c[q]);
         if (flag == 0) {
             if (s_swaps & 1) ld.y += 3.141592653589793;
             ld.y = remainder(ld.y, 6.283185307179586);
@@ -523,7 +549,7 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
 __global__ void delta_scale_kernel(int W, int nspin, const int* __restrict__ wexp0,
                                    const int* __restrict__ gmax0, const int* __restrict__ wexp1,
                                    const int* __restrict__ gmax1, float* __restrict__ inv_t,
-                                   double* __restrict__ scale) {
+                                   double* __restrict__ scale, int* __restrict__ texp) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= W) return;
     int b = max(wexp0[w] + gmax0[w] + 4, 0);
@@ -531,6 +557,7 @@ __global__ void delta_scale_kernel(int W, int nspin, const int* __restrict__ wex
     b = min(b, 900);
     scale[w] = ldexp(1.0, 12 - b);
     inv_t[w] = (float)ldexp(1.0, b - 12);
+    texp[w] = 12 - b;
 }
 
 }  // namespace
@@ -549,7 +576,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
     c->w_oz_bt.ensure(bt_spin * c->nspin * 2);
     c->w_oz_bs.ensure((size_t)kNS * 2 * nmax * W * p_pad * 2);
     c->w_oz_S.ensure((size_t)W * nmax * nmax * sizeof(double2));
-    c->w_oz_int.ensure((size_t)2 * W * (2 + nmax) * sizeof(int) + 256);
+    c->w_oz_int.ensure((size_t)(2 * W * (2 + nmax) + W) * sizeof(int) + 256);
     const size_t plane = (size_t)2 * W * c->ntot * r_pad;
     c->w_dhi.ensure(plane * 2);
     c->w_dlo.ensure(plane * 2);
@@ -565,6 +592,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
     auto wexp = [&](int s) { return ib + (size_t)s * W * (2 + nmax); };
     auto gmx = [&](int s) { return ib + (size_t)s * W * (2 + nmax) + W; };
     auto cexp = [&](int s) { return ib + (size_t)s * W * (2 + nmax) + 2 * W; };
+    int* texp = ib + (size_t)2 * W * (2 + nmax);
     uint16_t* At = c->w_oz_at.as<uint16_t>();
     uint16_t* Bt = c->w_oz_bt.as<uint16_t>();
     if (r_pad != M) {  // basis padding of the Delta planes is never written below
@@ -619,12 +647,12 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
             P.wexp = wexp(s);
             P.S_out = c->w_oz_S.as<double>();
             const int units = P.n_rt * P.n_ct * P.n_b;
-            ozaki_gemm_kernel<<<std::min(units, c->sm_count), 192, kOSmem, c->stream>>>(mA, mB, P);
+            ozaki_gemm_kernel<<<std::min(units, c->sm_count), kOThreads, kOSmem, c->stream>>>(mA, mB, P);
             LOAF_LAUNCH_CHECK();
         }
         {
             StageScope sc(c, "inverse_fp64", 1);
-            const size_t smem = (size_t)N * N * sizeof(double2) + (size_t)N * sizeof(double2) +
+            const size_t smem = (size_t)N * N * sizeof(double2) + (size_t)2 * N * sizeof(double2) +
                                 2 * N * sizeof(int) + 16;
             LOAF_CUDA(cudaFuncSetAttribute(gauss_jordan_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -636,7 +664,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
     }
     // phase 2: one Delta scale per walker over both spins
     delta_scale_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
-        W, c->nspin, wexp(0), gmx(0), wexp(c->nspin - 1), gmx(c->nspin - 1), inv_t, tscale);
+        W, c->nspin, wexp(0), gmx(0), wexp(c->nspin - 1), gmx(c->nspin - 1), inv_t, tscale, texp);
     LOAF_LAUNCH_CHECK();
     // phase 3, per spin: Theta = phi Z on the tensor cores -> Delta planes
     for (int s = 0; s < c->nspin; ++s) {
@@ -661,12 +689,12 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
         P.wexp = wexp(s);
         P.col_exp = cexp(s);
         P.trial = sd.d_trial.as<double>();
-        P.tscale = tscale;
+        P.texp = texp;
         P.dhi = c->w_dhi.as<uint16_t>();
         P.dlo = c->w_dlo.as<uint16_t>();
         P.bf16 = bf16 ? 1 : 0;
         const int units = P.n_rt * P.n_ct * P.n_b;
-        ozaki_gemm_kernel<<<std::min(units, c->sm_count), 192, kOSmem, c->stream>>>(mA, mB, P);
+        ozaki_gemm_kernel<<<std::min(units, c->sm_count), kOThreads, kOSmem, c->stream>>>(mA, mB, P);
         LOAF_LAUNCH_CHECK();
     }
 }
