@@ -40,7 +40,6 @@ constexpr int kBM = 128;             // MMA rows
 constexpr int kBNW = 128;            // walkers per tile
 constexpr int kBN = 2 * kBNW;        // MMA columns: (walker, re/im) interleaved
 constexpr int kStages = 2;
-constexpr int kThreadsTC = 192;      // 6 warps
 constexpr uint32_t kTileA = kBM * kRowB;   // 8 KB
 constexpr uint32_t kTileB = kBN * kRowB;   // 16 KB
 
@@ -545,7 +544,13 @@ struct LoParams {
     int* err;
 };
 
-__global__ void __launch_bounds__(kThreadsTC, 1)
+// 16 epilogue warps: four per TMEM lane quarter, each draining 2 of the 8
+// 32-column chunks, so the accumulators are released a quarter of the way
+// through the epilogue's work per unit.
+constexpr int kLEpiWarps = 16;
+constexpr int kLThreads = 64 + 32 * kLEpiWarps;
+
+__global__ void __launch_bounds__(kLThreads, 1)
 lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_constant__ CUtensorMap mUlo,
                       const __grid_constant__ CUtensorMap mVhi, const __grid_constant__ CUtensorMap mVlo,
                       const __grid_constant__ CUtensorMap mDhi, const __grid_constant__ CUtensorMap mDlo,
@@ -561,7 +566,7 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) { tc::mbar_init(&sh.full[s], 1); tc::mbar_init(&sh.empty[s], 1); }
         tc::mbar_init(&sh.tmem_full, 1);
-        tc::mbar_init(&sh.tmem_empty, 4);
+        tc::mbar_init(&sh.tmem_empty, kLEpiWarps);
         tc::mbar_init(&sh.drain, 1);
         sh.abort = 0;
         tc::fence_barrier_init();
@@ -662,11 +667,13 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
         //   da = inv_su * inv_t * acc_a, db = inv_sv * inv_t * acc_b
         //   val = p db + q da + da db   (complex; p, q real)
         // then a butterfly reduction over the 32 ranks of the warp and a sum
-        // over the 4 warps in shared memory.
-        const int q = warp & 3;
-        const int ep_tid = threadIdx.x - 64;  // 0..127
+        // over the 4 lane quarters in shared memory.
+        const int q = warp & 3;                       // TMEM lane quarter
+        const int sub = (warp - 2) >> 2;              // which pair of chunks
+        const int ep_tid = threadIdx.x - 64;          // 0..511
+        constexpr int kChunks = kBN / 32 / (kLEpiWarps / 4);
         uint32_t tph = 0;
-        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
+        for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
             const int pti = u / P.n_wt, wt = u % P.n_wt;
             const int4 t = P.pt[pti];
             const int rl = q * 32 + lane;
@@ -675,15 +682,24 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
             const float cb = rc.z * rc.y;   // p * inv_sv
             const float ca = rc.w * rc.x;   // q * inv_su
             const float cq = rc.x * rc.y;   // inv_su * inv_sv
-            if (!tc::mbar_wait(&sh.tmem_full, tph, abort)) break;
+            const bool got = tc::mbar_wait(&sh.tmem_full, tph, abort);
+            // leave together: the named barriers below expect every epilogue warp
+            if (tc::bar_or(!got, 1, 32 * kLEpiWarps)) break;
             tc::tc_fence_after();
 #pragma unroll 1
-            for (int ch = 0; ch < kBN / 32; ++ch) {
+            for (int c2 = 0; c2 < kChunks; ++c2) {
+                const int ch = sub * kChunks + c2;
                 float va[32], vb[32];
                 const uint32_t lane_off = (uint32_t)(q * 32) << 16;
                 tc::tmem_ld32(tmem + lane_off + ch * 32, va);
                 tc::tmem_ld32(tmem + lane_off + kBN + ch * 32, vb);
                 tc::tmem_wait_ld();
+                if (c2 == kChunks - 1) {
+                    // the last TMEM read of this warp is complete: release
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&sh.tmem_empty);
+                }
                 float v[32];
 #pragma unroll
                 for (int m = 0; m < 16; ++m) {
@@ -699,12 +715,9 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
                 const float r = tc::warp_transpose_sum(v, lane);
                 sh.red[q][ch * 32 + lane] = r;
             }
-            tc::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&sh.tmem_empty);
             tph ^= 1;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            {
+            asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
+            if (ep_tid < kBNW) {
                 const int w = wt * kBNW + ep_tid;
                 const double re = (double)sh.red[0][2 * ep_tid] + sh.red[1][2 * ep_tid] +
                                   sh.red[2][2 * ep_tid] + sh.red[3][2 * ep_tid];
@@ -712,7 +725,7 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
                                   sh.red[2][2 * ep_tid + 1] + sh.red[3][2 * ep_tid + 1];
                 if (w < P.W) P.part[(size_t)pti * P.ldp + w] = make_double2(re, im);
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
         }
     }
     tc::tc_fence_before();
@@ -1116,7 +1129,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             LOAF_CUDA(cudaFuncSetAttribute(lo_exchange_tc_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoSmem));
             StageScope lsc(c, "lo_exchange_tc", 1);
-            lo_exchange_tc_kernel<<<std::min(units, c->sm_count), kThreadsTC, kLoSmem, c->stream>>>(
+            lo_exchange_tc_kernel<<<std::min(units, c->sm_count), kLThreads, kLoSmem, c->stream>>>(
                 mx.mapU_hi, mx.mapU_lo, mx.mapV_hi, mx.mapV_lo, mDhi, mDlo, P);
             LOAF_LAUNCH_CHECK();
         }
