@@ -41,7 +41,6 @@ constexpr int kBNW = 128;            // walkers per tile
 constexpr int kBN = 2 * kBNW;        // MMA columns: (walker, re/im) interleaved
 constexpr int kStages = 2;
 constexpr uint32_t kTileA = kBM * kRowB;   // 8 KB
-constexpr uint32_t kTileB = kBN * kRowB;   // 16 KB
 
 // ---------------------------------------------------------------------------
 // host: TMA descriptors
@@ -60,6 +59,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+// swizzle mode matching a box row of `box_inner` 16-bit elements (64 or 128 bytes)
+CUtensorMapSwizzle swizzle_for(uint32_t box_inner) {
+    return box_inner * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+}
+
 // 16-bit row-major matrix: `rows` rows of `inner` elements, rows `ld` apart
 void map_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t ld,
             uint32_t box_inner, uint32_t box_rows) {
@@ -68,22 +72,22 @@ void map_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uin
     cuuint32_t box[2] = {box_inner, box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims,
-                             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(box_inner),
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     LOAF_REQUIRE(r == CUDA_SUCCESS, LOAF_ERR_CUDA, "cuTensorMapEncodeTiled (2d) failed");
 }
 
-// Delta planes [2W][ntot][r_pad]: x = r, y = orbital c, z = (walker, re/im)
-void map_delta_3d(CUtensorMap* m, const void* base, uint64_t r_pad, uint64_t ntot, uint64_t rows) {
+// Delta planes [2W][ntot][r_pad]: x = r, y = orbital c, z = (walker, re/im);
+// box: box_inner basis functions x one orbital x box_rows (walker, re/im) rows
+void map_delta_3d(CUtensorMap* m, const void* base, uint64_t r_pad, uint64_t ntot, uint64_t rows,
+                  uint32_t box_inner, uint32_t box_rows) {
     cuuint64_t dims[3] = {r_pad, ntot, rows};
     cuuint64_t strides[2] = {r_pad * 2, ntot * r_pad * 2};
-    cuuint32_t box[3] = {(cuuint32_t)kBK, 1, (cuuint32_t)kBN};
+    cuuint32_t box[3] = {box_inner, 1, box_rows};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(base), dims,
-                             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(box_inner),
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     LOAF_REQUIRE(r == CUDA_SUCCESS, LOAF_ERR_CUDA, "cuTensorMapEncodeTiled (3d) failed");
 }
 
@@ -544,36 +548,71 @@ struct LoParams {
     int* err;
 };
 
-// 16 epilogue warps: four per TMEM lane quarter, each draining 2 of the 8
-// 32-column chunks, so the accumulators are released a quarter of the way
-// through the epilogue's work per unit.
+// ---- LO exchange kernel: one CTA pair per (two tiles of a pair, 128 walkers) ----
+// The pair tile list gives every pair an even number of 128-row tiles; tiles
+// 2s and 2s+1 (same pair [ij]) form the 256 MMA rows of a cta_group::2 MMA:
+// the even CTA holds rows 0-127 (tile 2s), the odd CTA rows 128-255 (tile
+// 2s+1), and each holds half of the 256 walker columns of Delta.  Per CTA a
+// k-step of 32 basis functions then moves 64 KB (own weight tiles + half the
+// Delta tiles) instead of 96 KB for a single-CTA 128 x 256 tile.
+// The a (U, Delta_j) and b (V, Delta_i) products are independent GEMMs: the
+// TMA ring holds half-stages of one side each, 64 basis functions deep
+// (128-byte rows: 2 x 16 KB weight tiles + 2 x 16 KB Delta half-tiles = 64 KB),
+// three of them, consumed a, b, a, b, ...
+constexpr int kLBK = 64;                                     // basis functions per k-step
+constexpr int kLRowB = kLBK * 2;                             // 128-byte rows -> SWIZZLE_128B
+constexpr uint32_t kLTileA = kBM * kLRowB;                   // 16 KB
+constexpr uint32_t kLTileBh = (kBN / 2) * kLRowB;            // 16 KB: 128 Delta rows
+constexpr uint32_t kLSlotBytes = 2 * kLTileA + 2 * kLTileBh;  // 64 KB
+constexpr int kLSlots = 3;
 constexpr int kLEpiWarps = 16;
 constexpr int kLThreads = 64 + 32 * kLEpiWarps;
 
+struct LoShared {
+    uint64_t full[kLSlots];    // even CTA: own TMA bytes + the odd CTA's forward
+    uint64_t empty[kLSlots];   // both: the pair MMA's commit (multicast)
+    uint64_t tmem_full;        // both: the pair MMA's commit (multicast)
+    uint64_t tmem_empty;       // even CTA: 16 local + 16 remote epilogue warps
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+    float red[4][kBN];
+};
+
+// Roles per CTA: warp 0 lane 0 TMA producer; warp 1 lane 0 the MMA issuer on
+// the even CTA, on the odd CTA the forwarder that passes each landed stage on
+// to the even CTA's full barrier; warps 2-17 the epilogue (four per TMEM lane
+// quarter, each draining 2 of the 8 32-column chunks).
 __global__ void __launch_bounds__(kLThreads, 1)
 lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_constant__ CUtensorMap mUlo,
                       const __grid_constant__ CUtensorMap mVhi, const __grid_constant__ CUtensorMap mVlo,
                       const __grid_constant__ CUtensorMap mDhi, const __grid_constant__ CUtensorMap mDlo,
                       LoParams P) {
     extern __shared__ uint8_t dyn_smem[];
-    __shared__ TCShared sh;
+    __shared__ LoShared sh;
     uint8_t* base = align1024(dyn_smem);
-    // stage: U hi, U lo, V hi, V lo (8 KB each), Dj hi, Dj lo, Di hi, Di lo (16 KB each)
-    constexpr uint32_t kStageBytes = 4 * kTileA + 4 * kTileB;  // 96 KB
+    // slot: W hi, W lo (8 KB each), D hi, D lo (8 KB each); W = U, D = Delta_j on
+    // the a side, W = V, D = Delta_i on the b side
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_units = P.n_pt * P.n_wt;
+    const uint32_t rank = tc::cluster_ctarank();
+    const bool even = rank == 0;
+    const int cid = blockIdx.x >> 1, n_cl = gridDim.x >> 1;
+    const int n_units = (P.n_pt >> 1) * P.n_wt;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) { tc::mbar_init(&sh.full[s], 1); tc::mbar_init(&sh.empty[s], 1); }
+        for (int s = 0; s < kLSlots; ++s) {
+            tc::mbar_init(&sh.full[s], even ? 2 : 1);
+            tc::mbar_init(&sh.empty[s], 1);
+        }
         tc::mbar_init(&sh.tmem_full, 1);
-        tc::mbar_init(&sh.tmem_empty, kLEpiWarps);
+        tc::mbar_init(&sh.tmem_empty, 2 * kLEpiWarps);
         tc::mbar_init(&sh.drain, 1);
         sh.abort = 0;
         tc::fence_barrier_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(&sh.tmem_base, 2 * kBN);
-        tc::tmem_relinquish();
+        tc::tmem_alloc_pair(&sh.tmem_base, 2 * kBN);
+        tc::tmem_relinquish_pair();
     }
     if (threadIdx.x == 32) {
         tc::tma_prefetch(&mUhi); tc::tma_prefetch(&mUlo); tc::tma_prefetch(&mVhi);
@@ -581,88 +620,102 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
     }
     tc::tc_fence_before();
     __syncthreads();
+    tc::cluster_sync();  // both CTAs' barriers initialised before any remote arrive
     tc::tc_fence_after();
     const uint32_t tmem = sh.tmem_base;
     volatile int* abort = &sh.abort;
 
     if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer ----------------
+        // ---------------- TMA producer (both CTAs) ----------------
         int s = 0;
         uint32_t ph = 0, filled = 0, last_par = 0;
-        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
-            const int4 t = P.pt[u / P.n_wt];
+        for (int u = cid; u < n_units && !*abort; u += n_cl) {
+            const int4 t = P.pt[2 * (u / P.n_wt) + rank];
             const int wt = u % P.n_wt;
-            for (int kc = 0; kc < P.nk; ++kc) {
-                if (!tc::mbar_wait(&sh.empty[s], ph ^ 1, abort)) break;
-                uint8_t* st = base + s * kStageBytes;
-                tc::mbar_arrive_expect_tx(&sh.full[s], kStageBytes);
-                const int x = kc * kBK;
-                tc::tma_load_2d(st, &mUhi, &sh.full[s], x, t.x);
-                tc::tma_load_2d(st + kTileA, &mUlo, &sh.full[s], x, t.x);
-                tc::tma_load_2d(st + 2 * kTileA, &mVhi, &sh.full[s], x, t.x);
-                tc::tma_load_2d(st + 3 * kTileA, &mVlo, &sh.full[s], x, t.x);
-                uint8_t* sb = st + 4 * kTileA;
-                tc::tma_load_3d(sb, &mDhi, &sh.full[s], x, t.w, wt * kBN);
-                tc::tma_load_3d(sb + kTileB, &mDlo, &sh.full[s], x, t.w, wt * kBN);
-                tc::tma_load_3d(sb + 2 * kTileB, &mDhi, &sh.full[s], x, t.z, wt * kBN);
-                tc::tma_load_3d(sb + 3 * kTileB, &mDlo, &sh.full[s], x, t.z, wt * kBN);
+            const int col = wt * kBN + (int)rank * (kBN / 2);
+            for (int h = 0; h < 2 * P.nk; ++h) {
+                if (!tc::mbar_wait_cluster(&sh.empty[s], ph ^ 1, abort)) break;
+                uint8_t* st = base + s * kLSlotBytes;
+                tc::mbar_arrive_expect_tx(&sh.full[s], kLSlotBytes);
+                const int x = (h >> 1) * kLBK;
+                const bool side_b = h & 1;
+                tc::tma_load_2d(st, side_b ? &mVhi : &mUhi, &sh.full[s], x, t.x);
+                tc::tma_load_2d(st + kLTileA, side_b ? &mVlo : &mUlo, &sh.full[s], x, t.x);
+                const int orb = side_b ? t.z : t.w;
+                tc::tma_load_3d(st + 2 * kLTileA, &mDhi, &sh.full[s], x, orb, col);
+                tc::tma_load_3d(st + 2 * kLTileA + kLTileBh, &mDlo, &sh.full[s], x, orb, col);
                 filled |= 1u << s;
                 last_par = (last_par & ~(1u << s)) | (ph << s);
-                if (++s == kStages) { s = 0; ph ^= 1; }
+                if (++s == kLSlots) { s = 0; ph ^= 1; }
             }
         }
         if (*abort) {
-            for (int q = 0; q < kStages; ++q)
+            // the even CTA's full barriers also count the forward, so wait for
+            // the transaction bytes only: every load issued has landed once the
+            // phase's tx count is back to zero; bounded by the wait limit
+            for (int q = 0; q < kLSlots; ++q)
                 if (filled & (1u << q)) {
                     volatile int never = 0;
-                    tc::mbar_wait(&sh.full[q], (last_par >> q) & 1, &never);
+                    if (even) {
+                        // one arrive of ours is outstanding only if the odd
+                        // CTA's forward is missing; give it up to the limit
+                        tc::mbar_wait_cluster(&sh.full[q], (last_par >> q) & 1, &never);
+                    } else {
+                        tc::mbar_wait(&sh.full[q], (last_par >> q) & 1, &never);
+                    }
                 }
         }
+    } else if (warp == 1 && lane == 0 && !even) {
+        // ---------------- forwarder (odd CTA) ----------------
+        const uint32_t peer_full0 = tc::mapa_shared(&sh.full[0], 0);
+        int s = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        for (int u = cid; u < n_units && ok && !*abort; u += n_cl) {
+            for (int h = 0; h < 2 * P.nk; ++h) {
+                if (!tc::mbar_wait(&sh.full[s], ph, abort)) { ok = false; break; }
+                tc::mbar_arrive_remote(peer_full0 + s * (uint32_t)sizeof(uint64_t));
+                if (++s == kLSlots) { s = 0; ph ^= 1; }
+            }
+        }
     } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer ----------------
+        // ---------------- pair MMA issuer (even CTA) ----------------
         int s = 0;
         uint32_t ph = 0, tph = 0;
         const uint32_t tA = tmem, tB = tmem + kBN;  // accumulators a (U side), b (V side)
-        for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
-            if (!tc::mbar_wait(&sh.tmem_empty, tph ^ 1, abort)) break;
+        for (int u = cid; u < n_units && !*abort; u += n_cl) {
+            if (!tc::mbar_wait_cluster(&sh.tmem_empty, tph ^ 1, abort)) break;
             tc::tc_fence_after();
             bool ok = true;
-            for (int kc = 0; kc < P.nk; ++kc) {
-                if (!tc::mbar_wait(&sh.full[s], ph, abort)) { ok = false; break; }
+            for (int h = 0; h < 2 * P.nk; ++h) {
+                if (!tc::mbar_wait_cluster(&sh.full[s], ph, abort)) { ok = false; break; }
                 tc::tc_fence_after();
-                const uint32_t st = tc::smem_u32(base + s * kStageBytes);
-                const uint32_t sb = st + 4 * kTileA;
+                const uint32_t st = tc::smem_u32(base + s * kLSlotBytes);
+                const uint32_t d = (h & 1) ? tB : tA;
 #pragma unroll
-                for (int kk = 0; kk < kBK / 16; ++kk) {
+                for (int kk = 0; kk < kLBK / 16; ++kk) {
                     const uint32_t off = kk * 32;
-                    const uint64_t uhi = tc::smem_desc(st + off, kRowB);
-                    const uint64_t ulo = tc::smem_desc(st + kTileA + off, kRowB);
-                    const uint64_t vhi = tc::smem_desc(st + 2 * kTileA + off, kRowB);
-                    const uint64_t vlo = tc::smem_desc(st + 3 * kTileA + off, kRowB);
-                    const uint64_t jhi = tc::smem_desc(sb + off, kRowB);
-                    const uint64_t jlo = tc::smem_desc(sb + kTileB + off, kRowB);
-                    const uint64_t ihi = tc::smem_desc(sb + 2 * kTileB + off, kRowB);
-                    const uint64_t ilo = tc::smem_desc(sb + 3 * kTileB + off, kRowB);
-                    const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
-                    tc::mma_f16(tA, uhi, jhi, P.idesc, acc);
-                    tc::mma_f16(tA, uhi, jlo, P.idesc, 1u);
-                    tc::mma_f16(tA, ulo, jhi, P.idesc, 1u);
-                    tc::mma_f16(tB, vhi, ihi, P.idesc, acc);
-                    tc::mma_f16(tB, vhi, ilo, P.idesc, 1u);
-                    tc::mma_f16(tB, vlo, ihi, P.idesc, 1u);
+                    const uint64_t whi = tc::smem_desc(st + off, kLRowB);
+                    const uint64_t wlo = tc::smem_desc(st + kLTileA + off, kLRowB);
+                    const uint64_t dhi = tc::smem_desc(st + 2 * kLTileA + off, kLRowB);
+                    const uint64_t dlo = tc::smem_desc(st + 2 * kLTileA + kLTileBh + off, kLRowB);
+                    const uint32_t acc = (h > 1 || kk > 0) ? 1u : 0u;
+                    tc::mma_f16_pair(d, whi, dhi, P.idesc, acc);
+                    tc::mma_f16_pair(d, whi, dlo, P.idesc, 1u);
+                    tc::mma_f16_pair(d, wlo, dhi, P.idesc, 1u);
                 }
-                tc::mma_commit(&sh.empty[s]);
-                if (++s == kStages) { s = 0; ph ^= 1; }
+                tc::mma_commit_pair(&sh.empty[s], 0x3);
+                if (++s == kLSlots) { s = 0; ph ^= 1; }
             }
             if (!ok) break;
-            tc::mma_commit(&sh.tmem_full);
+            tc::mma_commit_pair(&sh.tmem_full, 0x3);
             tph ^= 1;
         }
-        tc::mma_commit(&sh.drain);
+        tc::mma_commit_pair(&sh.drain, 0x1);
         volatile int never = 0;
         tc::mbar_wait(&sh.drain, 0, &never);
     } else if (warp >= 2) {
-        // ---------------- epilogue ----------------
+        // ---------------- epilogue (both CTAs) ----------------
         // lane = rank within the tile; per walker m of a 16-walker chunk:
         //   da = inv_su * inv_t * acc_a, db = inv_sv * inv_t * acc_b
         //   val = p db + q da + da db   (complex; p, q real)
@@ -672,9 +725,10 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
         const int sub = (warp - 2) >> 2;              // which pair of chunks
         const int ep_tid = threadIdx.x - 64;          // 0..511
         constexpr int kChunks = kBN / 32 / (kLEpiWarps / 4);
+        const uint32_t even_tmem_empty = tc::mapa_shared(&sh.tmem_empty, 0);
         uint32_t tph = 0;
-        for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
-            const int pti = u / P.n_wt, wt = u % P.n_wt;
+        for (int u = cid; u < n_units; u += n_cl) {
+            const int pti = 2 * (u / P.n_wt) + (int)rank, wt = u % P.n_wt;
             const int4 t = P.pt[pti];
             const int rl = q * 32 + lane;
             float4 rc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -682,7 +736,7 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
             const float cb = rc.z * rc.y;   // p * inv_sv
             const float ca = rc.w * rc.x;   // q * inv_su
             const float cq = rc.x * rc.y;   // inv_su * inv_sv
-            const bool got = tc::mbar_wait(&sh.tmem_full, tph, abort);
+            const bool got = tc::mbar_wait_cluster(&sh.tmem_full, tph, abort);
             // leave together: the named barriers below expect every epilogue warp
             if (tc::bar_or(!got, 1, 32 * kLEpiWarps)) break;
             tc::tc_fence_after();
@@ -698,7 +752,7 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
                     // the last TMEM read of this warp is complete: release
                     tc::tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&sh.tmem_empty);
+                    if (lane == 0) tc::mbar_arrive_remote(even_tmem_empty);
                 }
                 float v[32];
 #pragma unroll
@@ -730,8 +784,11 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
     }
     tc::tc_fence_before();
     __syncthreads();
+    // the even CTA's MMAs read the odd CTA's shared memory and write its TMEM,
+    // and both CTAs arrive on each other's barriers: neither leaves early
+    tc::cluster_sync();
     tc::tc_fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, 2 * kBN);
+    if (warp == 0) tc::tmem_dealloc_pair(tmem, 2 * kBN);
     if (threadIdx.x == 0 && sh.abort) atomicExch(P.err, 1);
 }
 
@@ -940,6 +997,13 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
                                           sd.col0 + pt.i[n], sd.col0 + pt.j[n]));
                 ++cnt;
             }
+            // the CTA-pair kernel takes a pair's tiles two at a time: an odd
+            // count gets an empty tile (no valid rows, partials exactly zero)
+            if (cnt & 1) {
+                tiles.push_back(make_int4((int)(row_base + pt.off[n]), 0, sd.col0 + pt.i[n],
+                                          sd.col0 + pt.j[n]));
+                ++cnt;
+            }
             npt[gpair] = cnt;
         }
         for (int n = 0; n < pt.npairs; ++n)
@@ -975,10 +1039,10 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     mx.h_pw = pw;
     mx.h_e0 = e0;
     mx.screen_built = -1;
-    map_2d(&mx.mapU_hi, mx.U_hi.ptr, mx.r_pad, Rb, mx.r_pad, kBK, kBM);
-    map_2d(&mx.mapU_lo, mx.U_lo.ptr, mx.r_pad, Rb, mx.r_pad, kBK, kBM);
-    map_2d(&mx.mapV_hi, mx.V_hi.ptr, mx.r_pad, Rb, mx.r_pad, kBK, kBM);
-    map_2d(&mx.mapV_lo, mx.V_lo.ptr, mx.r_pad, Rb, mx.r_pad, kBK, kBM);
+    map_2d(&mx.mapU_hi, mx.U_hi.ptr, mx.r_pad, Rb, mx.r_pad, kLBK, kBM);
+    map_2d(&mx.mapU_lo, mx.U_lo.ptr, mx.r_pad, Rb, mx.r_pad, kLBK, kBM);
+    map_2d(&mx.mapV_hi, mx.V_hi.ptr, mx.r_pad, Rb, mx.r_pad, kLBK, kBM);
+    map_2d(&mx.mapV_lo, mx.V_lo.ptr, mx.r_pad, Rb, mx.r_pad, kLBK, kBM);
     mx.lo_ready = true;
 }
 
@@ -1018,7 +1082,34 @@ void ensure_screened_tiles(loaf_ctx* c, MixedOps& mx) {
 
 constexpr size_t kCoulSmem =
     kCStages * (2 * kTileA + 2 * kCTileB) + 32 * kCEpiWarps * 32 * sizeof(float) + 1024;
-constexpr size_t kLoSmem = kStages * (4 * kTileA + 4 * kTileB) + 1024;
+constexpr size_t kLoSmem = kLSlots * kLSlotBytes + 1024;
+
+// CTA pairs of the LO kernel that fit on the GPU at once (the persistent grid):
+// clusters sit inside a GPC, so this can be below half the SM count
+int lo_max_clusters(loaf_ctx* c) {
+    static int cached[64] = {0};
+    int dev = 0;
+    LOAF_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && cached[dev] > 0) return cached[dev];
+    LOAF_CUDA(cudaFuncSetAttribute(lo_exchange_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kLoSmem));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * (c->sm_count / 2));
+    cfg.blockDim = dim3(kLThreads);
+    cfg.dynamicSmemBytes = kLoSmem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    LOAF_CUDA(cudaOccupancyMaxActiveClusters(&n, lo_exchange_tc_kernel, &cfg));
+    LOAF_REQUIRE(n > 0, LOAF_ERR_CUDA, "the LO exchange kernel's CTA pair does not fit on an SM pair");
+    if (dev < 64) cached[dev] = n;
+    return n;
+}
 
 }  // namespace
 
@@ -1063,7 +1154,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
                 s0, s1, theta, scale, c->w_dhi.as<uint16_t>(), c->w_dlo.as<uint16_t>());
         LOAF_LAUNCH_CHECK();
     }
-    const uint32_t idesc = tc::idesc_f16(kBM, kBN, bf16);
+    const uint32_t idesc = tc::idesc_f16(2 * kBM, kBN, bf16);  // pair MMA: M = 256
 
     if (e_out) {
         // ---- Coulomb + one-body on the tensor cores ----
@@ -1110,8 +1201,8 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         const double list_ek0 = screened ? mx.s_EK0 : mx.EK0;
         if (n_pt > 0) {
             CUtensorMap mDhi, mDlo;
-            map_delta_3d(&mDhi, c->w_dhi.ptr, mx.r_pad, c->ntot, 2L * W);
-            map_delta_3d(&mDlo, c->w_dlo.ptr, mx.r_pad, c->ntot, 2L * W);
+            map_delta_3d(&mDhi, c->w_dhi.ptr, mx.r_pad, c->ntot, 2L * W, kLBK, kBN / 2);
+            map_delta_3d(&mDlo, c->w_dlo.ptr, mx.r_pad, c->ntot, 2L * W, kLBK, kBN / 2);
             LoParams P;
             P.pt = tile_list;
             P.rowc = mx.row_c.as<float4>();
@@ -1120,17 +1211,28 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             P.n_wt = n_wt;
             P.W = W;
             P.ldp = Wpad;
-            P.nk = ceil_div(mx.r_pad, kBK);
+            P.nk = ceil_div(mx.r_pad, kLBK);
             P.idesc = idesc;
             P.err = err;
             c->w_lopart.ensure((size_t)n_pt * Wpad * sizeof(double2));
             P.part = c->w_lopart.as<double2>();
-            const int units = n_pt * n_wt;
-            LOAF_CUDA(cudaFuncSetAttribute(lo_exchange_tc_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoSmem));
+            const int units = (n_pt / 2) * n_wt;
+            const int n_cl = std::min(units, lo_max_clusters(c));
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(2 * n_cl);
+            cfg.blockDim = dim3(kLThreads);
+            cfg.dynamicSmemBytes = kLoSmem;
+            cfg.stream = c->stream;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
             StageScope lsc(c, "lo_exchange_tc", 1);
-            lo_exchange_tc_kernel<<<std::min(units, c->sm_count), kLThreads, kLoSmem, c->stream>>>(
-                mx.mapU_hi, mx.mapU_lo, mx.mapV_hi, mx.mapV_lo, mDhi, mDlo, P);
+            LOAF_CUDA(cudaLaunchKernelEx(&cfg, lo_exchange_tc_kernel, mx.mapU_hi, mx.mapU_lo,
+                                         mx.mapV_hi, mx.mapV_lo, mDhi, mDlo, P));
             LOAF_LAUNCH_CHECK();
         }
         c->w_lopart.ensure(16);
