@@ -139,41 +139,55 @@ slice_phi_kernel(int M, int N, int ntot, int col0, int p_pad, int kpad, int W,
     signed char* dg = reinterpret_cast<signed char*>(sm);  // [kNS][kSliceRows][2N]
     __shared__ double red[32];
     const int w = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const double2* pw = phi + (size_t)w * M * ntot + col0;
+    // walker exponent: warps over rows p, lanes over orbitals j
     double m = 0.0;
-    for (long e = threadIdx.x; e < (long)M * N; e += blockDim.x) {
-        const double2 v = pw[(e / N) * ntot + e % N];
-        m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
-    }
+    for (int p = warp; p < M; p += nwarp)
+        for (int j = lane; j < N; j += 32) {
+            const double2 v = pw[(size_t)p * ntot + j];
+            m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+        }
     const int E = slice_exponent(block_max_d(m, red));
     if (threadIdx.x == 0) wexp[w] = E;
     const int twoN = 2 * N;
     for (int p0 = 0; p0 < p_pad; p0 += kSliceRows) {
         const int np = min(kSliceRows, p_pad - p0);
         __syncthreads();
-        for (int e = threadIdx.x; e < np * twoN; e += blockDim.x) {
-            const int pp = e / twoN, K = e % twoN;
-            const int p = p0 + pp, j = K >> 1, ri = K & 1;
-            double v = 0.0;
-            if (p < M) {
-                const double2 z = pw[(size_t)p * ntot + j];
-                v = ri ? z.y : z.x;
-            }
-            int d[kNS];
-            digits6(v, E, d);
+        // digits of (re, im) of phi[p][j]: K = 2j, 2j + 1 stored together
+        for (int pp = warp; pp < np; pp += nwarp) {
+            const int p = p0 + pp;
+            for (int j = lane; j < N; j += 32) {
+                double2 z = make_double2(0.0, 0.0);
+                if (p < M) z = pw[(size_t)p * ntot + j];
+                int dr[kNS], di[kNS];
+                digits6(z.x, E, dr);
+                digits6(z.y, E, di);
 #pragma unroll
-            for (int s = 0; s < kNS; ++s) {
-                dg[((size_t)s * kSliceRows + pp) * twoN + K] = (signed char)d[s];
-                if (p < M) At[(((size_t)s * W + w) * M + p) * kpad + K] = h16(d[s]);
+                for (int s = 0; s < kNS; ++s) {
+                    char2 c2;
+                    c2.x = (signed char)dr[s];
+                    c2.y = (signed char)di[s];
+                    *reinterpret_cast<char2*>(dg + ((size_t)s * kSliceRows + pp) * twoN + 2 * j) = c2;
+                    if (p < M)
+                        *reinterpret_cast<uint32_t*>(At + (((size_t)s * W + w) * M + p) * kpad + 2 * j) =
+                            (uint32_t)h16(dr[s]) | ((uint32_t)h16(di[s]) << 16);
+                }
             }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < kNS * twoN * np; e += blockDim.x) {
-            const int s = e / (twoN * np), rem = e % (twoN * np);
-            const int col = rem / np, pp = rem % np;  // col = ri * N + j
-            const int ri = col / N, j = col % N;
-            Bs[((size_t)s * 2 * N * W + (size_t)(2 * w + ri) * N + j) * p_pad + p0 + pp] =
-                h16(dg[((size_t)s * kSliceRows + pp) * twoN + 2 * j + ri]);
+        // transpose: one warp per (slice, ri, j) row of Bs, two basis rows per lane
+        for (int row = warp; row < kNS * twoN; row += nwarp) {
+            const int s = row / twoN, col = row - s * twoN;  // col = ri * N + j
+            const int ri = col >= N ? 1 : 0, j = col - ri * N;
+            const signed char* src = dg + (size_t)s * kSliceRows * twoN + 2 * j + ri;
+            uint16_t* dst = Bs + ((size_t)s * 2 * N * W + (size_t)(2 * w + ri) * N + j) * p_pad + p0;
+            const int pp = 2 * lane;
+            if (pp < np) {
+                const uint32_t lo = h16(src[(size_t)pp * twoN]);
+                const uint32_t hi = pp + 1 < np ? h16(src[(size_t)(pp + 1) * twoN]) : 0u;
+                *reinterpret_cast<uint32_t*>(dst + pp) = lo | (hi << 16);
+            }
         }
     }
 }
