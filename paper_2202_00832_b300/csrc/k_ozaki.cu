@@ -108,6 +108,16 @@ __device__ inline double block_max_d(double v, double* red) {
 // slicing
 // ---------------------------------------------------------------------------
 
+// Phi_T (M x N, row-major) -> column-major copy (N x M)
+__global__ void transpose_trial_kernel(int M, int N, const double* __restrict__ trial,
+                                       double* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < M * N) {
+        const int k = e / M, r = e - k * M;
+        out[e] = trial[(size_t)r * N + k];
+    }
+}
+
 // Phi_T^T rows i (per-row exponent), K = basis p: A_S[s][i][p_pad]
 __global__ void slice_trial_kernel(int M, int N, int p_pad, const double* __restrict__ trial,
                                    uint16_t* __restrict__ out, int* __restrict__ row_exp) {
@@ -205,7 +215,7 @@ struct OzParams {
     const int* wexp;      // exponent of each walker's phi block
     const int* col_exp;   // mode 1: [W][N] exponent of each column of S^-1
     double* S_out;        // mode 0: [W][N][N] complex as (re, im) doubles
-    const double* trial;  // mode 1: M x N
+    const double* trial_cm;  // mode 1: Phi_T column-major, N x M
     const int* texp;      // mode 1: per-walker Delta scale exponent (scale = 2^texp)
     uint16_t* dhi;
     uint16_t* dlo;
@@ -231,7 +241,7 @@ __device__ inline uint8_t* align1k(uint8_t* p) {
 __device__ inline void store_delta(const OzParams& P, int w, int r, int cc, long long z, int e, int te) {
     const int k = cc >> 1, ro = cc & 1;
     const double zt = (double)z * pow2d(e + te);
-    const double dl = ro ? zt : fma(-P.trial[(size_t)r * P.N + k], pow2d(te), zt);
+    const double dl = ro ? zt : fma(-P.trial_cm[(size_t)k * P.M + r], pow2d(te), zt);
     const float f = (float)dl;
     uint16_t h, l;
     if (P.bf16) {
@@ -248,7 +258,7 @@ __device__ inline void store_delta(const OzParams& P, int w, int r, int cc, long
     P.dlo[o] = l;
 }
 
-constexpr int kOEpiWarps = 8;  // two per TMEM lane quarter, 40 columns each
+constexpr int kOEpiWarps = 16;  // four per TMEM lane quarter, 8-column chunks h, h + 4, h + 8
 constexpr int kOThreads = 64 + 32 * kOEpiWarps;
 
 __global__ void __launch_bounds__(kOThreads, 1)
@@ -344,7 +354,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
         tc::mbar_wait(&sh.drain, 0, &never);
     } else if (warp >= 2) {
         const int q = warp & 3;
-        const int h = (warp - 2) >> 2;  // columns [40 h, 40 h + 40)
+        const int h = (warp - 2) >> 2;  // chunk h, h + 4, ... of 8 columns
         uint32_t tph = 0;
         for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
             const int ct = u % P.n_ct, rt = (u / P.n_ct) % P.n_rt, b = u / (P.n_ct * P.n_rt);
@@ -352,7 +362,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
             tc::tc_fence_after();
             const int row = rt * kOBM + q * 32 + lane;
 #pragma unroll 1
-            for (int c0 = h * 40; c0 < h * 40 + 40; c0 += 8) {
+            for (int c0 = h * 8; c0 < kOBN; c0 += 32) {
                 float v[kND][8];
 #pragma unroll
                 for (int D = 0; D < kND; ++D)
@@ -362,8 +372,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
                 for (int c = 0; c < 8; ++c) {
                     long long z = 0;
 #pragma unroll
-                    for (int D = 0; D < kND; ++D)
-                        z += (long long)__float2ll_rn(v[D][c]) * (1LL << (7 * (kND - 1 - D)));
+                    for (int D = 0; D < kND; ++D)  // |v| < 2^24: exact as int32
+                        z += (long long)__float2int_rn(v[D][c]) * (1LL << (7 * (kND - 1 - D)));
                     const int col = ct * kOBN + c0 + c;
                     if (row >= P.rows_valid || col >= P.cols_valid) continue;
                     if (P.mode == 0) {
@@ -627,6 +637,10 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
                                                        sd.oz_trialT.as<uint16_t>(),
                                                        sd.oz_rowexp.as<int>());
             LOAF_LAUNCH_CHECK();
+            sd.oz_trial_cm.ensure((size_t)N * M * sizeof(double));
+            transpose_trial_kernel<<<ceil_div(M * N, 256), 256, 0, c->stream>>>(
+                M, N, sd.d_trial.as<double>(), sd.oz_trial_cm.as<double>());
+            LOAF_LAUNCH_CHECK();
             sd.oz_trial_version = c->trial_version;
         }
         {
@@ -702,7 +716,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
         P.cols_valid = twoN;
         P.wexp = wexp(s);
         P.col_exp = cexp(s);
-        P.trial = sd.d_trial.as<double>();
+        P.trial_cm = sd.oz_trial_cm.as<double>();
         P.texp = texp;
         P.dhi = c->w_dhi.as<uint16_t>();
         P.dlo = c->w_dlo.as<uint16_t>();
