@@ -83,8 +83,50 @@ struct DevBuf {
         LOAF_CUDA(cudaMalloc(&ptr, nbytes));
         bytes = nbytes;
     }
+    // as ensure, and zero-filled whenever it had to (re)allocate
+    void ensure_zeroed(size_t nbytes, cudaStream_t stream) {
+        if (nbytes <= bytes) return;
+        ensure(nbytes);
+        LOAF_CUDA(cudaMemsetAsync(ptr, 0, nbytes, stream));
+    }
     template <class T> T* as() const { return static_cast<T*>(ptr); }
 };
+
+// ---------------------------------------------------------------------------
+// 16-bit operand tiles for the tensor cores
+// ---------------------------------------------------------------------------
+// A tile is 128 rows x 64 k of 16-bit values (16 KB) stored as the shared-
+// memory image the MMA reads with the 128-byte swizzle: row r occupies bytes
+// [128 r, 128 r + 128) and its 16-byte chunk j (k = 8 j .. 8 j + 7) sits at
+// chunk position j ^ (r mod 8).  A whole tile moves with one bulk copy.
+constexpr int kTileRows = 128;
+constexpr int kTileK = 64;
+constexpr int kTileElems = kTileRows * kTileK;
+constexpr uint32_t kTileBytes = kTileElems * 2;
+
+__host__ __device__ inline int sw128_elem(int row, int k) {
+    return row * kTileK + ((((k >> 3) ^ (row & 7)) << 3) | (k & 7));
+}
+
+// Delta planes (hi and lo, one each): tile (c, rb, kb) holds walker rows
+// z = 2w + re/im in [128 rb, 128 rb + 128) of orbital column c and basis
+// functions r in [64 kb, 64 kb + 64); r >= M stays zero (the planes are zero-
+// filled on allocation and never written there).
+struct DeltaGeom {
+    int nkb = 0, nrb = 0;
+    size_t plane = 0;  // 16-bit elements per plane
+};
+inline DeltaGeom delta_geom(int M, int ntot, int W) {
+    DeltaGeom g;
+    g.nkb = (M + kTileK - 1) / kTileK;
+    g.nrb = 2 * ((W + kTileRows - 1) / kTileRows);  // even: whole 128-walker tiles
+    g.plane = (size_t)ntot * g.nrb * g.nkb * kTileElems;
+    return g;
+}
+__device__ inline size_t delta_elem(int z, int c, int r, int nrb, int nkb) {
+    return ((size_t)((size_t)c * nrb + (z >> 7)) * nkb + (r >> 6)) * kTileElems +
+           sw128_elem(z & 127, r & 63);
+}
 
 // ---------------------------------------------------------------------------
 // per-spin data
@@ -159,19 +201,21 @@ struct MixedOps {
     DevBuf L_hi, L_lo, L_inv;  // (X+1) x kflat 16-bit; inverse row scale (float)
     DevBuf J0;                 // X doubles: trial Coulomb vector
     double E1_0 = 0.0;         // trial one-body energy
-    CUtensorMap mapL_hi, mapL_lo;
+    int nkb = 0;               // 64-wide basis blocks per orbital
+    int n_mt = 0;              // 128-row blocks of the Coulomb operand
+    DevBuf Lb_hi, Lb_lo;       // Coulomb operand tiles [mt][c][kb]
     // LO operand: rows of Ubar^T and Vbar of both spins, concatenated
     long R = 0;
     DevBuf U_hi, U_lo, V_hi, V_lo;  // R x r_pad 16-bit
     DevBuf row_c;              // R float4 {inv_su, inv_sv, p, q}
-    DevBuf pt;                 // pair tiles int4 {row0, nvalid, ci, cj}
+    DevBuf pt;                 // pair tiles int4 {row0, nvalid, ci << 16 | cj, tile block}
     int n_pt = 0;
     int n_pairs = 0;           // pairs over both spins
     DevBuf pair_pt0, pair_npt; // first pair tile and count per pair (int)
     DevBuf pair_w;             // per pair: 0.5 * mult * (1 or 2) (double)
     DevBuf e0;                 // per pair: trial value p . q (double)
     double EK0 = 0.0;          // 1/2 sum_sigma mult sum_n wgt_n e0_n
-    CUtensorMap mapU_hi, mapU_lo, mapV_hi, mapV_lo;
+    DevBuf Ub_hi, Ub_lo, Vb_hi, Vb_lo;  // LO operand tiles [tile][kb]
     // host copies of the unscreened tile list, and the screened list
     std::vector<int4> h_tiles;
     std::vector<int> h_pt0, h_npt, h_order;
@@ -181,7 +225,8 @@ struct MixedOps {
     double s_EK0 = 0.0;
     void release() {
         for (DevBuf* b : {&L_hi, &L_lo, &L_inv, &J0, &U_hi, &U_lo, &V_hi, &V_lo, &row_c, &pt,
-                          &pair_pt0, &pair_npt, &pair_w, &e0, &s_pt, &s_pt0, &s_npt, &s_pw})
+                          &pair_pt0, &pair_npt, &pair_w, &e0, &s_pt, &s_pt0, &s_npt, &s_pw,
+                          &Lb_hi, &Lb_lo, &Ub_hi, &Ub_lo, &Vb_hi, &Vb_lo})
             b->release();
         coul_ready = lo_ready = false;
         screen_built = -1;

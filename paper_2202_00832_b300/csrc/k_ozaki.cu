@@ -211,6 +211,7 @@ struct OzParams {
     int* err;
     int mode;  // 0: overlap S, 1: Theta -> Delta planes
     int M, N, ntot, col0, r_pad, W, rows_valid, cols_valid;
+    int nrb, nkb;         // mode 1: Delta tile geometry
     const int* row_exp;   // mode 0: exponent of each Phi_T^T row
     const int* wexp;      // exponent of each walker's phi block
     const int* col_exp;   // mode 1: [W][N] exponent of each column of S^-1
@@ -253,7 +254,7 @@ __device__ inline void store_delta(const OzParams& P, int w, int r, int cc, long
         h = __half_as_ushort(a);
         l = __half_as_ushort(__float2half(f - __half2float(a)));
     }
-    const size_t o = ((size_t)(2 * w + ro) * P.ntot + P.col0 + k) * P.r_pad + r;
+    const size_t o = delta_elem(2 * w + ro, P.col0 + k, r, P.nrb, P.nkb);
     P.dhi[o] = h;
     P.dlo[o] = l;
 }
@@ -601,9 +602,9 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
     c->w_oz_bs.ensure((size_t)kNS * 2 * nmax * W * p_pad * 2);
     c->w_oz_S.ensure((size_t)W * nmax * nmax * sizeof(double2));
     c->w_oz_int.ensure((size_t)(2 * W * (2 + nmax) + W) * sizeof(int) + 256);
-    const size_t plane = (size_t)2 * W * c->ntot * r_pad;
-    c->w_dhi.ensure(plane * 2);
-    c->w_dlo.ensure(plane * 2);
+    const DeltaGeom dg = delta_geom(M, c->ntot, W);
+    c->w_dhi.ensure_zeroed(dg.plane * 2, c->stream);
+    c->w_dlo.ensure_zeroed(dg.plane * 2, c->stream);
     c->w_dscale.ensure((size_t)W * (sizeof(float) + sizeof(double)) + 64);
     float* inv_t = c->w_dscale.as<float>();
     double* tscale =
@@ -619,10 +620,6 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
     int* texp = ib + (size_t)2 * W * (2 + nmax);
     uint16_t* At = c->w_oz_at.as<uint16_t>();
     uint16_t* Bt = c->w_oz_bt.as<uint16_t>();
-    if (r_pad != M) {  // basis padding of the Delta planes is never written below
-        LOAF_CUDA(cudaMemsetAsync(c->w_dhi.ptr, 0, plane * 2, c->stream));
-        LOAF_CUDA(cudaMemsetAsync(c->w_dlo.ptr, 0, plane * 2, c->stream));
-    }
     LOAF_CUDA(cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kOSmem));
 
@@ -669,6 +666,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
             P.err = err;
             P.mode = 0;
             P.M = M; P.N = N; P.ntot = c->ntot; P.col0 = sd.col0; P.r_pad = r_pad; P.W = W;
+            P.nrb = dg.nrb; P.nkb = dg.nkb;
             P.rows_valid = N;
             P.cols_valid = twoN * W;
             P.row_exp = sd.oz_rowexp.as<int>();
@@ -712,6 +710,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
         P.err = err;
         P.mode = 1;
         P.M = M; P.N = N; P.ntot = c->ntot; P.col0 = sd.col0; P.r_pad = r_pad; P.W = W;
+        P.nrb = dg.nrb; P.nkb = dg.nkb;
         P.rows_valid = M;
         P.cols_valid = twoN;
         P.wexp = wexp(s);

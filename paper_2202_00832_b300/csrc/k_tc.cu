@@ -25,7 +25,6 @@
 #include "common.cuh"
 #include "tc_ptx.cuh"
 
-#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -34,62 +33,9 @@ namespace loaf {
 
 namespace {
 
-constexpr int kBK = 32;              // basis functions per stage (64-byte rows)
-constexpr int kRowB = kBK * 2;       // bytes per tile row -> SWIZZLE_64B
-constexpr int kBM = 128;             // MMA rows
-constexpr int kBNW = 128;            // walkers per tile
-constexpr int kBN = 2 * kBNW;        // MMA columns: (walker, re/im) interleaved
-constexpr int kStages = 2;
-constexpr uint32_t kTileA = kBM * kRowB;   // 8 KB
-
-// ---------------------------------------------------------------------------
-// host: TMA descriptors
-// ---------------------------------------------------------------------------
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        LOAF_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                                   cudaEnableDefault, &q));
-        LOAF_REQUIRE(p && q == cudaDriverEntryPointSuccess, LOAF_ERR_CUDA,
-                     "cuTensorMapEncodeTiled is unavailable");
-        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
-// swizzle mode matching a box row of `box_inner` 16-bit elements (64 or 128 bytes)
-CUtensorMapSwizzle swizzle_for(uint32_t box_inner) {
-    return box_inner * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-}
-
-// 16-bit row-major matrix: `rows` rows of `inner` elements, rows `ld` apart
-void map_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t ld,
-            uint32_t box_inner, uint32_t box_rows) {
-    cuuint64_t dims[2] = {inner, rows};
-    cuuint64_t strides[1] = {ld * 2};
-    cuuint32_t box[2] = {box_inner, box_rows};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims,
-                             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(box_inner),
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    LOAF_REQUIRE(r == CUDA_SUCCESS, LOAF_ERR_CUDA, "cuTensorMapEncodeTiled (2d) failed");
-}
-
-// Delta planes [2W][ntot][r_pad]: x = r, y = orbital c, z = (walker, re/im);
-// box: box_inner basis functions x one orbital x box_rows (walker, re/im) rows
-void map_delta_3d(CUtensorMap* m, const void* base, uint64_t r_pad, uint64_t ntot, uint64_t rows,
-                  uint32_t box_inner, uint32_t box_rows) {
-    cuuint64_t dims[3] = {r_pad, ntot, rows};
-    cuuint64_t strides[2] = {r_pad * 2, ntot * r_pad * 2};
-    cuuint32_t box[3] = {box_inner, 1, box_rows};
-    cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(base), dims,
-                             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(box_inner),
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    LOAF_REQUIRE(r == CUDA_SUCCESS, LOAF_ERR_CUDA, "cuTensorMapEncodeTiled (3d) failed");
-}
+constexpr int kBM = 128;             // MMA rows per CTA
+constexpr int kBNW = 128;            // walkers per LO tile
+constexpr int kBN = 2 * kBNW;        // LO MMA columns: (walker, re/im) interleaved
 
 // ---------------------------------------------------------------------------
 // 16-bit split helpers
@@ -232,6 +178,39 @@ __global__ void row_split_kernel(int M, int r_pad, const double* __restrict__ sr
     if (threadIdx.x == 0) inv[row] = (float)(1.0 / sc);
 }
 
+// One 128 x 64 operand tile from a row-major 16-bit plane (rows `ld` apart):
+// rows [row0, row0 + nvalid), columns [col0, col0 + kvalid) (kvalid a multiple
+// of 8), zero elsewhere, written as the swizzled shared-memory image.
+__device__ void write_tile(const uint16_t* __restrict__ src, long ld, long row0, int nvalid,
+                           long col0, int kvalid, uint16_t* __restrict__ dst) {
+    for (int q = threadIdx.x; q < kTileRows * 8; q += blockDim.x) {
+        const int row = q >> 3, j = q & 7;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (row < nvalid && j * 8 < kvalid)
+            v = *reinterpret_cast<const uint4*>(src + (row0 + row) * ld + col0 + j * 8);
+        *reinterpret_cast<uint4*>(dst + sw128_elem(row, j * 8)) = v;
+    }
+}
+
+// LO operand tiles: tile t (list entry {row0, nvalid, -, block}) x basis block kb
+__global__ void lo_tiles_kernel(const uint16_t* __restrict__ plane, int r_pad, int nkb,
+                                const int4* __restrict__ tiles, uint16_t* __restrict__ out) {
+    const int4 t = tiles[blockIdx.x];
+    const int kb = blockIdx.y;
+    write_tile(plane, r_pad, t.x, t.y, (long)kb * kTileK, r_pad - kb * kTileK,
+               out + ((size_t)t.w * nkb + kb) * kTileElems);
+}
+
+// Coulomb operand tiles [mt][c][kb] from the (X+1) x (ntot r_pad) plane
+__global__ void coul_tiles_kernel(const uint16_t* __restrict__ plane, int rows, int ntot, int r_pad,
+                                  int nkb, uint16_t* __restrict__ out) {
+    const int mt = blockIdx.x / ntot, c = blockIdx.x % ntot, kb = blockIdx.y;
+    const long ld = (long)ntot * r_pad;
+    write_tile(plane, ld, (long)mt * kTileRows, min(kTileRows, rows - mt * kTileRows),
+               (long)c * r_pad + (long)kb * kTileK, r_pad - kb * kTileK,
+               out + (((size_t)mt * ntot + c) * nkb + kb) * kTileElems);
+}
+
 // p = Ubar^T row . Phi_j, q = Vbar row . Phi_i (FP64), one warp per row
 __global__ void pq_kernel(int M, long rows, const double* __restrict__ U,
                           const double* __restrict__ V, const int* __restrict__ row_pair,
@@ -296,7 +275,7 @@ __global__ void delta_max_kernel(int M, int ntot, int nspin, SpinRef s0, SpinRef
 }
 
 template <bool BF16>
-__global__ void delta_split_kernel(int M, int ntot, int r_pad, int W, int nspin, SpinRef s0,
+__global__ void delta_split_kernel(int M, int ntot, int nrb, int nkb, int nspin, SpinRef s0,
                                    SpinRef s1, const double2* __restrict__ theta,
                                    const double* __restrict__ scale, uint16_t* __restrict__ hi,
                                    uint16_t* __restrict__ lo) {
@@ -305,39 +284,25 @@ __global__ void delta_split_kernel(int M, int ntot, int r_pad, int W, int nspin,
     const int i = c - sp.col0;
     const double sc = scale[w];
     const double2* th = theta + ((size_t)w * ntot + c) * M;
-    const size_t o_re = ((size_t)(2 * w) * ntot + c) * r_pad;
-    const size_t o_im = ((size_t)(2 * w + 1) * ntot + c) * r_pad;
-    for (int r = threadIdx.x; r < r_pad; r += blockDim.x) {
-        double vr = 0.0, vi = 0.0;
-        if (r < M) {
-            const double2 t = th[r];
-            vr = (t.x - sp.trial[(size_t)r * sp.N + i]) * sc;
-            vi = t.y * sc;
-        }
+    for (int r = threadIdx.x; r < M; r += blockDim.x) {
+        const double2 t = th[r];
+        const double vr = (t.x - sp.trial[(size_t)r * sp.N + i]) * sc;
+        const double vi = t.y * sc;
+        const size_t o_re = delta_elem(2 * w, c, r, nrb, nkb);
+        const size_t o_im = delta_elem(2 * w + 1, c, r, nrb, nkb);
         uint16_t h, l;
         split16<BF16>(vr, h, l);
-        hi[o_re + r] = h;
-        lo[o_re + r] = l;
+        hi[o_re] = h;
+        lo[o_re] = l;
         split16<BF16>(vi, h, l);
-        hi[o_im + r] = h;
-        lo[o_im + r] = l;
+        hi[o_im] = h;
+        lo[o_im] = l;
     }
 }
 
 // ---------------------------------------------------------------------------
 // tensor-core kernels
 // ---------------------------------------------------------------------------
-struct TCShared {
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
-    uint64_t tmem_full;
-    uint64_t tmem_empty;
-    uint64_t drain;
-    uint32_t tmem_base;
-    int abort;
-    float red[4][kBN];
-};
-
 __device__ inline uint8_t* align1024(uint8_t* p) {
     return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
@@ -351,12 +316,11 @@ __device__ inline uint8_t* align1024(uint8_t* p) {
 // the finished buffer into a double-float (hi, lo) register accumulator with
 // an error-free TwoSum, so the long (c, r) contraction is summed to ~2^-44.
 constexpr int kCBN = 128;            // columns: 64 walkers, re/im interleaved
-constexpr int kCStages = 4;
-constexpr int kCGroup = 4;           // k-chunks per TMEM accumulation chain
+constexpr int kCStages = 2;
+constexpr int kCGroup = 2;           // 64-wide k-chunks per TMEM accumulation chain
 constexpr int kCBufs = 4;            // TMEM buffers of kCBN columns
 constexpr int kCEpiWarps = 16;       // 4 per TMEM lane quarter, 32 columns each
 constexpr int kCThreads = 64 + 32 * kCEpiWarps;
-constexpr uint32_t kCTileB = kCBN * kRowB;  // 8 KB
 
 struct CoulShared {
     uint64_t full[kCStages];
@@ -369,9 +333,14 @@ struct CoulShared {
 };
 
 struct CoulParams {
+    const uint16_t* a_hi;  // operand tiles [mt][c][kb]
+    const uint16_t* a_lo;
+    const uint16_t* b_hi;  // Delta tiles [c][rb][kb]
+    const uint16_t* b_lo;
     double* part;      // [split][rows][ldp] FP64 partial sums
     int rows;          // X + 1
     int n_mt, n_wt, n_split, nk, ldp;
+    int nkb, nrb;      // basis blocks per orbital, Delta row blocks
     uint32_t idesc;
     int* err;
 };
@@ -387,13 +356,11 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
 // dJ partial tile: rows g (128) x 128 columns (64 walkers, re/im) over the
 // k-chunks [split * nk / n_split, (split+1) * nk / n_split)
 __global__ void __launch_bounds__(kCThreads, 1)
-coulomb_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
-                  const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
-                  CoulParams P) {
+coulomb_tc_kernel(CoulParams P) {
     extern __shared__ uint8_t dyn_smem[];
     __shared__ CoulShared sh;
     uint8_t* base = align1024(dyn_smem);
-    constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kCTileB;  // 32 KB
+    constexpr uint32_t kStageBytes = 4 * kTileBytes;  // A hi, A lo, B hi, B lo: 64 KB
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_units = P.n_mt * P.n_wt * P.n_split;
 
@@ -408,10 +375,6 @@ coulomb_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constan
         tc::tmem_alloc(&sh.tmem_base, kCBufs * kCBN);
         tc::tmem_relinquish();
     }
-    if (threadIdx.x == 32) {
-        tc::tma_prefetch(&mAhi); tc::tma_prefetch(&mAlo);
-        tc::tma_prefetch(&mBhi); tc::tma_prefetch(&mBlo);
-    }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -419,7 +382,7 @@ coulomb_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constan
     volatile int* abort = &sh.abort;
 
     if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer ----------------
+        // ---------------- bulk-copy producer ----------------
         int s = 0;
         uint32_t ph = 0, filled = 0, last_par = 0;
         for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
@@ -429,10 +392,13 @@ coulomb_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constan
                 if (!tc::mbar_wait(&sh.empty[s], ph ^ 1, abort)) break;
                 uint8_t* st = base + s * kStageBytes;
                 tc::mbar_arrive_expect_tx(&sh.full[s], kStageBytes);
-                tc::tma_load_2d(st, &mAhi, &sh.full[s], kc * kBK, mt * kBM);
-                tc::tma_load_2d(st + kTileA, &mAlo, &sh.full[s], kc * kBK, mt * kBM);
-                tc::tma_load_2d(st + 2 * kTileA, &mBhi, &sh.full[s], kc * kBK, wt * kCBN);
-                tc::tma_load_2d(st + 2 * kTileA + kCTileB, &mBlo, &sh.full[s], kc * kBK, wt * kCBN);
+                const int cc = kc / P.nkb, kb = kc - cc * P.nkb;
+                const size_t ao = ((size_t)mt * P.nk + kc) * kTileElems;
+                const size_t bo = (((size_t)cc * P.nrb + wt) * P.nkb + kb) * kTileElems;
+                tc::bulk_load(st, P.a_hi + ao, kTileBytes, &sh.full[s]);
+                tc::bulk_load(st + kTileBytes, P.a_lo + ao, kTileBytes, &sh.full[s]);
+                tc::bulk_load(st + 2 * kTileBytes, P.b_hi + bo, kTileBytes, &sh.full[s]);
+                tc::bulk_load(st + 3 * kTileBytes, P.b_lo + bo, kTileBytes, &sh.full[s]);
                 filled |= 1u << s;
                 last_par = (last_par & ~(1u << s)) | (ph << s);
                 if (++s == kCStages) { s = 0; ph ^= 1; }
@@ -465,12 +431,12 @@ coulomb_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constan
                     tc::tc_fence_after();
                     const uint32_t st = tc::smem_u32(base + s * kStageBytes);
 #pragma unroll
-                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                    for (int kk = 0; kk < kTileK / 16; ++kk) {
                         const uint32_t off = kk * 32;
-                        const uint64_t ahi = tc::smem_desc(st + off, kRowB);
-                        const uint64_t alo = tc::smem_desc(st + kTileA + off, kRowB);
-                        const uint64_t bhi = tc::smem_desc(st + 2 * kTileA + off, kRowB);
-                        const uint64_t blo = tc::smem_desc(st + 2 * kTileA + kCTileB + off, kRowB);
+                        const uint64_t ahi = tc::smem_desc(st + off, 128);
+                        const uint64_t alo = tc::smem_desc(st + kTileBytes + off, 128);
+                        const uint64_t bhi = tc::smem_desc(st + 2 * kTileBytes + off, 128);
+                        const uint64_t blo = tc::smem_desc(st + 3 * kTileBytes + off, 128);
                         const uint32_t acc = (kc > g0 || kk > 0) ? 1u : 0u;
                         tc::mma_f16(d, ahi, bhi, P.idesc, acc);
                         tc::mma_f16(d, ahi, blo, P.idesc, 1u);
@@ -539,7 +505,14 @@ coulomb_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constan
 }
 
 struct LoParams {
-    const int4* pt;       // pair tiles {row0, nvalid, ci, cj}
+    const uint16_t* u_hi;  // operand tiles [tile][kb]
+    const uint16_t* u_lo;
+    const uint16_t* v_hi;
+    const uint16_t* v_lo;
+    const uint16_t* d_hi;  // Delta tiles [c][rb][kb]
+    const uint16_t* d_lo;
+    int nrb;
+    const int4* pt;       // pair tiles {row0, nvalid, ci << 16 | cj, tile block}
     const float4* rowc;   // per packed row {inv_su, inv_sv, p, q}
     const float* inv_t;   // per walker inverse Delta scale
     double2* part;        // [n_pt][ldp] per pair tile and walker
@@ -559,10 +532,9 @@ struct LoParams {
 // TMA ring holds half-stages of one side each, 64 basis functions deep
 // (128-byte rows: 2 x 16 KB weight tiles + 2 x 16 KB Delta half-tiles = 64 KB),
 // three of them, consumed a, b, a, b, ...
-constexpr int kLBK = 64;                                     // basis functions per k-step
-constexpr int kLRowB = kLBK * 2;                             // 128-byte rows -> SWIZZLE_128B
-constexpr uint32_t kLTileA = kBM * kLRowB;                   // 16 KB
-constexpr uint32_t kLTileBh = (kBN / 2) * kLRowB;            // 16 KB: 128 Delta rows
+constexpr int kLBK = kTileK;                                 // basis functions per k-step
+constexpr uint32_t kLTileA = kTileBytes;                     // 16 KB: 128 weight rows
+constexpr uint32_t kLTileBh = kTileBytes;                    // 16 KB: 128 Delta rows
 constexpr uint32_t kLSlotBytes = 2 * kLTileA + 2 * kLTileBh;  // 64 KB
 constexpr int kLSlots = 3;
 constexpr int kLEpiWarps = 16;
@@ -584,10 +556,7 @@ struct LoShared {
 // to the even CTA's full barrier; warps 2-17 the epilogue (four per TMEM lane
 // quarter, each draining 2 of the 8 32-column chunks).
 __global__ void __launch_bounds__(kLThreads, 1)
-lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_constant__ CUtensorMap mUlo,
-                      const __grid_constant__ CUtensorMap mVhi, const __grid_constant__ CUtensorMap mVlo,
-                      const __grid_constant__ CUtensorMap mDhi, const __grid_constant__ CUtensorMap mDlo,
-                      LoParams P) {
+lo_exchange_tc_kernel(LoParams P) {
     extern __shared__ uint8_t dyn_smem[];
     __shared__ LoShared sh;
     uint8_t* base = align1024(dyn_smem);
@@ -614,10 +583,6 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
         tc::tmem_alloc_pair(&sh.tmem_base, 2 * kBN);
         tc::tmem_relinquish_pair();
     }
-    if (threadIdx.x == 32) {
-        tc::tma_prefetch(&mUhi); tc::tma_prefetch(&mUlo); tc::tma_prefetch(&mVhi);
-        tc::tma_prefetch(&mVlo); tc::tma_prefetch(&mDhi); tc::tma_prefetch(&mDlo);
-    }
     tc::tc_fence_before();
     __syncthreads();
     tc::cluster_sync();  // both CTAs' barriers initialised before any remote arrive
@@ -626,24 +591,25 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
     volatile int* abort = &sh.abort;
 
     if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer (both CTAs) ----------------
+        // ---------------- bulk-copy producer (both CTAs) ----------------
         int s = 0;
         uint32_t ph = 0, filled = 0, last_par = 0;
         for (int u = cid; u < n_units && !*abort; u += n_cl) {
             const int4 t = P.pt[2 * (u / P.n_wt) + rank];
-            const int wt = u % P.n_wt;
-            const int col = wt * kBN + (int)rank * (kBN / 2);
+            const int rb = 2 * (u % P.n_wt) + (int)rank;  // this CTA's 128 Delta rows
             for (int h = 0; h < 2 * P.nk; ++h) {
                 if (!tc::mbar_wait_cluster(&sh.empty[s], ph ^ 1, abort)) break;
                 uint8_t* st = base + s * kLSlotBytes;
                 tc::mbar_arrive_expect_tx(&sh.full[s], kLSlotBytes);
-                const int x = (h >> 1) * kLBK;
+                const int kb = h >> 1;
                 const bool side_b = h & 1;
-                tc::tma_load_2d(st, side_b ? &mVhi : &mUhi, &sh.full[s], x, t.x);
-                tc::tma_load_2d(st + kLTileA, side_b ? &mVlo : &mUlo, &sh.full[s], x, t.x);
-                const int orb = side_b ? t.z : t.w;
-                tc::tma_load_3d(st + 2 * kLTileA, &mDhi, &sh.full[s], x, orb, col);
-                tc::tma_load_3d(st + 2 * kLTileA + kLTileBh, &mDlo, &sh.full[s], x, orb, col);
+                const size_t ao = ((size_t)t.w * P.nk + kb) * kTileElems;
+                const int orb = side_b ? (t.z >> 16) : (t.z & 0xffff);
+                const size_t bo = (((size_t)orb * P.nrb + rb) * P.nk + kb) * kTileElems;
+                tc::bulk_load(st, (side_b ? P.v_hi : P.u_hi) + ao, kLTileA, &sh.full[s]);
+                tc::bulk_load(st + kLTileA, (side_b ? P.v_lo : P.u_lo) + ao, kLTileA, &sh.full[s]);
+                tc::bulk_load(st + 2 * kLTileA, P.d_hi + bo, kLTileBh, &sh.full[s]);
+                tc::bulk_load(st + 2 * kLTileA + kLTileBh, P.d_lo + bo, kLTileBh, &sh.full[s]);
                 filled |= 1u << s;
                 last_par = (last_par & ~(1u << s)) | (ph << s);
                 if (++s == kLSlots) { s = 0; ph ^= 1; }
@@ -695,10 +661,10 @@ lo_exchange_tc_kernel(const __grid_constant__ CUtensorMap mUhi, const __grid_con
 #pragma unroll
                 for (int kk = 0; kk < kLBK / 16; ++kk) {
                     const uint32_t off = kk * 32;
-                    const uint64_t whi = tc::smem_desc(st + off, kLRowB);
-                    const uint64_t wlo = tc::smem_desc(st + kLTileA + off, kLRowB);
-                    const uint64_t dhi = tc::smem_desc(st + 2 * kLTileA + off, kLRowB);
-                    const uint64_t dlo = tc::smem_desc(st + 2 * kLTileA + kLTileBh + off, kLRowB);
+                    const uint64_t whi = tc::smem_desc(st + off, 128);
+                    const uint64_t wlo = tc::smem_desc(st + kLTileA + off, 128);
+                    const uint64_t dhi = tc::smem_desc(st + 2 * kLTileA + off, 128);
+                    const uint64_t dlo = tc::smem_desc(st + 2 * kLTileA + kLTileBh + off, 128);
                     const uint32_t acc = (h > 1 || kk > 0) ? 1u : 0u;
                     tc::mma_f16_pair(d, whi, dhi, P.idesc, acc);
                     tc::mma_f16_pair(d, whi, dlo, P.idesc, 1u);
@@ -897,11 +863,23 @@ void ensure_coulomb_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     LOAF_LAUNCH_CHECK();
     trial_coulomb_kernel<<<rows, 256, 0, c->stream>>>(c->M, c->X, c->nspin, s0, s1, mx.J0.as<double>());
     LOAF_LAUNCH_CHECK();
+    // operand tiles [mt][c][kb]; the row-major staging planes are then dropped
+    mx.nkb = ceil_div(c->M, kTileK);
+    mx.n_mt = ceil_div(rows, kTileRows);
+    const size_t tiles_bytes = (size_t)mx.n_mt * c->ntot * mx.nkb * kTileBytes;
+    mx.Lb_hi.ensure(tiles_bytes);
+    mx.Lb_lo.ensure(tiles_bytes);
+    const dim3 tg(mx.n_mt * c->ntot, mx.nkb);
+    coul_tiles_kernel<<<tg, 256, 0, c->stream>>>(mx.L_hi.as<uint16_t>(), rows, c->ntot, mx.r_pad, mx.nkb,
+                                                mx.Lb_hi.as<uint16_t>());
+    coul_tiles_kernel<<<tg, 256, 0, c->stream>>>(mx.L_lo.as<uint16_t>(), rows, c->ntot, mx.r_pad, mx.nkb,
+                                                mx.Lb_lo.as<uint16_t>());
+    LOAF_LAUNCH_CHECK();
     LOAF_CUDA(cudaMemcpyAsync(&mx.E1_0, mx.J0.as<double>() + c->X, sizeof(double),
                               cudaMemcpyDeviceToHost, c->stream));
     LOAF_CUDA(cudaStreamSynchronize(c->stream));
-    map_2d(&mx.mapL_hi, mx.L_hi.ptr, mx.kflat, rows, mx.kflat, kBK, kBM);
-    map_2d(&mx.mapL_lo, mx.L_lo.ptr, mx.kflat, rows, mx.kflat, kBK, kBM);
+    mx.L_hi.release();
+    mx.L_lo.release();
     mx.coul_ready = true;
 }
 
@@ -992,16 +970,16 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
             mx.h_order.push_back(gpair);
             pt0[gpair] = (int)tiles.size();
             int cnt = 0;
+            const int cij = ((sd.col0 + pt.i[n]) << 16) | (sd.col0 + pt.j[n]);
             for (int k0 = 0; k0 < pt.K[n]; k0 += kBM) {
                 tiles.push_back(make_int4((int)(row_base + pt.off[n] + k0), std::min(kBM, pt.K[n] - k0),
-                                          sd.col0 + pt.i[n], sd.col0 + pt.j[n]));
+                                          cij, (int)tiles.size()));
                 ++cnt;
             }
             // the CTA-pair kernel takes a pair's tiles two at a time: an odd
-            // count gets an empty tile (no valid rows, partials exactly zero)
+            // count gets an empty tile (no valid rows: zero operand, zero partials)
             if (cnt & 1) {
-                tiles.push_back(make_int4((int)(row_base + pt.off[n]), 0, sd.col0 + pt.i[n],
-                                          sd.col0 + pt.j[n]));
+                tiles.push_back(make_int4((int)(row_base + pt.off[n]), 0, cij, (int)tiles.size()));
                 ++cnt;
             }
             npt[gpair] = cnt;
@@ -1039,10 +1017,22 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     mx.h_pw = pw;
     mx.h_e0 = e0;
     mx.screen_built = -1;
-    map_2d(&mx.mapU_hi, mx.U_hi.ptr, mx.r_pad, Rb, mx.r_pad, kLBK, kBM);
-    map_2d(&mx.mapU_lo, mx.U_lo.ptr, mx.r_pad, Rb, mx.r_pad, kLBK, kBM);
-    map_2d(&mx.mapV_hi, mx.V_hi.ptr, mx.r_pad, Rb, mx.r_pad, kLBK, kBM);
-    map_2d(&mx.mapV_lo, mx.V_lo.ptr, mx.r_pad, Rb, mx.r_pad, kLBK, kBM);
+    // operand tiles [tile][kb]; the row-major staging planes are then dropped
+    mx.nkb = ceil_div(M, kTileK);
+    if (mx.n_pt > 0) {
+        const size_t tb = (size_t)mx.n_pt * mx.nkb * kTileBytes;
+        const dim3 tg(mx.n_pt, mx.nkb);
+        DevBuf* dst[4] = {&mx.Ub_hi, &mx.Ub_lo, &mx.Vb_hi, &mx.Vb_lo};
+        DevBuf* src[4] = {&mx.U_hi, &mx.U_lo, &mx.V_hi, &mx.V_lo};
+        for (int q = 0; q < 4; ++q) {
+            dst[q]->ensure(tb);
+            lo_tiles_kernel<<<tg, 256, 0, c->stream>>>(src[q]->as<uint16_t>(), mx.r_pad, mx.nkb,
+                                                      mx.pt.as<int4>(), dst[q]->as<uint16_t>());
+            LOAF_LAUNCH_CHECK();
+        }
+        LOAF_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    for (DevBuf* b : {&mx.U_hi, &mx.U_lo, &mx.V_hi, &mx.V_lo}) b->release();
     mx.lo_ready = true;
 }
 
@@ -1081,7 +1071,7 @@ void ensure_screened_tiles(loaf_ctx* c, MixedOps& mx) {
 }
 
 constexpr size_t kCoulSmem =
-    kCStages * (2 * kTileA + 2 * kCTileB) + 32 * kCEpiWarps * 32 * sizeof(float) + 1024;
+    kCStages * 4 * kTileBytes + 32 * kCEpiWarps * 32 * sizeof(float) + 1024;
 constexpr size_t kLoSmem = kLSlots * kLSlotBytes + 1024;
 
 // CTA pairs of the LO kernel that fit on the GPU at once (the persistent grid):
@@ -1132,40 +1122,43 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
     // written by the tensor-core Theta stage when theta is NULL
     const int n_wt = ceil_div(W, kBNW);
     const int Wpad = n_wt * kBNW;
-    const size_t plane = (size_t)2 * W * c->ntot * mx.r_pad;
+    const DeltaGeom dg = delta_geom(c->M, c->ntot, W);
     c->w_dscale.ensure((size_t)W * (sizeof(float) + sizeof(double)) + 64);
     float* inv_t = c->w_dscale.as<float>();
     double* scale = reinterpret_cast<double*>(c->w_dscale.as<uint8_t>() + ((W * sizeof(float) + 15) / 16) * 16);
     c->w_flag.ensure(16);
     int* err = c->w_flag.as<int>();
     if (theta) {
-        c->w_dhi.ensure(plane * 2);
-        c->w_dlo.ensure(plane * 2);
+        c->w_dhi.ensure_zeroed(dg.plane * 2, c->stream);
+        c->w_dlo.ensure_zeroed(dg.plane * 2, c->stream);
         LOAF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
         SpinRef s0 = spin_ref(c->sp[0]), s1 = c->nspin > 1 ? spin_ref(c->sp[1]) : s0;
         StageScope dsc(c, "delta_split", 2);
         delta_max_kernel<<<W, 256, 0, c->stream>>>(c->M, c->ntot, c->nspin, s0, s1, theta, inv_t, scale);
         LOAF_LAUNCH_CHECK();
         if (bf16)
-            delta_split_kernel<true><<<W * c->ntot, 128, 0, c->stream>>>(c->M, c->ntot, mx.r_pad, W, c->nspin,
-                s0, s1, theta, scale, c->w_dhi.as<uint16_t>(), c->w_dlo.as<uint16_t>());
+            delta_split_kernel<true><<<W * c->ntot, 128, 0, c->stream>>>(c->M, c->ntot, dg.nrb, dg.nkb,
+                c->nspin, s0, s1, theta, scale, c->w_dhi.as<uint16_t>(), c->w_dlo.as<uint16_t>());
         else
-            delta_split_kernel<false><<<W * c->ntot, 128, 0, c->stream>>>(c->M, c->ntot, mx.r_pad, W, c->nspin,
-                s0, s1, theta, scale, c->w_dhi.as<uint16_t>(), c->w_dlo.as<uint16_t>());
+            delta_split_kernel<false><<<W * c->ntot, 128, 0, c->stream>>>(c->M, c->ntot, dg.nrb, dg.nkb,
+                c->nspin, s0, s1, theta, scale, c->w_dhi.as<uint16_t>(), c->w_dlo.as<uint16_t>());
         LOAF_LAUNCH_CHECK();
     }
     const uint32_t idesc = tc::idesc_f16(2 * kBM, kBN, bf16);  // pair MMA: M = 256
 
     if (e_out) {
         // ---- Coulomb + one-body on the tensor cores ----
-        CUtensorMap mBhi, mBlo;
-        map_2d(&mBhi, c->w_dhi.ptr, mx.kflat, 2L * W, mx.kflat, kBK, kCBN);
-        map_2d(&mBlo, c->w_dlo.ptr, mx.kflat, 2L * W, mx.kflat, kBK, kCBN);
         CoulParams P;
+        P.a_hi = mx.Lb_hi.as<uint16_t>();
+        P.a_lo = mx.Lb_lo.as<uint16_t>();
+        P.b_hi = c->w_dhi.as<uint16_t>();
+        P.b_lo = c->w_dlo.as<uint16_t>();
+        P.nkb = dg.nkb;
+        P.nrb = dg.nrb;
         P.rows = c->X + 1;
-        P.n_mt = ceil_div(P.rows, kBM);
+        P.n_mt = mx.n_mt;
         P.n_wt = ceil_div(2L * W, kCBN);
-        P.nk = (int)((mx.kflat + kBK - 1) / kBK);
+        P.nk = c->ntot * dg.nkb;
         const int tiles = P.n_mt * P.n_wt;
         P.n_split = std::max(1, std::min(ceil_div(P.nk, kCGroup), (3 * c->sm_count + tiles - 1) / tiles));
         P.ldp = P.n_wt * kCBN;
@@ -1177,8 +1170,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         LOAF_CUDA(cudaFuncSetAttribute(coulomb_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kCoulSmem));
         StageScope csc(c, "coulomb_tc", 1);
-        coulomb_tc_kernel<<<std::min(units, c->sm_count), kCThreads, kCoulSmem, c->stream>>>(
-            mx.mapL_hi, mx.mapL_lo, mBhi, mBlo, P);
+        coulomb_tc_kernel<<<std::min(units, c->sm_count), kCThreads, kCoulSmem, c->stream>>>(P);
         LOAF_LAUNCH_CHECK();
         csc.end();
         StageScope rsc(c, "coulomb_reduce", 1);
@@ -1200,10 +1192,14 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         const double* list_pw = screened ? mx.s_pw.as<double>() : mx.pair_w.as<double>();
         const double list_ek0 = screened ? mx.s_EK0 : mx.EK0;
         if (n_pt > 0) {
-            CUtensorMap mDhi, mDlo;
-            map_delta_3d(&mDhi, c->w_dhi.ptr, mx.r_pad, c->ntot, 2L * W, kLBK, kBN / 2);
-            map_delta_3d(&mDlo, c->w_dlo.ptr, mx.r_pad, c->ntot, 2L * W, kLBK, kBN / 2);
             LoParams P;
+            P.u_hi = mx.Ub_hi.as<uint16_t>();
+            P.u_lo = mx.Ub_lo.as<uint16_t>();
+            P.v_hi = mx.Vb_hi.as<uint16_t>();
+            P.v_lo = mx.Vb_lo.as<uint16_t>();
+            P.d_hi = c->w_dhi.as<uint16_t>();
+            P.d_lo = c->w_dlo.as<uint16_t>();
+            P.nrb = dg.nrb;
             P.pt = tile_list;
             P.rowc = mx.row_c.as<float4>();
             P.inv_t = inv_t;
@@ -1211,7 +1207,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             P.n_wt = n_wt;
             P.W = W;
             P.ldp = Wpad;
-            P.nk = ceil_div(mx.r_pad, kLBK);
+            P.nk = dg.nkb;
             P.idesc = idesc;
             P.err = err;
             c->w_lopart.ensure((size_t)n_pt * Wpad * sizeof(double2));
@@ -1231,8 +1227,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             StageScope lsc(c, "lo_exchange_tc", 1);
-            LOAF_CUDA(cudaLaunchKernelEx(&cfg, lo_exchange_tc_kernel, mx.mapU_hi, mx.mapU_lo,
-                                         mx.mapV_hi, mx.mapV_lo, mDhi, mDlo, P));
+            LOAF_CUDA(cudaLaunchKernelEx(&cfg, lo_exchange_tc_kernel, P));
             LOAF_LAUNCH_CHECK();
         }
         c->w_lopart.ensure(16);
