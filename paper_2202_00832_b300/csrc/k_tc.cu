@@ -763,21 +763,28 @@ lo_exchange_tc_kernel(LoParams P) {
 // ---------------------------------------------------------------------------
 
 // E1 = E1_0 + dE1,  E_J = 1/2 sum_g (J0_g + dJ_g)^2,  dJ from the split partials
+// The reductions run on a (walker block, slice) grid: slice sl of the rows g
+// (Coulomb) or pairs n (exchange) sums into red[sl][w]; a final pass adds the
+// slices in order, so the result does not depend on the launch.
+constexpr int kRedSlices = 16;
+
+// sum_g (J0_g + dJ_g)^2 over the rows of this slice, dJ from the split partials
 __global__ void coulomb_tc_reduce_kernel(int X, int W, int n_split, int ldp,
                                          const double* __restrict__ part,
                                          const float* __restrict__ inv_s,
                                          const float* __restrict__ inv_t,
-                                         const double* __restrict__ J0, double E1_0,
-                                         double2* __restrict__ e1, double2* __restrict__ ej) {
+                                         const double* __restrict__ J0,
+                                         double2* __restrict__ red_out) {
     // 32 walkers x 8 row groups
     __shared__ double2 red[8][32];
     const int wl = threadIdx.x & 31, gg = threadIdx.x >> 5;
-    const int w = blockIdx.x * 32 + wl;
+    const int w = blockIdx.x * 32 + wl, sl = blockIdx.y, nsl = gridDim.y;
+    const int g0 = (int)((long)sl * X / nsl), g1 = (int)((long)(sl + 1) * X / nsl);
     double2 acc = make_double2(0.0, 0.0);
     const size_t plane = (size_t)(X + 1) * ldp;
     if (w < W) {
         const double it = inv_t[w];
-        for (int g = gg; g < X; g += 8) {
+        for (int g = g0 + gg; g < g1; g += 8) {
             double re = 0.0, im = 0.0;
             for (int s = 0; s < n_split; ++s) {
                 const double2 v = *reinterpret_cast<const double2*>(part + s * plane + (size_t)g * ldp + 2 * w);
@@ -794,30 +801,47 @@ __global__ void coulomb_tc_reduce_kernel(int X, int W, int n_split, int ldp,
     if (gg == 0 && w < W) {
         double2 t = make_double2(0.0, 0.0);
         for (int k = 0; k < 8; ++k) t = cadd(t, red[k][wl]);
-        ej[w] = cscale(t, 0.5);
-        double re = 0.0, im = 0.0;
-        for (int s = 0; s < n_split; ++s) {
-            const double2 v = *reinterpret_cast<const double2*>(part + s * plane + (size_t)X * ldp + 2 * w);
-            re += v.x;
-            im += v.y;
-        }
-        const double f = (double)inv_s[X] * inv_t[w];
-        e1[w] = make_double2(E1_0 + re * f, im * f);
+        red_out[(size_t)sl * W + w] = t;
     }
 }
 
-// per pair: e_n(w) = e0_n + sum over its tiles; E_K(w) = EK0 + sum_n pw_n de_n(w)
+// E_J = 1/2 sum over slices; E1 = E1_0 + the one-body row X
+__global__ void coulomb_tc_final_kernel(int X, int W, int n_split, int ldp, int nsl,
+                                        const double* __restrict__ part,
+                                        const float* __restrict__ inv_s,
+                                        const float* __restrict__ inv_t, double E1_0,
+                                        const double2* __restrict__ red, double2* __restrict__ e1,
+                                        double2* __restrict__ ej) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    double2 t = make_double2(0.0, 0.0);
+    for (int sl = 0; sl < nsl; ++sl) t = cadd(t, red[(size_t)sl * W + w]);
+    ej[w] = cscale(t, 0.5);
+    const size_t plane = (size_t)(X + 1) * ldp;
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < n_split; ++s) {
+        const double2 v = *reinterpret_cast<const double2*>(part + s * plane + (size_t)X * ldp + 2 * w);
+        re += v.x;
+        im += v.y;
+    }
+    const double f = (double)inv_s[X] * inv_t[w];
+    e1[w] = make_double2(E1_0 + re * f, im * f);
+}
+
+// per pair of this slice: e_n(w) = e0_n + sum over its tiles; the slice's
+// share of E_K - EK0 = sum_n pw_n de_n(w)
 __global__ void lo_tc_reduce_kernel(int n_pairs, int W, int ldp, const int* __restrict__ pt0,
                                     const int* __restrict__ npt, const double* __restrict__ pw,
-                                    const double* __restrict__ e0, double EK0,
-                                    const double2* __restrict__ part, double2* __restrict__ ek,
+                                    const double* __restrict__ e0,
+                                    const double2* __restrict__ part, double2* __restrict__ red_out,
                                     double2* __restrict__ e_pairs) {
     __shared__ double2 red[8][32];
     const int wl = threadIdx.x & 31, gg = threadIdx.x >> 5;
-    const int w = blockIdx.x * 32 + wl;
+    const int w = blockIdx.x * 32 + wl, sl = blockIdx.y, nsl = gridDim.y;
+    const int n0 = (int)((long)sl * n_pairs / nsl), n1 = (int)((long)(sl + 1) * n_pairs / nsl);
     double2 acc = make_double2(0.0, 0.0);
     if (w < W) {
-        for (int n = gg; n < n_pairs; n += 8) {
+        for (int n = n0 + gg; n < n1; n += 8) {
             double2 d = make_double2(0.0, 0.0);
             for (int k = 0; k < npt[n]; ++k) d = cadd(d, part[(size_t)(pt0[n] + k) * ldp + w]);
             if (e_pairs) e_pairs[(size_t)n * W + w] = make_double2(e0[n] + d.x, d.y);
@@ -826,11 +850,21 @@ __global__ void lo_tc_reduce_kernel(int n_pairs, int W, int ldp, const int* __re
     }
     red[gg][wl] = acc;
     __syncthreads();
-    if (gg == 0 && w < W && ek) {
-        double2 t = make_double2(EK0, 0.0);
+    if (gg == 0 && w < W) {
+        double2 t = make_double2(0.0, 0.0);
         for (int k = 0; k < 8; ++k) t = cadd(t, red[k][wl]);
-        ek[w] = t;
+        red_out[(size_t)sl * W + w] = t;
     }
+}
+
+// E_K(w) = EK0 + the slices in order
+__global__ void lo_tc_final_kernel(int W, int nsl, double EK0, const double2* __restrict__ red,
+                                   double2* __restrict__ ek) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    double2 t = make_double2(EK0, 0.0);
+    for (int sl = 0; sl < nsl; ++sl) t = cadd(t, red[(size_t)sl * W + w]);
+    ek[w] = t;
 }
 
 SpinRef spin_ref(const SpinData& s) {
@@ -1173,10 +1207,15 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         coulomb_tc_kernel<<<std::min(units, c->sm_count), kCThreads, kCoulSmem, c->stream>>>(P);
         LOAF_LAUNCH_CHECK();
         csc.end();
-        StageScope rsc(c, "coulomb_reduce", 1);
-        coulomb_tc_reduce_kernel<<<ceil_div(W, 32), 256, 0, c->stream>>>(
+        StageScope rsc(c, "coulomb_reduce", 2);
+        c->w_red.ensure((size_t)kRedSlices * W * sizeof(double2));
+        coulomb_tc_reduce_kernel<<<dim3(ceil_div(W, 32), kRedSlices), 256, 0, c->stream>>>(
             c->X, W, P.n_split, P.ldp, P.part, mx.L_inv.as<float>(), inv_t, mx.J0.as<double>(),
-            mx.E1_0, e_out, e_out + W);
+            c->w_red.as<double2>());
+        LOAF_LAUNCH_CHECK();
+        coulomb_tc_final_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
+            c->X, W, P.n_split, P.ldp, kRedSlices, P.part, mx.L_inv.as<float>(), inv_t, mx.E1_0,
+            c->w_red.as<double2>(), e_out, e_out + W);
         LOAF_LAUNCH_CHECK();
     }
     if (mode == LOAF_MODE_LO) {
@@ -1231,11 +1270,18 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             LOAF_LAUNCH_CHECK();
         }
         c->w_lopart.ensure(16);
-        StageScope lrs(c, "lo_reduce", 1);
-        lo_tc_reduce_kernel<<<ceil_div(W, 32), 256, 0, c->stream>>>(
-            mx.n_pairs, W, Wpad, list_pt0, list_npt, list_pw, mx.e0.as<double>(), list_ek0,
-            c->w_lopart.as<double2>(), ek, e_pairs);
+        StageScope lrs(c, "lo_reduce", ek ? 2 : 1);
+        const int nsl = std::max(1, std::min(kRedSlices, mx.n_pairs));
+        c->w_red.ensure((size_t)kRedSlices * W * sizeof(double2));
+        lo_tc_reduce_kernel<<<dim3(ceil_div(W, 32), nsl), 256, 0, c->stream>>>(
+            mx.n_pairs, W, Wpad, list_pt0, list_npt, list_pw, mx.e0.as<double>(),
+            c->w_lopart.as<double2>(), c->w_red.as<double2>(), e_pairs);
         LOAF_LAUNCH_CHECK();
+        if (ek) {
+            lo_tc_final_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(W, nsl, list_ek0,
+                                                                      c->w_red.as<double2>(), ek);
+            LOAF_LAUNCH_CHECK();
+        }
     } else if (e_out) {
         // full mode: Coulomb on the tensor cores, exchange in FP64
         StageScope fsc(c, "exchange_full_fp64", c->nspin + 1);
