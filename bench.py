@@ -122,6 +122,22 @@ class ClockSampler:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
+PROFILE_TRAFFIC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
+                               "lo_exchange_tc_pentacene_M440_W1024_dram.md")
+
+
+def lo_traffic(wl, W, args):
+    """DRAM bytes per launch of the LO kernel from the committed one-pass ncu capture,
+    for the configuration it was taken on (else None)."""
+    if wl is not synth.PENTACENE_440 or W != 1024 or args.threshold != 1e-4 \
+            or args.precision != "fp16x3" or not os.path.exists(PROFILE_TRAFFIC):
+        return None, None
+    for line in open(PROFILE_TRAFFIC):
+        if line.startswith("traffic_bytes_per_launch"):
+            return float(line.split("=")[1]) / 1e9, "GB per launch, ncu one-pass capture (profiles/)"
+    return None, None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -280,9 +296,11 @@ def run_ours(args, rank, world, local):
     per_launch_ms = {k: v[0] / max(v[1], 1) for k, v in kernels.items()}
     # algorithmic work per launch (one launch covers the W-walker batch)
     lo_flops = 8.0 * M * sum_k * W                      # a = Ubar^T Theta_j, b = Vbar Theta_i
-    n_tiles = sum((int(k) + 127) // 128 for k in msvd)
-    lo_issued = (3 * 2 * 2 * 128 * 256 * int(((M + 7) // 8 * 8 + 31) // 32 * 32) * int(n_tiles)
-                 * int((W + 127) // 128))
+    # issued MMA flops: pairs padded to an even number of 128-row tiles, 64-deep
+    # basis blocks, 256-column walker tiles, a and b sides, three hi/lo products
+    n_tiles = sum(2 * (((int(k) + 127) // 128 + 1) // 2) for k in msvd)
+    lo_issued = (n_tiles * 128 * 2 * 3 * 2 * (64 * ((M + 63) // 64))
+                 * (256 * ((W + 127) // 128)))
     coul_flops = 4.0 * (X + 1) * N * M * W            # dJ_g = sum_ir Lbar_gir Delta_ri (complex)
     theta_flops = (4.0 * N * N * M + 8.0 / 3.0 * N ** 3 + 8.0 * M * N * N) * W
     fp64_peak_tflops = 1.25  # nominal B300 FP64 (2 DFMA / clk / SM class figure)
@@ -299,9 +317,21 @@ def run_ours(args, rank, world, local):
     if "lo_exchange_tc" in per_launch_ms:
         r = tc_roof("lo_exchange_tc", lo_flops)
         r["issued_tflops"] = lo_issued / (per_launch_ms["lo_exchange_tc"] / 1e3) / 1e12
+        r["issued_frac_of_burst"] = r["issued_tflops"] / peaks["bf16_tflops"]
+        r["traffic"], r["traffic_source"] = lo_traffic(wl, W, args)
         rooflines["lo_exchange_tc"] = r
     if "coulomb_tc" in per_launch_ms:
         rooflines["coulomb_tc"] = tc_roof("coulomb_tc", coul_flops)
+    if "inverse_fp64" in per_launch_ms:
+        # Gauss-Jordan inverse of the complex N x N overlap: N^3 complex FMAs (8 flops)
+        # per walker and spin (one spin for a closed shell)
+        t = per_launch_ms["inverse_fp64"] / 1e3
+        n3 = N ** 3 if mol.closed_shell else mol.n_alpha ** 3 + mol.n_beta ** 3
+        ach = 8.0 * n3 * W / t / 1e12
+        rooflines["inverse_fp64"] = {"kernel": "gauss_jordan", "bound": "alu", "achieved": ach,
+                                     "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                                     "frac": ach / fp64_peak_tflops, "traffic": None,
+                                     "peak_source": "nominal FP64 ALU peak of B300"}
     if "theta_fp64" in per_launch_ms:
         t = per_launch_ms["theta_fp64"] / 1e3
         ach = theta_flops / t / 1e12
@@ -346,8 +376,9 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": f"{args.precision}: fp16 hi+lo x3 tcgen05 (fp32 acc) contractions; fp64 "
-                 f"overlap/LU/Theta/reductions" if args.precision != "fp64" else "f64",
+        "dtype": f"{args.precision}: 16-bit hi+lo x3 tcgen05 contractions (fp32 acc); overlap and "
+                 f"Theta as exact 7-bit slice products on tcgen05; f64 inverse/log-det/reductions"
+                 if args.precision != "fp64" else "f64",
         "data": "synthetic",
         "config": {"workload": wl.name + (" (pentacene-scale acene ribbon)" if wl is synth.PENTACENE_440
                                           else ""), "M": M, "N_occ": N,
