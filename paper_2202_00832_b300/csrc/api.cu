@@ -245,6 +245,9 @@ loaf_status loaf_destroy(loaf_ctx* c) {
                             &c->w_lopart, &c->w_red, &c->w_flag, &c->d_keep, &c->w_oz_at, &c->w_oz_bs,
                             &c->w_oz_bt, &c->w_oz_S, &c->w_oz_int})
         b->release();
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    for (cudaEvent_t e : {c->ev_start, c->ev_copied[0], c->ev_copied[1], c->ev_free[0], c->ev_free[1]})
+        if (e) cudaEventDestroy(e);
     if (c->cublas) cublasDestroy(c->cublas);
     if (c->cusolver) cusolverDnDestroy(c->cusolver);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -336,77 +339,126 @@ loaf_status walkers_theta(loaf_ctx* c, int W, const void* phi, void* theta_out, 
     return st;
 }
 
+namespace {
+
+__global__ void flag_or_kernel(const int* __restrict__ flag, int* __restrict__ acc) {
+    if (*flag) *acc = 1;
+}
+
+// Theta, the energy terms and finalize for W walkers at dphi; the results go
+// to de / dld / dst (device), the worst walker status to *dbad and any
+// pipeline timeout to *dtimeout.
+void energy_batch(loaf_ctx* c, int W, const double2* dphi, int mode, int precision, double2* de,
+                  double2* dld, int* dst, int* dbad, int* dtimeout) {
+    // the LO split-precision path forms Delta on the tensor cores; the FP64
+    // path and the full mode use the FP64 Theta kernel
+    const bool tc_theta = precision != LOAF_PREC_FP64 && mode == LOAF_MODE_LO;
+    if (tc_theta) {
+        run_theta_tc(c, W, dphi, precision);
+    } else {
+        StageScope sc(c, "theta_fp64", c->nspin);
+        stage_theta(c, W, dphi);
+    }
+    double2* e1 = c->w_out.as<double2>();
+    double2* ej = e1 + W;
+    double2* ek = ej + W;
+    if (precision == LOAF_PREC_FP64) {
+        {
+            StageScope sc(c, "coulomb_fp64", 2);
+            run_coulomb_fp64(c, W, c->w_theta.as<double2>(), e1);
+        }
+        if (mode == LOAF_MODE_FULL) {
+            StageScope sc(c, "exchange_full_fp64", c->nspin + 1);
+            run_energy_fp64_full(c, W, c->w_theta.as<double2>(), ek);
+        } else {
+            StageScope sc(c, "exchange_lo_fp64", 2 * c->nspin);
+            run_energy_fp64_lo(c, W, c->w_theta.as<double2>(), ek, c->w_part.as<double2>());
+        }
+    } else {
+        run_energy_mixed(c, W, mode, precision, tc_theta ? nullptr : c->w_theta.as<double2>(),
+                         e1, nullptr);
+    }
+    StageScope fsc(c, "finalize_d2h", precision != LOAF_PREC_FP64 ? 2 : 1);
+    finalize_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
+        W, c->nspin, c->sp[0].mult, c->nspin > 1 ? c->sp[1].mult : 0.0, c->e0,
+        c->w_logdet.as<double2>(), c->w_status.as<int>(), e1, ej, ek, de, dld, dst, dbad);
+    LOAF_LAUNCH_CHECK();
+    if (precision != LOAF_PREC_FP64) {
+        flag_or_kernel<<<1, 1, 0, c->stream>>>(c->w_flag.as<int>(), dtimeout);
+        LOAF_LAUNCH_CHECK();
+    }
+}
+
+// walkers per upload chunk for a host array of W walkers (0: one piece)
+int host_chunk(int W) {
+    if (W < 512) return 0;
+    return ceil_div(ceil_div(W, 4), 128) * 128;
+}
+
+}  // namespace
+
 loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int precision,
                            void* e_out, void* logdet_out, int* walker_status) {
     if (!c) return LOAF_ERR_ARG;
-    int bad = 0, timeout = 0;
+    int flags[2] = {0, 0};  // worst walker status, timeout
     loaf_status st = guarded(c, [&] {
         LOAF_CUDA(cudaSetDevice(c->device));
         check_ready(c, W, phi, mode, precision);
         LOAF_REQUIRE(e_out != nullptr, LOAF_ERR_ARG, "e_out is NULL");
         ensure_workspace(c, W, mode);
-        const double2* dphi;
-        {
-            StageScope sc(c, "h2d_walkers", 0);
-            dphi = stage_walkers(c, W, phi);
-        }
-        // the LO split-precision path forms Delta on the tensor cores; the FP64
-        // path and the full mode use the FP64 Theta kernel
-        const bool tc_theta = precision != LOAF_PREC_FP64 && mode == LOAF_MODE_LO;
-        if (tc_theta) {
-            run_theta_tc(c, W, dphi, precision);
-        } else {
-            StageScope sc(c, "theta_fp64", c->nspin);
-            stage_theta(c, W, dphi);
-        }
-        double2* e1 = c->w_out.as<double2>();
-        double2* ej = e1 + W;
-        double2* ek = ej + W;
-        if (precision == LOAF_PREC_FP64) {
-            {
-                StageScope sc(c, "coulomb_fp64", 2);
-                run_coulomb_fp64(c, W, c->w_theta.as<double2>(), e1);
-            }
-            if (mode == LOAF_MODE_FULL) {
-                StageScope sc(c, "exchange_full_fp64", c->nspin + 1);
-                run_energy_fp64_full(c, W, c->w_theta.as<double2>(), ek);
-            } else {
-                StageScope sc(c, "exchange_lo_fp64", 2 * c->nspin);
-                run_energy_fp64_lo(c, W, c->w_theta.as<double2>(), ek, c->w_part.as<double2>());
-            }
-        } else {
-            run_energy_mixed(c, W, mode, precision, tc_theta ? nullptr : c->w_theta.as<double2>(),
-                             e1, nullptr);
-        }
         double2* de = c->w_host_stage.as<double2>();
         double2* dld = de + W;
         int* dst = reinterpret_cast<int*>(dld + W);
-        int* dbad = dst + W;
-        {
-            StageScope fsc(c, "finalize_d2h", 1);
-            LOAF_CUDA(cudaMemsetAsync(dbad, 0, sizeof(int), c->stream));
-            finalize_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
-                W, c->nspin, c->sp[0].mult, c->nspin > 1 ? c->sp[1].mult : 0.0, c->e0,
-                c->w_logdet.as<double2>(), c->w_status.as<int>(), e1, ej, ek, de, dld, dst, dbad);
-            LOAF_LAUNCH_CHECK();
-            deliver(c, e_out, de, (size_t)W * sizeof(double2));
-            deliver(c, logdet_out, dld, (size_t)W * sizeof(double2));
-            deliver(c, walker_status, dst, (size_t)W * sizeof(int));
+        int* dflags = dst + W;  // [worst status, timeout]
+        LOAF_CUDA(cudaMemsetAsync(dflags, 0, 2 * sizeof(int), c->stream));
+        const int Wc = is_device_ptr(phi) ? 0 : host_chunk(W);
+        if (Wc == 0) {
+            const double2* dphi;
+            {
+                StageScope sc(c, "h2d_walkers", 0);
+                dphi = stage_walkers(c, W, phi);
+            }
+            energy_batch(c, W, dphi, mode, precision, de, dld, dst, dflags, dflags + 1);
+        } else {
+            // upload chunk k + 1 on the copy stream while chunk k computes; two
+            // device buffers of Wc walkers alternate
+            if (!c->copy_stream) {
+                LOAF_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+                for (cudaEvent_t* e : {&c->ev_start, &c->ev_copied[0], &c->ev_copied[1], &c->ev_free[0],
+                                       &c->ev_free[1]})
+                    LOAF_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+            }
+            const size_t per_w = (size_t)c->M * c->ntot;
+            const double2* hphi = static_cast<const double2*>(phi);
+            double2* buf[2] = {c->w_phi.as<double2>(), c->w_phi.as<double2>() + (size_t)Wc * per_w};
+            LOAF_CUDA(cudaEventRecord(c->ev_start, c->stream));  // earlier users of w_phi are done
+            LOAF_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_start, 0));
+            for (int k = 0, w0 = 0; w0 < W; ++k, w0 += Wc) {
+                const int b = k & 1, Wk = std::min(Wc, W - w0);
+                if (k >= 2) LOAF_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_free[b], 0));
+                LOAF_CUDA(cudaMemcpyAsync(buf[b], hphi + (size_t)w0 * per_w, (size_t)Wk * per_w * sizeof(double2),
+                                          cudaMemcpyHostToDevice, c->copy_stream));
+                LOAF_CUDA(cudaEventRecord(c->ev_copied[b], c->copy_stream));
+                LOAF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_copied[b], 0));
+                energy_batch(c, Wk, buf[b], mode, precision, de + w0, dld + w0, dst + w0, dflags,
+                             dflags + 1);
+                LOAF_CUDA(cudaEventRecord(c->ev_free[b], c->stream));
+            }
         }
-        LOAF_CUDA(cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        if (precision != LOAF_PREC_FP64)
-            LOAF_CUDA(cudaMemcpyAsync(&timeout, c->w_flag.ptr, sizeof(int), cudaMemcpyDeviceToHost,
-                                      c->stream));
+        deliver(c, e_out, de, (size_t)W * sizeof(double2));
+        deliver(c, logdet_out, dld, (size_t)W * sizeof(double2));
+        deliver(c, walker_status, dst, (size_t)W * sizeof(int));
+        LOAF_CUDA(cudaMemcpyAsync(flags, dflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         LOAF_CUDA(cudaStreamSynchronize(c->stream));
         prof_collect(c);
     });
-    if (st == LOAF_OK && timeout) {
+    if (st == LOAF_OK && flags[1]) {
         c->err = "a tensor-core kernel gave up waiting on a pipeline barrier";
         return LOAF_ERR_TIMEOUT;
     }
-    if (st == LOAF_OK && bad) {
+    if (st == LOAF_OK && flags[0]) {
         c->err = "at least one walker overlap is singular or non-finite";
-        return bad == LOAF_WALKER_SINGULAR ? LOAF_ERR_SINGULAR : LOAF_ERR_NAN;
+        return flags[0] == LOAF_WALKER_SINGULAR ? LOAF_ERR_SINGULAR : LOAF_ERR_NAN;
     }
     return st;
 }

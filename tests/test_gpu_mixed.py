@@ -121,3 +121,25 @@ def test_naphthalene_scale_long_contractions():
     err = np.abs(e16 - e64).max()
     print("naphthalene fp16x3 vs fp64 LO max |dE| (Ha):", err)
     assert err < TOL_MIXED
+
+
+def test_host_walkers_are_uploaded_in_chunks(chain_lo):
+    """Host walker arrays of W >= 512 are uploaded chunk by chunk while the previous
+    chunk computes (three chunks of 256, 256 and 8 here).  Per-walker results equal
+    those of one device-resident batch up to the summation order of the Coulomb
+    split, which depends on the batch size; the first walkers also match the oracle."""
+    import torch
+    ctx, mol, walk, ref = chain_lo
+    many = synth.CHAIN_60.walkers(mol, W=520, processes=1)
+    many[:len(walk)] = walk
+    e_host, ld_host, st_host = ctx.walkers_energy(many, mode="lo", precision="fp16x3")
+    phi_d = torch.from_numpy(many).cuda()
+    e_d = torch.zeros(520, dtype=torch.complex128, device="cuda")
+    ld_d = torch.zeros_like(e_d)
+    st_d = torch.zeros(520, dtype=torch.int32, device="cuda")
+    ctx.walkers_energy(phi_d, mode="lo", precision="fp16x3", e_out=e_d, logdet_out=ld_d,
+                       walker_status=st_d)
+    assert np.all(st_host == 0) and np.all(st_d.cpu().numpy() == 0)
+    assert np.abs(e_host - e_d.cpu().numpy()).max() < 1e-8
+    assert np.array_equal(ld_host, ld_d.cpu().numpy())
+    assert np.abs(e_host[:len(walk)] - ref).max() < TOL_MIXED
