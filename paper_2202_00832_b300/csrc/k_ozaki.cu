@@ -81,9 +81,33 @@ __device__ inline int slice_exponent(double maxabs) {
 // 2^e as a double from its bit pattern (|e| < 1000)
 __device__ inline double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 
+// 2^e as a float (e clamped to the normal range)
+__device__ inline float pow2f(int e) { return __int_as_float((min(max(e, -126), 127) + 127) << 23); }
+
+// round(v 2^s) for a double v, from its bit pattern with integer arithmetic
+// only (B300 issues FP64 at 1/64 of the FP32 rate); the caller keeps
+// |v| 2^s < 2^62.  Ties round away from zero.
+__device__ inline long long round_scaled(double v, int s) {
+    const long long b = __double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) return 0;  // zero or subnormal
+    const long long m = (b & 0xfffffffffffffLL) | 0x10000000000000LL;  // 53-bit significand
+    const int sh = 1075 - ex - s;                                        // v 2^s = m 2^-sh
+    long long r;
+    if (sh <= 0) r = m << (-sh);
+    else if (sh > 54) r = 0;
+    else r = (m + (1LL << (sh - 1))) >> sh;
+    return b < 0 ? -r : r;
+}
+
+// |v| as an ordered integer key (non-negative doubles order like their bits)
+__device__ inline unsigned long long abs_key(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+
 // six balanced base-128 digits of x = v 2^-E (|x| <= 1/4), most significant first
 __device__ inline void digits6(double v, int E, int (&d)[kNS]) {
-    long long X = __double2ll_rn(v * pow2d(42 - E));
+    long long X = round_scaled(v, 42 - E);
 #pragma unroll
     for (int s = kNS - 1; s >= 0; --s) {
         const int r = (int)((X + 64) & 127) - 64;
@@ -93,6 +117,16 @@ __device__ inline void digits6(double v, int E, int (&d)[kNS]) {
 }
 
 __device__ inline uint16_t h16(int d) { return __half_as_ushort(__int2half_rn(d)); }
+
+__device__ inline unsigned long long block_max_key(unsigned long long v, unsigned long long* red) {
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned long long m = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = max(m, red[k]);
+    return m;
+}
 
 __device__ inline double block_max_d(double v, double* red) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -147,18 +181,18 @@ slice_phi_kernel(int M, int N, int ntot, int col0, int p_pad, int kpad, int W,
                  int* __restrict__ wexp) {
     extern __shared__ __align__(16) unsigned char sm[];
     signed char* dg = reinterpret_cast<signed char*>(sm);  // [kNS][kSliceRows][2N]
-    __shared__ double red[32];
+    __shared__ unsigned long long red[32];
     const int w = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const double2* pw = phi + (size_t)w * M * ntot + col0;
-    // walker exponent: warps over rows p, lanes over orbitals j
-    double m = 0.0;
+    // walker exponent: warps over rows p, lanes over orbitals j (integer max of |v|)
+    unsigned long long m = 0;
     for (int p = warp; p < M; p += nwarp)
         for (int j = lane; j < N; j += 32) {
             const double2 v = pw[(size_t)p * ntot + j];
-            m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+            m = max(m, max(abs_key(v.x), abs_key(v.y)));
         }
-    const int E = slice_exponent(block_max_d(m, red));
+    const int E = slice_exponent(__longlong_as_double((long long)block_max_key(m, red)));
     if (threadIdx.x == 0) wexp[w] = E;
     const int twoN = 2 * N;
     for (int p0 = 0; p0 < p_pad; p0 += kSliceRows) {
@@ -239,11 +273,13 @@ __device__ inline uint8_t* align1k(uint8_t* p) {
 
 // z 2^e - Phi_T (real part only), times the walker's Delta scale 2^te, as the
 // 16-bit hi/lo pair of the Delta planes; cc = 2k + ro of this spin
+// Delta = z 2^e - Phi_T (the trial is real: only the real part ro = 0 moves),
+// formed exactly in integer units of 2^e, then scaled by the walker's 2^te
 __device__ inline void store_delta(const OzParams& P, int w, int r, int cc, long long z, int e, int te) {
     const int k = cc >> 1, ro = cc & 1;
-    const double zt = (double)z * pow2d(e + te);
-    const double dl = ro ? zt : fma(-P.trial_cm[(size_t)k * P.M + r], pow2d(te), zt);
-    const float f = (float)dl;
+    long long D = z;
+    if (!ro) D -= round_scaled(P.trial_cm[(size_t)k * P.M + r], -e);
+    const float f = __ll2float_rn(D) * pow2f(e + te);
     uint16_t h, l;
     if (P.bf16) {
         const __nv_bfloat16 a = __float2bfloat16(f);
