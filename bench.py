@@ -322,16 +322,18 @@ def run_ours(args, rank, world, local):
         rooflines["lo_exchange_tc"] = r
     if "coulomb_tc" in per_launch_ms:
         rooflines["coulomb_tc"] = tc_roof("coulomb_tc", coul_flops)
-    if "inverse_fp64" in per_launch_ms:
-        # Gauss-Jordan inverse of the complex N x N overlap: N^3 complex FMAs (8 flops)
-        # per walker and spin (one spin for a closed shell)
-        t = per_launch_ms["inverse_fp64"] / 1e3
+    if "inverse_df" in per_launch_ms:
+        # double-float Gauss-Jordan: N^3 complex FMAs per walker and spin, each four
+        # error-free double-float multiply-adds of 15 FP32 operations (60 in all);
+        # peak: 148 SMs x 128 FP32 lanes x 2.032 GHz
+        t = per_launch_ms["inverse_df"] / 1e3
         n3 = N ** 3 if mol.closed_shell else mol.n_alpha ** 3 + mol.n_beta ** 3
-        ach = 8.0 * n3 * W / t / 1e12
-        rooflines["inverse_fp64"] = {"kernel": "gauss_jordan", "bound": "alu", "achieved": ach,
-                                     "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                                     "frac": ach / fp64_peak_tflops, "traffic": None,
-                                     "peak_source": "nominal FP64 ALU peak of B300"}
+        ach = 60.0 * n3 * W / t / 1e12
+        pk = 148 * 128 * 2.032e9 / 1e12
+        rooflines["inverse_df"] = {"kernel": "gauss_jordan (double-float)", "bound": "alu",
+                                   "achieved": ach, "peak": pk, "unit": "T FP32 lane-ops/s",
+                                   "frac": ach / pk, "traffic": None,
+                                   "peak_source": "148 SMs x 128 FP32 lanes x 2.032 GHz"}
     if "theta_fp64" in per_launch_ms:
         t = per_launch_ms["theta_fp64"] / 1e3
         ach = theta_flops / t / 1e12
@@ -377,7 +379,8 @@ def run_ours(args, rank, world, local):
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": f"{args.precision}: 16-bit hi+lo x3 tcgen05 contractions (fp32 acc); overlap and "
-                 f"Theta as exact 7-bit slice products on tcgen05; f64 inverse/log-det/reductions"
+                 f"Theta as exact 7-bit slice products on tcgen05; double-float (2 x f32) inverse and "
+                 f"log-det; f64 reductions"
                  if args.precision != "fp64" else "f64",
         "data": "synthetic",
         "config": {"workload": wl.name + (" (pentacene-scale acene ribbon)" if wl is synth.PENTACENE_440

@@ -444,8 +444,72 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
 // ---------------------------------------------------------------------------
 __device__ inline double mag2(double2 a) { return a.x * a.x + a.y * a.y; }
 
-// Z = S^-1 of one walker and spin.  Writes the log-det part, the status, the
-// per-column exponents g_k and the digits of the real block form of Z:
+// ---- double-float arithmetic (a value is hi + lo, two FP32 numbers) ----
+// B300 issues FP32 about 64x faster than FP64; an error-free product (FMA) and
+// sum (Knuth TwoSum) carry about 48 significant bits, enough for an inverse
+// whose columns feed 7-bit digit slices and, through Delta, 22-bit operands.
+// A complex double-float is a float4 {re.hi, re.lo, im.hi, im.lo}.
+struct dfl {
+    float hi, lo;
+};
+__device__ inline dfl df_from(double x) {
+    dfl r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+__device__ inline double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
+__device__ inline dfl df_neg(dfl a) { return dfl{-a.hi, -a.lo}; }
+// c + a b.  The _rn intrinsics are never contracted into FMAs, which would
+// break the error-free sums.
+__device__ inline dfl df_fma(dfl a, dfl b, dfl c) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);  // exact error of the product
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float s = __fadd_rn(c.hi, p);  // TwoSum(c.hi, p)
+    const float v = __fsub_rn(s, c.hi);
+    float t = __fadd_rn(__fsub_rn(c.hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+    t = __fadd_rn(t, c.lo);
+    t = __fadd_rn(t, e);
+    dfl r;
+    r.hi = __fadd_rn(s, t);  // renormalise
+    r.lo = __fsub_rn(t, __fsub_rn(r.hi, s));
+    return r;
+}
+__device__ inline dfl df_mul(dfl a, dfl b) { return df_fma(a, b, dfl{0.f, 0.f}); }
+__device__ inline float4 cdf_from(double2 z) {
+    const dfl r = df_from(z.x), i = df_from(z.y);
+    return make_float4(r.hi, r.lo, i.hi, i.lo);
+}
+__device__ inline double2 cdf_to(float4 z) {
+    return make_double2(df_to(dfl{z.x, z.y}), df_to(dfl{z.z, z.w}));
+}
+// v - f u (complex)
+__device__ inline float4 cdf_sub_mul(float4 v, float4 f, float4 u) {
+    const dfl fr{f.x, f.y}, fi{f.z, f.w}, ur{u.x, u.y}, ui{u.z, u.w};
+    dfl re{v.x, v.y}, im{v.z, v.w};
+    re = df_fma(df_neg(fr), ur, re);
+    re = df_fma(fi, ui, re);
+    im = df_fma(df_neg(fr), ui, im);
+    im = df_fma(df_neg(fi), ur, im);
+    return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+// x y (complex)
+__device__ inline float4 cdf_mul(float4 x, float4 y) {
+    const dfl xr{x.x, x.y}, xi{x.z, x.w}, yr{y.x, y.y}, yi{y.z, y.w};
+    const dfl re = df_fma(df_neg(xi), yi, df_mul(xr, yr));
+    const dfl im = df_fma(xi, yr, df_mul(xr, yi));
+    return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+constexpr int kGJMaxCols = (LOAF_MAX_NOCC + 15) / 16;  // columns per thread of the 16 x 16 grid
+
+// Z = S^-1 of one walker and spin by Gauss-Jordan elimination with partial
+// pivoting in double-float arithmetic (pivot search on |.|^2 of the leading
+// parts, each pivot's reciprocal and the log-det in FP64).  Writes the log-det
+// part, the status, the per-column exponents g_k and the digits of the real
+// block form of Z:
 //   Bt[s][w][2k + ro][2j + ri] = {Zr, -Zi, Zi, Zr}[ri][ro] (j, k) / 2^g_k,
 // the B operand of the Theta GEMM (Theta = [phi_re phi_im] B, column pairs).
 __global__ void __launch_bounds__(256)
@@ -453,20 +517,24 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
                     int* __restrict__ col_exp, int* __restrict__ gmax, double2* __restrict__ ld_part,
                     int* __restrict__ st_part) {
     extern __shared__ __align__(16) unsigned char sm[];
-    double2* A = reinterpret_cast<double2*>(sm);  // N x N
-    double2* colk = A + N * N;                     // N
-    double2* pivv = colk + N;                      // N pivots
-    int* piv = reinterpret_cast<int*>(pivv + N);   // N
-    int* gk = piv + N;                             // N
+    float4* A = reinterpret_cast<float4*>(sm);    // N x N complex double-float
+    float4* colk = A + N * N;                     // N
+    double2* pivv = reinterpret_cast<double2*>(colk + N);  // N pivots (FP64)
+    int* piv = reinterpret_cast<int*>(pivv + N);  // N
+    int* gk = piv + N;                            // N
     __shared__ double red_v[32];
     __shared__ double2 red_c[32];
     __shared__ int s_p, s_flag, s_swaps;
     __shared__ double s_tol;
+    __shared__ float4 s_inv;
     const int w = blockIdx.x, tid = threadIdx.x;
     const int ti = tid >> 4, tj = tid & 15;  // 16 x 16 grid over the matrix
-    for (int e = tid; e < N * N; e += blockDim.x) A[e] = S[(size_t)w * N * N + e];
     double m = 0.0;
-    for (int e = tid; e < N * N; e += blockDim.x) m = fmax(m, mag2(A[e]));
+    for (int e = tid; e < N * N; e += blockDim.x) {
+        const double2 z = S[(size_t)w * N * N + e];
+        A[e] = cdf_from(z);
+        m = fmax(m, mag2(z));
+    }
     m = block_max_d(m, red_v);
     if (tid == 0) {
         const double tol = (double)N * 2.220446049250313e-16 * sqrt(m);
@@ -477,22 +545,29 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
     __syncthreads();
     for (int k = 0; k < N && s_flag == 0; ++k) {
         if (tid < 32) {
-            double best = -1.0;
+            float best = -1.f;
             int bi = k;
             for (int i = k + tid; i < N; i += 32) {
-                const double v = mag2(A[i * N + k]);
+                const float4 a = A[i * N + k];
+                const float v = a.x * a.x + a.z * a.z;
                 if (v > best) { best = v; bi = i; }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const float ov = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
             }
             if (tid == 0) {
                 s_p = bi;
                 piv[k] = bi;
-                if (!(best > s_tol)) s_flag = 1;
                 if (bi != k) s_swaps += 1;
+                const double2 pv = cdf_to(A[bi * N + k]);
+                if (!(mag2(pv) > s_tol)) {
+                    s_flag = 1;
+                } else {
+                    pivv[k] = pv;
+                    s_inv = cdf_from(cdiv(make_double2(1.0, 0.0), pv));
+                }
             }
         }
         __syncthreads();
@@ -500,30 +575,35 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
         const int p = s_p;
         if (p != k)
             for (int c = tid; c < N; c += blockDim.x) {
-                const double2 t = A[k * N + c];
+                const float4 t = A[k * N + c];
                 A[k * N + c] = A[p * N + c];
                 A[p * N + c] = t;
             }
         __syncthreads();
-        const double2 pv = A[k * N + k];
-        const double2 inv = cdiv(make_double2(1.0, 0.0), pv);
-        if (tid == 0) pivv[k] = pv;
+        const float4 inv = s_inv;
         for (int i = tid; i < N; i += blockDim.x) colk[i] = A[i * N + k];
         __syncthreads();
         // pivot row: A[k][j] *= 1/pv, with A[k][k] = 1/pv
         for (int j = tid; j < N; j += blockDim.x)
-            A[k * N + j] = j == k ? inv : cmul(A[k * N + j], inv);
+            A[k * N + j] = j == k ? inv : cdf_mul(A[k * N + j], inv);
         __syncthreads();
         // other rows: A[i][j] -= A[i][k] (old) * A[k][j] (new); A[i][k] starts from 0
+        float4 u[kGJMaxCols];
+#pragma unroll
+        for (int q = 0; q < kGJMaxCols; ++q) {
+            const int j = tj + 16 * q;
+            u[q] = j < N ? A[k * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         for (int i = ti; i < N; i += 16) {
             if (i == k) continue;
-            const double2 f = colk[i];
-            for (int j = tj; j < N; j += 16) {
-                const double2 u = A[k * N + j];
-                double2 v = j == k ? make_double2(0.0, 0.0) : A[i * N + j];
-                v.x = fma(-f.x, u.x, fma(f.y, u.y, v.x));
-                v.y = fma(-f.x, u.y, fma(-f.y, u.x, v.y));
-                A[i * N + j] = v;
+            const float4 f = colk[i];
+#pragma unroll
+            for (int q = 0; q < kGJMaxCols; ++q) {
+                const int j = tj + 16 * q;
+                if (j < N) {
+                    const float4 v = j == k ? make_float4(0.f, 0.f, 0.f, 0.f) : A[i * N + j];
+                    A[i * N + j] = cdf_sub_mul(v, f, u[q]);
+                }
             }
         }
         __syncthreads();
@@ -536,7 +616,7 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
             const int p = piv[k];
             if (p != k)
                 for (int i = tid; i < N; i += blockDim.x) {
-                    const double2 t = A[i * N + k];
+                    const float4 t = A[i * N + k];
                     A[i * N + k] = A[i * N + p];
                     A[i * N + p] = t;
                 }
@@ -574,7 +654,10 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
     for (int k = wid; k < N; k += nw) {
         double mm = 0.0;
         if (flag == 0)
-            for (int j = lane; j < N; j += 32) mm = fmax(mm, fmax(fabs(A[j * N + k].x), fabs(A[j * N + k].y)));
+            for (int j = lane; j < N; j += 32) {
+                const double2 z = cdf_to(A[j * N + k]);
+                mm = fmax(mm, fmax(fabs(z.x), fabs(z.y)));
+            }
         for (int o = 16; o > 0; o >>= 1) mm = fmax(mm, __shfl_xor_sync(0xffffffffu, mm, o));
         if (lane == 0) {
             const int g = slice_exponent(mm);
@@ -594,7 +677,7 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
         const int k = cc >> 1, ro = cc & 1, j = K >> 1, ri = K & 1;
         double v = 0.0;
         if (flag == 0) {
-            const double2 z = A[j * N + k];
+            const double2 z = cdf_to(A[j * N + k]);
             v = (ri == ro) ? z.x : (ri ? -z.y : z.y);
         }
         int d[kNS];
@@ -713,7 +796,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
             LOAF_LAUNCH_CHECK();
         }
         {
-            StageScope sc(c, "inverse_fp64", 1);
+            StageScope sc(c, "inverse_df", 1);
             const size_t smem = (size_t)N * N * sizeof(double2) + (size_t)2 * N * sizeof(double2) +
                                 2 * N * sizeof(int) + 16;
             LOAF_CUDA(cudaFuncSetAttribute(gauss_jordan_kernel,

@@ -116,11 +116,15 @@ def test_naphthalene_scale_long_contractions():
     ref = oracle_energies(mol, walk[:3])
     assert np.max(np.abs(e64f - ref) / np.abs(ref)) < 1e-10
     ctx.lo_localize_compress(1e-4, position_operators(mol), localize=True)
-    e64, _, _ = ctx.walkers_energy(walk, mode="lo", precision="fp64")
-    e16, _, _ = ctx.walkers_energy(walk, mode="lo", precision="fp16x3")
+    e64, ld64, _ = ctx.walkers_energy(walk, mode="lo", precision="fp64")
+    e16, ld16, _ = ctx.walkers_energy(walk, mode="lo", precision="fp16x3")
     err = np.abs(e16 - e64).max()
     print("naphthalene fp16x3 vs fp64 LO max |dE| (Ha):", err)
     assert err < TOL_MIXED
+    # double-float inverse and log-det (N = 34) against the FP64 LU path: the
+    # absolute log error is the relative error of the overlap ratios it feeds
+    assert np.max(np.abs(ld16.real - ld64.real)) < 1e-10
+    assert np.max(np.abs(np.angle(np.exp(1j * (ld16.imag - ld64.imag))))) < 1e-10
 
 
 def test_host_walkers_are_uploaded_in_chunks(chain_lo):
@@ -143,3 +147,19 @@ def test_host_walkers_are_uploaded_in_chunks(chain_lo):
     assert np.abs(e_host - e_d.cpu().numpy()).max() < 1e-8
     assert np.array_equal(ld_host, ld_d.cpu().numpy())
     assert np.abs(e_host[:len(walk)] - ref).max() < TOL_MIXED
+
+
+def test_mixed_logdet_matches_oracle(chain_lo):
+    """The split-precision path forms S from six 7-bit digit slices (42 bits per
+    operand) and takes S^-1 and log det S from a double-float Gauss-Jordan
+    elimination (about 48 significant bits); its log-det matches the oracle's
+    partial-pivot LU to 1e-10 in log units (the relative error of the overlap
+    ratio exp(log det))."""
+    ctx, mol, walk, _ = chain_lo
+    _, ld, st = ctx.walkers_energy(walk, mode="lo", precision="fp16x3")
+    assert np.all(st == 0)
+    for w in range(len(walk)):
+        ref = 2 * E.logdet(E.overlap(mol.trial_a, walk[w]))
+        assert abs(ld[w].real - ref.real) <= 1e-10
+        dphi = np.angle(np.exp(1j * (ld[w].imag - ref.imag)))
+        assert abs(dphi) <= 1e-10
