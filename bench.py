@@ -51,6 +51,12 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=3, help="walkers timed on the oracle")
     ap.add_argument("--full-sample", type=int, default=64, help="walkers of the FP64 full GPU leg")
     ap.add_argument("--no-extras", action="store_true", help="skip accuracy / FP64 / CPU legs")
+    ap.add_argument("--screen-report", action="store_true",
+                    help="learned pair screen on the open-shell metallocene-scale cage instead of the "
+                         "throughput line: train on walkers 0-255, pairs kept and speed at each cutoff, "
+                         "energy changes against unscreened LO and full FP64, and a bound screen")
+    ap.add_argument("--screen-cutoffs", default="1e-6,1e-3,1e-2,1e-1",
+                    help="per-pair cutoffs (Ha) of the screen report")
     return ap.parse_args()
 
 
@@ -404,9 +410,116 @@ def run_ours(args, rank, world, local):
         dist.barrier()
 
 
+def screen_report(args):
+    """Learned pair screen (a8) on the metallocene-scale cage (M 500, N 48/47, X 2000):
+    the network is trained on walkers 0-255; at each cutoff the screen's kept pairs,
+    the step time of the screened LO energy against the unscreened one (1024
+    device-resident walkers), and the energy change per walker on held-out walkers
+    against unscreened LO (FP16x3) and against the full FP64 energy.  The bound
+    screen keeps a pair when max_w sigma_1 |Theta_i(w)| |Theta_j(w)| over the
+    training walkers reaches the cutoff (|e_ij| <= sigma_1 |Theta_i| |Theta_j|)."""
+    import torch
+    from paper_2202_00832_b300.lo_afqmc import Context, init_screen_params, position_operators
+
+    torch.cuda.set_device(0)
+    wl = synth.METALLOCENE_500
+    mol = wl.molecule()
+    W = args.walkers or 1024
+    n_train, n_test = 256, 16
+    walk = wl.walkers(mol, W=max(W, n_train + n_test), processes=min(16, os.cpu_count() or 1))
+    stream = torch.cuda.current_stream()
+    ctx = Context(0, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    ctx.load_molecule(mol)
+    pct, msvd = ctx.lo_localize_compress(args.threshold, position_operators(mol), localize=True)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = ctx.pair_screen_train(walk[:n_train], init_screen_params(0), epochs=1000, lr=3e-3)
+    t_train = time.perf_counter() - t0
+    q = ctx.pair_screen_query()
+    n_pairs = ctx.num_pairs
+    test = walk[n_train:n_train + n_test]
+
+    # pair order and energy weight: spins concatenated, i <= j, weight 1/2 mult (1 or 2)
+    pairs, wgt = [], []
+    spins = [(0, mol.n_alpha)] if mol.closed_shell else [(0, mol.n_alpha), (mol.n_alpha, mol.n_beta)]
+    mult = 2.0 if mol.closed_shell else 1.0
+    for col0, n in spins:
+        for i in range(n):
+            for j in range(i, n):
+                pairs.append((col0 + i, col0 + j))
+                wgt.append(0.5 * mult * (1.0 if i == j else 2.0))
+    pairs, wgt = np.array(pairs), np.array(wgt)
+    assert len(pairs) == n_pairs
+
+    # bound screen from the training walkers' Theta column norms (FP64 path)
+    th, _, _ = ctx.walkers_theta(walk[:n_train])
+    norms = np.linalg.norm(th, axis=2)                       # (W, ntot)
+    sigma1 = np.exp(q["features"][:, 4])
+    bound = sigma1 * np.max(norms[:, pairs[:, 0]] * norms[:, pairs[:, 1]], axis=0)
+
+    phi_d = torch.from_numpy(walk[:W]).to("cuda")
+    e_d = torch.zeros(W, dtype=torch.complex128, device="cuda")
+
+    def step_ms():
+        for _ in range(2):
+            ctx.walkers_energy(phi_d, mode="lo", precision=args.precision, e_out=e_d)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(3):
+            ctx.walkers_energy(phi_d, mode="lo", precision=args.precision, e_out=e_d)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / 3
+
+    ctx.pair_screen_set(-1.0)
+    t_unscreened = step_ms()
+    e_lo, _, _ = ctx.walkers_energy(test, mode="lo", precision=args.precision)
+    e_full, _, _ = ctx.walkers_energy(test[:4], mode="full", precision="fp64")
+    ep = ctx.walkers_pair_exchange(test, precision="fp64")   # (pairs, walkers)
+    rows = []
+    # the fixed cutoffs, then cutoffs at the 10 / 25 / 50 % quantiles of the
+    # predicted log10 |e_ij| (these synthetic pairs are all large, so the fixed
+    # ones keep everything; the quantile ones show the speed / error trade)
+    cutoffs = [float(x) for x in args.screen_cutoffs.split(",")]
+    cutoffs += [float(10 ** np.quantile(q["pred"], f)) for f in (0.10, 0.25, 0.50)]
+    for cut in cutoffs:
+        kept = ctx.pair_screen_set(cut)
+        t_s = step_ms()
+        e_s, _, _ = ctx.walkers_energy(test, mode="lo", precision=args.precision)
+        keep_b = bound >= cut
+        # E_K loses the dropped pairs' values: E rises by their weighted sum
+        e_b = e_lo + (wgt[~keep_b, None] * ep[~keep_b]).sum(axis=0)
+        rows.append({
+            "cutoff_ha": cut, "pairs_kept": kept, "pairs_total": n_pairs,
+            "ms_per_step": t_s, "speedup_vs_unscreened": t_unscreened / t_s,
+            "max_abs_dE_vs_unscreened_mha": float(np.abs(e_s - e_lo).max() * 1e3),
+            "max_abs_dE_vs_full_fp64_mha": float(np.abs(e_s[:4] - e_full).max() * 1e3),
+            "bound_screen": {"pairs_kept": int(keep_b.sum()),
+                             "max_abs_dE_vs_unscreened_mha": float(np.abs(e_b - e_lo).max() * 1e3)},
+        })
+    ctx.pair_screen_set(-1.0)
+    out = {"screen_report": {
+        "workload": wl.name, "walkers_timed": W, "train_walkers": n_train, "test_walkers": n_test,
+        "t_svd": args.threshold, "precision": args.precision, "compression_pct": pct,
+        "setup_s": t_setup, "train_s": t_train, "train_loss_first_last": [float(hist[0]), float(hist[-1])],
+        "pred_target_corr": float(np.corrcoef(q["pred"], q["target"])[0, 1]),
+        "target_log10_max_abs_e_min_median_max": [float(np.min(q["target"])), float(np.median(q["target"])),
+                                                  float(np.max(q["target"]))],
+        "unscreened_ms_per_step": t_unscreened,
+        "unscreened_vs_full_fp64_max_mha": float(np.abs(e_lo[:4] - e_full).max() * 1e3),
+        "cutoffs": rows}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.screen_report:
+        if rank == 0:
+            screen_report(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
