@@ -150,9 +150,40 @@ loaf_status lo_localize_compress(loaf_ctx *ctx, double t_svd, const double *r_op
  * A singular overlap marks that walker LOAF_WALKER_SINGULAR, writes NaN to
  * its energy and makes the call return LOAF_ERR_SINGULAR after finishing the
  * others.  Workspace grows to the largest W seen and is kept by the context.
+ * A host phi of W >= 512 walkers is uploaded in chunks while the previous
+ * chunk computes; the call returns when every output has been written.
  */
 loaf_status walkers_energy(loaf_ctx *ctx, int W, const void *phi, int mode, int precision,
                            void *e_out, void *logdet_out, int *walker_status);
+
+/*
+ * walkers_energy_multi -- local energies of several systems in one launch.
+ *
+ * The walkers_energy computation (mode LO, precision FP16X3 or BF16X3) for n
+ * loaded contexts (for example molecules of different sizes), each with its
+ * own batch, recorded once as a single CUDA graph whose branches run side by
+ * side and replayed on later calls with the same signature (contexts, sizes,
+ * buffers, loaded trial and screen).  With autotune = 1 the first call also
+ * chooses how many SMs the persistent kernels of each system may fill (all of
+ * them, or shares proportional to each system's LO work) by timing the
+ * candidate graphs; sm_caps reports the choice.
+ *   ctxs          n distinct contexts on the same device, each after
+ *                 lo_localize_compress
+ *   W             n batch sizes (>= 1)
+ *   phi           n device arrays, W[k] x M_k x Ntot_k complex128
+ *   e_out         n device arrays of W[k] complex128
+ *   logdet_out    n device arrays of W[k] complex128, or NULL (array or entries)
+ *   walker_status n device arrays of W[k] ints, or NULL (array or entries)
+ *   sm_caps       out (host, may be NULL): n SM budgets used (0 = all)
+ * Device buffers only (the graph keeps their addresses).  Errors as for
+ * walkers_energy; LOAF_ERR_ARG for host buffers or repeated contexts,
+ * LOAF_ERR_UNSUPPORTED for another mode or precision.  The call returns when
+ * every system's outputs are written.
+ */
+loaf_status walkers_energy_multi(loaf_ctx *const *ctxs, int n, const int *W, const void *const *phi,
+                                 int mode, int precision, void *const *e_out,
+                                 void *const *logdet_out, int *const *walker_status, int autotune,
+                                 int *sm_caps);
 
 /*
  * walkers_theta -- the first stage alone: Theta = phi (Phi_T^T phi)^-1 and

@@ -5,8 +5,13 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 using namespace loaf;
+
+namespace {
+void forget_plans(loaf_ctx* c);  // multi-system graphs using c
+}  // namespace
 
 namespace {
 
@@ -236,6 +241,10 @@ loaf_status loaf_destroy(loaf_ctx* c) {
     if (!c) return LOAF_OK;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    forget_plans(c);
+    if (c->branch_stream) cudaStreamDestroy(c->branch_stream);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->h_flags) cudaFreeHost(c->h_flags);
     for (auto& s : c->sp) s.release();
     for (auto& m : c->mix) m.release();
     c->d_h.release(); c->d_L.release();
@@ -458,6 +467,261 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
     }
     if (st == LOAF_OK && flags[0]) {
         c->err = "at least one walker overlap is singular or non-finite";
+        return flags[0] == LOAF_WALKER_SINGULAR ? LOAF_ERR_SINGULAR : LOAF_ERR_NAN;
+    }
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// several systems in one graph
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+struct MultiPlan {
+    std::vector<loaf_ctx*> ctxs;
+    std::vector<int> W, screen_v, trial_v, caps;
+    std::vector<const void*> phi;
+    std::vector<void*> e, ld;
+    std::vector<int*> st;
+    int mode = 0, precision = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void release() {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (cudaEvent_t ev : {fork, t0, t1})
+            if (ev) cudaEventDestroy(ev);
+        if (stream) cudaStreamDestroy(stream);
+        exec = nullptr;
+        stream = nullptr;
+        fork = t0 = t1 = nullptr;
+    }
+};
+
+std::mutex g_multi_mu;
+std::vector<MultiPlan*> g_plans;
+
+// drop every plan that uses context c (it is being destroyed)
+void forget_plans(loaf_ctx* c) {
+    std::lock_guard<std::mutex> lk(g_multi_mu);
+    for (auto it = g_plans.begin(); it != g_plans.end();) {
+        if (std::find((*it)->ctxs.begin(), (*it)->ctxs.end(), c) != (*it)->ctxs.end()) {
+            (*it)->release();
+            delete *it;
+            it = g_plans.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+// The n branches of one multi-system graph: each context's batch on its own
+// branch stream (the context's stream is swapped for the capture), outputs
+// copied to the caller's buffers and the status flags to pinned host memory.
+cudaGraphExec_t capture_multi(MultiPlan& P, const std::vector<int>& caps) {
+    const int n = (int)P.ctxs.size();
+    std::vector<cudaStream_t> saved(n);
+    for (int k = 0; k < n; ++k) saved[k] = P.ctxs[k]->stream;
+    auto restore = [&] {
+        for (int k = 0; k < n; ++k) {
+            P.ctxs[k]->stream = saved[k];
+            P.ctxs[k]->grid_cap = 0;
+        }
+    };
+    LOAF_CUDA(cudaStreamBeginCapture(P.stream, cudaStreamCaptureModeRelaxed));
+    try {
+        LOAF_CUDA(cudaEventRecord(P.fork, P.stream));
+        for (int k = 0; k < n; ++k) {
+            loaf_ctx* c = P.ctxs[k];
+            c->stream = c->branch_stream;
+            c->grid_cap = caps[k];
+            LOAF_CUDA(cudaStreamWaitEvent(c->stream, P.fork, 0));
+            const int W = P.W[k];
+            double2* de = c->w_host_stage.as<double2>();
+            double2* dld = de + W;
+            int* dst = reinterpret_cast<int*>(dld + W);
+            int* dflags = dst + W;
+            LOAF_CUDA(cudaMemsetAsync(dflags, 0, 2 * sizeof(int), c->stream));
+            energy_batch(c, W, static_cast<const double2*>(P.phi[k]), P.mode, P.precision, de, dld,
+                         dst, dflags, dflags + 1);
+            LOAF_CUDA(cudaMemcpyAsync(P.e[k], de, (size_t)W * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                      c->stream));
+            if (P.ld[k])
+                LOAF_CUDA(cudaMemcpyAsync(P.ld[k], dld, (size_t)W * sizeof(double2),
+                                          cudaMemcpyDeviceToDevice, c->stream));
+            if (P.st[k])
+                LOAF_CUDA(cudaMemcpyAsync(P.st[k], dst, (size_t)W * sizeof(int), cudaMemcpyDeviceToDevice,
+                                          c->stream));
+            LOAF_CUDA(cudaMemcpyAsync(c->h_flags, dflags, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                      c->stream));
+            LOAF_CUDA(cudaEventRecord(c->ev_join, c->stream));
+            LOAF_CUDA(cudaStreamWaitEvent(P.stream, c->ev_join, 0));
+            c->stream = saved[k];
+            c->grid_cap = 0;
+        }
+    } catch (...) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(P.stream, &g);
+        if (g) cudaGraphDestroy(g);
+        restore();
+        throw;
+    }
+    restore();
+    cudaGraph_t graph = nullptr;
+    LOAF_CUDA(cudaStreamEndCapture(P.stream, &graph));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    LOAF_CUDA(ie);
+    return exec;
+}
+
+float time_graph(MultiPlan& P, cudaGraphExec_t exec, int reps) {
+    LOAF_CUDA(cudaGraphLaunch(exec, P.stream));
+    LOAF_CUDA(cudaEventRecord(P.t0, P.stream));
+    for (int r = 0; r < reps; ++r) LOAF_CUDA(cudaGraphLaunch(exec, P.stream));
+    LOAF_CUDA(cudaEventRecord(P.t1, P.stream));
+    LOAF_CUDA(cudaEventSynchronize(P.t1));
+    float ms = 0.f;
+    LOAF_CUDA(cudaEventElapsedTime(&ms, P.t0, P.t1));
+    return ms / reps;
+}
+
+}  // namespace
+
+extern "C" {
+
+loaf_status walkers_energy_multi(loaf_ctx* const* ctxs, int n, const int* W, const void* const* phi,
+                                 int mode, int precision, void* const* e_out, void* const* logdet_out,
+                                 int* const* walker_status, int autotune, int* sm_caps) {
+    if (!ctxs || n < 1 || !W || !phi || !e_out) return LOAF_ERR_ARG;
+    loaf_ctx* c0 = ctxs[0];
+    if (!c0) return LOAF_ERR_ARG;
+    int flags[2] = {0, 0};
+    loaf_status st = guarded(c0, [&] {
+        LOAF_REQUIRE(mode == LOAF_MODE_LO, LOAF_ERR_UNSUPPORTED, "the multi-system launch runs the LO mode");
+        LOAF_REQUIRE(precision == LOAF_PREC_FP16X3 || precision == LOAF_PREC_BF16X3, LOAF_ERR_UNSUPPORTED,
+                     "the multi-system launch runs the split-precision path");
+        for (int k = 0; k < n; ++k) {
+            loaf_ctx* c = ctxs[k];
+            LOAF_REQUIRE(c != nullptr && c->device == c0->device, LOAF_ERR_ARG,
+                         "contexts must be non-NULL and on one device");
+            for (int q = 0; q < k; ++q) LOAF_REQUIRE(ctxs[q] != c, LOAF_ERR_ARG, "a context appears twice");
+            LOAF_REQUIRE(c->compressed, LOAF_ERR_NOT_READY, "lo_localize_compress has not been called");
+            LOAF_REQUIRE(W[k] >= 1 && phi[k] && e_out[k], LOAF_ERR_ARG, "empty batch or NULL buffer");
+            LOAF_REQUIRE(is_device_ptr(phi[k]) && is_device_ptr(e_out[k]) &&
+                             (!logdet_out || !logdet_out[k] || is_device_ptr(logdet_out[k])) &&
+                             (!walker_status || !walker_status[k] || is_device_ptr(walker_status[k])),
+                         LOAF_ERR_ARG, "the multi-system launch takes device buffers only");
+        }
+        LOAF_CUDA(cudaSetDevice(c0->device));
+        std::lock_guard<std::mutex> lk(g_multi_mu);
+        // find the plan of this signature
+        MultiPlan* P = nullptr;
+        for (MultiPlan* q : g_plans) {
+            if ((int)q->ctxs.size() != n || q->mode != mode || q->precision != precision) continue;
+            bool same = true;
+            for (int k = 0; k < n && same; ++k)
+                same = q->ctxs[k] == ctxs[k] && q->W[k] == W[k] && q->phi[k] == phi[k] && q->e[k] == e_out[k] &&
+                       q->ld[k] == (logdet_out ? logdet_out[k] : nullptr) &&
+                       q->st[k] == (walker_status ? walker_status[k] : nullptr) &&
+                       q->screen_v[k] == ctxs[k]->screen_version && q->trial_v[k] == ctxs[k]->trial_version;
+            if (same) { P = q; break; }
+        }
+        if (!P) {
+            // first call of this signature: an eager pass on each context sets up
+            // its operands and workspace, then the graph is recorded
+            for (int k = 0; k < n; ++k) {
+                loaf_ctx* c = ctxs[k];
+                check_ready(c, W[k], phi[k], mode, precision);
+                ensure_workspace(c, W[k], mode);
+                if (!c->branch_stream) {
+                    LOAF_CUDA(cudaStreamCreateWithFlags(&c->branch_stream, cudaStreamNonBlocking));
+                    LOAF_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+                    LOAF_CUDA(cudaHostAlloc(&c->h_flags, 2 * sizeof(int), cudaHostAllocDefault));
+                }
+                double2* de = c->w_host_stage.as<double2>();
+                double2* dld = de + W[k];
+                int* dst = reinterpret_cast<int*>(dld + W[k]);
+                int* dflags = dst + W[k];
+                const bool prof = c->prof_on;
+                c->prof_on = false;
+                LOAF_CUDA(cudaMemsetAsync(dflags, 0, 2 * sizeof(int), c->stream));
+                energy_batch(c, W[k], static_cast<const double2*>(phi[k]), mode, precision, de, dld, dst,
+                             dflags, dflags + 1);
+                LOAF_CUDA(cudaStreamSynchronize(c->stream));
+                c->prof_on = prof;
+            }
+            P = new MultiPlan;
+            g_plans.push_back(P);
+            P->ctxs.assign(ctxs, ctxs + n);
+            P->W.assign(W, W + n);
+            P->phi.assign(phi, phi + n);
+            P->e.assign(e_out, e_out + n);
+            for (int k = 0; k < n; ++k) {
+                P->ld.push_back(logdet_out ? logdet_out[k] : nullptr);
+                P->st.push_back(walker_status ? walker_status[k] : nullptr);
+                P->screen_v.push_back(ctxs[k]->screen_version);
+                P->trial_v.push_back(ctxs[k]->trial_version);
+            }
+            P->mode = mode;
+            P->precision = precision;
+            LOAF_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+            LOAF_CUDA(cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming));
+            LOAF_CUDA(cudaEventCreate(&P->t0));
+            LOAF_CUDA(cudaEventCreate(&P->t1));
+            std::vector<bool> prof(n);
+            for (int k = 0; k < n; ++k) { prof[k] = ctxs[k]->prof_on; ctxs[k]->prof_on = false; }
+            // candidate SM budgets: every system may fill the GPU, or each gets a
+            // share proportional to its LO work (W x rows x M), rounded to SM pairs
+            std::vector<std::vector<int>> cands{std::vector<int>(n, 0)};
+            if (autotune && n > 1) {
+                std::vector<double> work(n);
+                double tot = 0.0;
+                for (int k = 0; k < n; ++k) {
+                    const MixedOps& mx = ctxs[k]->mix[precision == LOAF_PREC_BF16X3 ? 1 : 0];
+                    work[k] = (double)W[k] * (double)std::max<long>(mx.R, 1) * ctxs[k]->M;
+                    tot += work[k];
+                }
+                std::vector<int> prop(n);
+                for (int k = 0; k < n; ++k) {
+                    int cap = (int)std::lround(c0->sm_count * work[k] / tot);
+                    cap = std::max(8, std::min(c0->sm_count, (cap + 1) / 2 * 2));
+                    prop[k] = cap;
+                }
+                cands.push_back(prop);
+            }
+            float best = 0.f;
+            for (size_t q = 0; q < cands.size(); ++q) {
+                cudaGraphExec_t ex = capture_multi(*P, cands[q]);
+                const float ms = cands.size() > 1 ? time_graph(*P, ex, 3) : 0.f;
+                if (!P->exec || ms < best) {
+                    if (P->exec) cudaGraphExecDestroy(P->exec);
+                    P->exec = ex;
+                    P->caps = cands[q];
+                    best = ms;
+                } else {
+                    cudaGraphExecDestroy(ex);
+                }
+            }
+            for (int k = 0; k < n; ++k) ctxs[k]->prof_on = prof[k];
+        }
+        LOAF_CUDA(cudaGraphLaunch(P->exec, P->stream));
+        LOAF_CUDA(cudaStreamSynchronize(P->stream));
+        for (int k = 0; k < n; ++k) {
+            flags[0] = std::max(flags[0], ctxs[k]->h_flags[0]);
+            flags[1] = std::max(flags[1], ctxs[k]->h_flags[1]);
+            if (sm_caps) sm_caps[k] = P->caps[k];
+        }
+    });
+    if (st == LOAF_OK && flags[1]) {
+        c0->err = "a tensor-core kernel gave up waiting on a pipeline barrier";
+        return LOAF_ERR_TIMEOUT;
+    }
+    if (st == LOAF_OK && flags[0]) {
+        c0->err = "at least one walker overlap is singular or non-finite";
         return flags[0] == LOAF_WALKER_SINGULAR ? LOAF_ERR_SINGULAR : LOAF_ERR_NAN;
     }
     return st;

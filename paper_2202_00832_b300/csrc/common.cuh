@@ -9,6 +9,7 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -253,6 +254,14 @@ struct loaf_ctx {
     cublasHandle_t cublas = nullptr;
     cusolverDnHandle_t cusolver = nullptr;
     int sm_count = 0;
+    // SMs the persistent tensor-core kernels of this context may fill (0: all);
+    // set by the multi-system launch so that several systems share the GPU
+    int grid_cap = 0;
+    int persistent_grid() const { return grid_cap > 0 ? std::min(grid_cap, sm_count) : sm_count; }
+    // multi-system launches: a private branch stream, fork/join events, pinned flags
+    cudaStream_t branch_stream = nullptr;
+    cudaEvent_t ev_join = nullptr;
+    int* h_flags = nullptr;
 
     bool loaded = false;
     bool compressed = false;

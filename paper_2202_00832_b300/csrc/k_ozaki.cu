@@ -792,7 +792,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
             P.wexp = wexp(s);
             P.S_out = c->w_oz_S.as<double>();
             const int units = P.n_rt * P.n_ct * P.n_b;
-            ozaki_gemm_kernel<<<std::min(units, c->sm_count), kOThreads, kOSmem, c->stream>>>(mA, mB, P);
+            ozaki_gemm_kernel<<<std::min(units, c->persistent_grid()), kOThreads, kOSmem, c->stream>>>(mA, mB, P);
             LOAF_LAUNCH_CHECK();
         }
         {
@@ -840,7 +840,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
         P.dlo = c->w_dlo.as<uint16_t>();
         P.bf16 = bf16 ? 1 : 0;
         const int units = P.n_rt * P.n_ct * P.n_b;
-        ozaki_gemm_kernel<<<std::min(units, c->sm_count), kOThreads, kOSmem, c->stream>>>(mA, mB, P);
+        ozaki_gemm_kernel<<<std::min(units, c->persistent_grid()), kOThreads, kOSmem, c->stream>>>(mA, mB, P);
         LOAF_LAUNCH_CHECK();
     }
 }

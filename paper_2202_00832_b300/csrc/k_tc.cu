@@ -1194,7 +1194,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         P.n_wt = ceil_div(2L * W, kCBN);
         P.nk = c->ntot * dg.nkb;
         const int tiles = P.n_mt * P.n_wt;
-        P.n_split = std::max(1, std::min(ceil_div(P.nk, kCGroup), (3 * c->sm_count + tiles - 1) / tiles));
+        P.n_split = std::max(1, std::min(ceil_div(P.nk, kCGroup), (3 * c->persistent_grid() + tiles - 1) / tiles));
         P.ldp = P.n_wt * kCBN;
         P.idesc = tc::idesc_f16(kBM, kCBN, bf16);
         P.err = err;
@@ -1204,7 +1204,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         LOAF_CUDA(cudaFuncSetAttribute(coulomb_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kCoulSmem));
         StageScope csc(c, "coulomb_tc", 1);
-        coulomb_tc_kernel<<<std::min(units, c->sm_count), kCThreads, kCoulSmem, c->stream>>>(P);
+        coulomb_tc_kernel<<<std::min(units, c->persistent_grid()), kCThreads, kCoulSmem, c->stream>>>(P);
         LOAF_LAUNCH_CHECK();
         csc.end();
         StageScope rsc(c, "coulomb_reduce", 2);
@@ -1252,7 +1252,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             c->w_lopart.ensure((size_t)n_pt * Wpad * sizeof(double2));
             P.part = c->w_lopart.as<double2>();
             const int units = (n_pt / 2) * n_wt;
-            const int n_cl = std::min(units, lo_max_clusters(c));
+            const int n_cl = std::max(1, std::min({units, lo_max_clusters(c), c->persistent_grid() / 2}));
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;

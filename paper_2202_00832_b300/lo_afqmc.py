@@ -39,6 +39,7 @@ SIGNATURES = [
     ("ao_load_cholesky", _I, [_P, _I, _I, _P, _P, _I, _I, _P, _P, _D, _I]),
     ("lo_localize_compress", _I, [_P, _D, _P, _I, _I, _P, _P]),
     ("walkers_energy", _I, [_P, _I, _P, _I, _I, _P, _P, _P]),
+    ("walkers_energy_multi", _I, [_P, _I, _P, _P, _I, _I, _P, _P, _P, _I, _P]),
     ("walkers_theta", _I, [_P, _I, _P, _P, _P, _P]),
     ("walkers_pair_exchange", _I, [_P, _I, _P, _I, _P]),
     ("loaf_num_pairs", _I, [_P]),
@@ -323,6 +324,28 @@ def mlp_loss_grad(x, t, params, device: int = 0):
     if code != 0:
         raise LoafError(code, "mlp_loss_grad", "")
     return float(loss.value), g
+
+
+def walkers_energy_multi(ctxs, phis, e_outs, logdet_outs=None, statuses=None, mode="lo",
+                         precision="fp16x3", autotune: bool = True):
+    """Energies of several systems in one graph launch (device tensors only).
+    Returns the SM budget chosen for each system (0 = the whole GPU)."""
+    lib = load_library()
+    n = len(ctxs)
+    for a in phis:
+        _check_dtype(a, "c16")
+    arr = lambda vals, typ=_P: (typ * n)(*vals)
+    caps = (ctypes.c_int * n)()
+    W = arr([int(a.shape[0]) for a in phis], ctypes.c_int)
+    ld = arr([_ptr(a) for a in logdet_outs]) if logdet_outs is not None else None
+    st = arr([_ptr(a) for a in statuses]) if statuses is not None else None
+    code = lib.walkers_energy_multi(arr([c._h for c in ctxs]), n, W, arr([_ptr(a) for a in phis]),
+                                    MODES.get(mode, mode), PRECISIONS.get(precision, precision),
+                                    arr([_ptr(a) for a in e_outs]), ld, st, int(bool(autotune)), caps)
+    if code != 0:
+        msg = lib.loaf_last_error(ctxs[0]._h).decode()
+        raise LoafError(code, "walkers_energy_multi", msg)
+    return list(caps)
 
 
 def init_screen_params(seed: int = 0) -> np.ndarray:
