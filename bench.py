@@ -55,6 +55,10 @@ def parse():
                     help="learned pair screen on the open-shell metallocene-scale cage instead of the "
                          "throughput line: train on walkers 0-255, pairs kept and speed at each cutoff, "
                          "energy changes against unscreened LO and full FP64, and a bound screen")
+    ap.add_argument("--hetero-report", action="store_true",
+                    help="the six-molecule heterogeneous batch (acene ribbons M 100..480) instead of the "
+                         "throughput line: aggregate walker energies/s of one multi-system graph launch "
+                         "against one walkers_energy call per molecule, per-molecule error, SM budgets")
     ap.add_argument("--screen-cutoffs", default="1e-6,1e-3,1e-2,1e-1",
                     help="per-pair cutoffs (Ha) of the screen report")
     return ap.parse_args()
@@ -513,9 +517,75 @@ def screen_report(args):
     print(json.dumps(out), flush=True)
 
 
+def hetero_report(args):
+    """Six acene ribbons of different sizes (M 100..480, N 14..80, W 512..128;
+    LO, T_SVD = 1e-4, FP16x3): the aggregate rate of one walkers_energy_multi
+    graph launch (autotuned SM budgets) against one walkers_energy call per
+    molecule in turn, both on device-resident walkers, and each molecule's
+    energy error against its FP64 LO path on 4 walkers."""
+    import torch
+    from paper_2202_00832_b300.lo_afqmc import Context, position_operators, walkers_energy_multi
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctxs, phis, walks, info = [], [], [], []
+    t0 = time.perf_counter()
+    for wl in synth.HETERO_BATCH:
+        mol = wl.molecule()
+        walk = wl.walkers(mol, processes=min(16, os.cpu_count() or 1))
+        c = Context(0, stream=stream.cuda_stream)
+        c.load_molecule(mol)
+        pct, msvd = c.lo_localize_compress(args.threshold, position_operators(mol), localize=True)
+        ctxs.append(c)
+        walks.append(walk)
+        phis.append(torch.from_numpy(walk).cuda())
+        info.append({"workload": wl.name, "M": mol.M, "N": mol.n_alpha, "X": mol.X, "W": len(walk),
+                     "pairs": int(len(msvd)), "compression_pct": pct})
+    t_setup = time.perf_counter() - t0
+    total_w = sum(p.shape[0] for p in phis)
+    e = [torch.zeros(p.shape[0], dtype=torch.complex128, device="cuda") for p in phis]
+
+    def timed(fn, reps=5):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    def sequential():
+        for c, p, x in zip(ctxs, phis, e):
+            c.walkers_energy(p, mode="lo", precision=args.precision, e_out=x)
+
+    caps = walkers_energy_multi(ctxs, phis, e, precision=args.precision, autotune=True)
+    t_multi = timed(lambda: walkers_energy_multi(ctxs, phis, e, precision=args.precision, autotune=True))
+    t_seq = timed(sequential)
+    walkers_energy_multi(ctxs, phis, e, precision=args.precision, autotune=True)
+    for k, c in enumerate(ctxs):
+        got = e[k][:4].cpu().numpy()
+        e64, _, _ = c.walkers_energy(walks[k][:4], mode="lo", precision="fp64")
+        info[k]["max_abs_dE_vs_fp64_lo_mha"] = float(np.abs(got - e64).max() * 1e3)
+        info[k]["sm_budget"] = caps[k]
+    out = {"hetero_report": {
+        "molecules": info, "walkers_total": total_w, "setup_s": t_setup,
+        "multi_graph": {"ms_per_batch": t_multi, "walker_energies_per_s": total_w / (t_multi / 1e3)},
+        "sequential_calls": {"ms_per_batch": t_seq, "walker_energies_per_s": total_w / (t_seq / 1e3)},
+        "speedup": t_seq / t_multi,
+        "sm_budget_note": "0 = the persistent kernels may fill all 148 SMs"}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.hetero_report:
+        if rank == 0:
+            hetero_report(args)
+        return
     if args.screen_report:
         if rank == 0:
             screen_report(args)
