@@ -59,6 +59,9 @@ def parse():
                     help="the six-molecule heterogeneous batch (acene ribbons M 100..480) instead of the "
                          "throughput line: aggregate walker energies/s of one multi-system graph launch "
                          "against one walkers_energy call per molecule, per-molecule error, SM budgets")
+    ap.add_argument("--tsvd-report", action="store_true",
+                    help="the T_SVD sweep on the naphthalene-scale honeycomb instead of the throughput line: "
+                         "compression, <M_SVD>, LO-vs-full and mixed-vs-FP64 errors, truncation bound")
     ap.add_argument("--screen-cutoffs", default="1e-6,1e-3,1e-2,1e-1",
                     help="per-pair cutoffs (Ha) of the screen report")
     return ap.parse_args()
@@ -579,9 +582,56 @@ def hetero_report(args):
     print(json.dumps(out), flush=True)
 
 
+def tsvd_report(args):
+    """T_SVD sweep on the naphthalene-scale honeycomb (M 250, N 34, X 1000; 64
+    walkers): per threshold the compression, <M_SVD> (Boys-localized and canonical
+    orbitals), the LO-vs-full error of the FP64 path, the mixed-vs-FP64 LO error,
+    and the closed-form truncation bound |E_K^LO - E_K| < (mult/2) sum_sigma
+    T (sum_i |Theta_i|)^2 (every dropped singular value is below T), checked per
+    walker."""
+    from paper_2202_00832_b300.lo_afqmc import Context, position_operators
+
+    wl = synth.NAPHTHALENE_250
+    mol = wl.molecule()
+    walk = wl.walkers(mol, W=64, processes=min(16, os.cpu_count() or 1))
+    ctx = Context(0)
+    ctx.load_molecule(mol)
+    e_full, _, _ = ctx.walkers_energy(walk, mode="full", precision="fp64")
+    canon = Context(0)
+    canon.load_molecule(mol)
+    mult = 2.0 if mol.closed_shell else 1.0
+    rows = []
+    for T in [1e-2, 1e-3, 1e-4, 1e-5]:
+        pct, msvd = ctx.lo_localize_compress(T, position_operators(mol), localize=True)
+        pct_c, msvd_c = canon.lo_localize_compress(T, position_operators(mol), localize=False)
+        th, _, _ = ctx.walkers_theta(walk)                   # localized trial: (W, ntot, M)
+        nrm = np.linalg.norm(th, axis=2)
+        if mol.closed_shell:
+            bound = mult / 2 * T * nrm.sum(axis=1) ** 2
+        else:
+            na = mol.n_alpha
+            bound = mult / 2 * T * (nrm[:, :na].sum(axis=1) ** 2 + nrm[:, na:].sum(axis=1) ** 2)
+        e64, _, _ = ctx.walkers_energy(walk, mode="lo", precision="fp64")
+        e16, _, _ = ctx.walkers_energy(walk, mode="lo", precision=args.precision)
+        err = np.abs(e64 - e_full)
+        rows.append({
+            "t_svd": T, "compression_pct": pct, "mean_m_svd": float(msvd.mean()),
+            "canonical_compression_pct": pct_c, "canonical_mean_m_svd": float(msvd_c.mean()),
+            "lo_vs_full_fp64_mean_mha": float(err.mean() * 1e3), "lo_vs_full_fp64_max_mha": float(err.max() * 1e3),
+            "mixed_vs_fp64_lo_max_mha": float(np.abs(e16 - e64).max() * 1e3),
+            "bound_max_mha": float(bound.max() * 1e3), "bound_holds_all_walkers": bool(np.all(err <= bound)),
+        })
+    print(json.dumps({"tsvd_report": {"workload": wl.name, "walkers": len(walk), "precision": args.precision,
+                                      "rows": rows}}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.tsvd_report:
+        if rank == 0:
+            tsvd_report(args)
+        return
     if args.hetero_report:
         if rank == 0:
             hetero_report(args)
