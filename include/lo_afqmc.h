@@ -49,7 +49,7 @@ typedef enum {
     LOAF_ERR_UNSUPPORTED = 9  /* valid request this build does not provide */
 } loaf_status;
 
-enum { LOAF_MODE_FULL = 0, LOAF_MODE_LO = 1 };
+enum { LOAF_MODE_FULL = 0, LOAF_MODE_LO = 1, LOAF_MODE_LO_JK = 2 };
 
 /*
  * Arithmetic of the contractions (overlap, LU, log-det and Theta are FP64
@@ -141,7 +141,11 @@ loaf_status lo_localize_compress(loaf_ctx *ctx, double t_svd, const double *r_op
  *   W          >= 1 walkers
  *   phi        W x M x Ntot complex128, Ntot = n_alpha (closed shell) or
  *              n_alpha + n_beta (alpha columns first); host or device
- *   mode       LOAF_MODE_FULL or LOAF_MODE_LO (LO needs lo_localize_compress)
+ *   mode       LOAF_MODE_FULL, LOAF_MODE_LO (LO needs lo_localize_compress), or
+ *              LOAF_MODE_LO_JK: LO exchange and the Coulomb from the same
+ *              compressed pair factors, E_J = 2 sum_ij (Ubar^[ij]T Theta_i).
+ *              (Vbar^[ij] Theta_j) (eq. 2e_HR_RCAS, the 4 Q_ri Q_sj term; closed
+ *              shells only, LOAF_ERR_UNSUPPORTED otherwise)
  *   precision  LOAF_PREC_*; the full mode supports FP64 and FP16X3/BF16X3
  *              (Coulomb on tensor cores, exchange FP64)
  *   e_out      W complex128 energies (host or device)

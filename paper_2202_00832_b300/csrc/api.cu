@@ -86,7 +86,7 @@ void ensure_workspace(loaf_ctx* c, int W, int mode) {
     c->w_out.ensure((size_t)3 * W * sizeof(double2));
     c->w_part2.ensure((size_t)W * (c->X + 1) * sizeof(double2));
     c->w_host_stage.ensure((size_t)W * (2 * sizeof(double2) + sizeof(int)) + 64);
-    if (mode == LOAF_MODE_LO) {
+    if (mode != LOAF_MODE_FULL) {
         long np = 0;
         for (int s = 0; s < c->nspin; ++s) np += c->sp[s].pairs.npairs;
         c->w_part.ensure((size_t)std::max<long>(np, 1) * W * sizeof(double2));
@@ -116,11 +116,14 @@ void check_ready(loaf_ctx* c, int W, const void* phi, int mode, int precision) {
     LOAF_REQUIRE(c->loaded, LOAF_ERR_NOT_READY, "ao_load_cholesky has not been called");
     LOAF_REQUIRE(W >= 1, LOAF_ERR_ARG, "W must be >= 1");
     LOAF_REQUIRE(phi != nullptr, LOAF_ERR_ARG, "phi is NULL");
-    LOAF_REQUIRE(mode == LOAF_MODE_FULL || mode == LOAF_MODE_LO, LOAF_ERR_ARG, "unknown mode");
+    LOAF_REQUIRE(mode == LOAF_MODE_FULL || mode == LOAF_MODE_LO || mode == LOAF_MODE_LO_JK, LOAF_ERR_ARG,
+                 "unknown mode");
+    LOAF_REQUIRE(mode != LOAF_MODE_LO_JK || c->closed, LOAF_ERR_UNSUPPORTED,
+                 "the compressed Coulomb (LO_JK) is defined for closed shells");
     LOAF_REQUIRE(precision == LOAF_PREC_FP64 || precision == LOAF_PREC_FP16X3 ||
                      precision == LOAF_PREC_BF16X3,
                  LOAF_ERR_ARG, "unknown precision");
-    LOAF_REQUIRE(mode != LOAF_MODE_LO || c->compressed, LOAF_ERR_NOT_READY,
+    LOAF_REQUIRE(mode == LOAF_MODE_FULL || c->compressed, LOAF_ERR_NOT_READY,
                  "LO mode needs lo_localize_compress");
 }
 
@@ -361,7 +364,7 @@ void energy_batch(loaf_ctx* c, int W, const double2* dphi, int mode, int precisi
                   double2* dld, int* dst, int* dbad, int* dtimeout) {
     // the LO split-precision path forms Delta on the tensor cores; the FP64
     // path and the full mode use the FP64 Theta kernel
-    const bool tc_theta = precision != LOAF_PREC_FP64 && mode == LOAF_MODE_LO;
+    const bool tc_theta = precision != LOAF_PREC_FP64 && mode != LOAF_MODE_FULL;
     if (tc_theta) {
         run_theta_tc(c, W, dphi, precision);
     } else {
@@ -382,6 +385,10 @@ void energy_batch(loaf_ctx* c, int W, const double2* dphi, int mode, int precisi
         } else {
             StageScope sc(c, "exchange_lo_fp64", 2 * c->nspin);
             run_energy_fp64_lo(c, W, c->w_theta.as<double2>(), ek, c->w_part.as<double2>());
+        }
+        if (mode == LOAF_MODE_LO_JK) {
+            StageScope sc(c, "coulomb_lo_fp64", 2);
+            run_coulomb_lo_fp64(c, W, c->w_theta.as<double2>(), ej, c->w_part.as<double2>());
         }
     } else {
         run_energy_mixed(c, W, mode, precision, tc_theta ? nullptr : c->w_theta.as<double2>(),

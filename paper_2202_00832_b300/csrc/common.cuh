@@ -224,10 +224,15 @@ struct MixedOps {
     DevBuf s_pt, s_pt0, s_npt, s_pw;
     int s_n_pt = 0, screen_built = -1;
     double s_EK0 = 0.0;
+    // compressed Coulomb (closed shell): the same tiles with the pair's
+    // orbitals swapped, row constants {inv_su, inv_sv, U.Phi_i, V.Phi_j},
+    // per-pair trial parts, weights 2 (1 or 2) and their trial sum
+    DevBuf pt_J, row_cJ, e0_J, pw_J;
+    double EJ0 = 0.0;
     void release() {
         for (DevBuf* b : {&L_hi, &L_lo, &L_inv, &J0, &U_hi, &U_lo, &V_hi, &V_lo, &row_c, &pt,
                           &pair_pt0, &pair_npt, &pair_w, &e0, &s_pt, &s_pt0, &s_npt, &s_pw,
-                          &Lb_hi, &Lb_lo, &Ub_hi, &Ub_lo, &Vb_hi, &Vb_lo})
+                          &Lb_hi, &Lb_lo, &Ub_hi, &Ub_lo, &Vb_hi, &Vb_lo, &pt_J, &row_cJ, &e0_J, &pw_J})
             b->release();
         coul_ready = lo_ready = false;
         screen_built = -1;
@@ -351,6 +356,8 @@ void run_energy_fp64_full(loaf_ctx* c, int W, const double2* theta, double2* e_o
 void run_energy_fp64_lo(loaf_ctx* c, int W, const double2* theta, double2* e_out,
                         double2* e_pairs);
 void run_coulomb_fp64(loaf_ctx* c, int W, const double2* theta, double2* e_part);
+// E_J from the compressed pair factors (closed shell): 2 sum_ij (Ubar^T Theta_i).(Vbar Theta_j)
+void run_coulomb_lo_fp64(loaf_ctx* c, int W, const double2* theta, double2* ej_out, double2* scratch);
 void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2* theta,
                       double2* e_out, double2* e_pairs);
 void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision);

@@ -388,4 +388,27 @@ void run_energy_fp64_lo(loaf_ctx* c, int W, const double2* theta, double2* ek_ou
     }
 }
 
+// The pair kernel with i and j exchanged gives d_ij = (Ubar^T Theta_i).(Vbar Theta_j);
+// E_J = 2 sum_ij d_ij = 2 (sum_i d_ii + 2 sum_{i<j} d_ij)  (closed shell, eq. 2e_HR_RCAS)
+void run_coulomb_lo_fp64(loaf_ctx* c, int W, const double2* theta, double2* ej_out, double2* scratch) {
+    LOAF_REQUIRE(c->nspin == 1, LOAF_ERR_UNSUPPORTED, "the compressed Coulomb is defined for closed shells");
+    const SpinData& sd = c->sp[0];
+    const PairTable& pt = sd.pairs;
+    if (pt.npairs == 0) {
+        LOAF_CUDA(cudaMemsetAsync(ej_out, 0, (size_t)W * sizeof(double2), c->stream));
+        return;
+    }
+    const size_t smem = (size_t)2 * kLW * c->M * sizeof(double2);
+    LOAF_CUDA(cudaFuncSetAttribute(pair_exchange_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+    pair_exchange_fp64_kernel<<<dim3(pt.npairs, ceil_div(W, kLW)), kThreads, smem, c->stream>>>(
+        c->M, W, c->ntot, sd.col0, pt.d_j.as<int>(), pt.d_i.as<int>(), pt.d_K.as<int>(), pt.d_off.as<long>(),
+        pt.d_U.as<double>(), pt.d_V.as<double>(), theta, scratch);
+    LOAF_LAUNCH_CHECK();
+    pair_reduce_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(pt.npairs, W, pt.d_i.as<int>(),
+                                                                pt.d_j.as<int>(), scratch, nullptr, 2.0,
+                                                                ej_out, 0);
+    LOAF_LAUNCH_CHECK();
+}
+
 }  // namespace loaf

@@ -933,11 +933,17 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     mx.V_hi.ensure((size_t)Rb * mx.r_pad * 2);
     mx.V_lo.ensure((size_t)Rb * mx.r_pad * 2);
     mx.row_c.ensure((size_t)Rb * sizeof(float4));
-    DevBuf inv_u, inv_v, pbuf, qbuf;
+    DevBuf inv_u, inv_v, pbuf, qbuf, pJ, qJ;
     inv_u.ensure(Rb * sizeof(float));
     inv_v.ensure(Rb * sizeof(float));
     pbuf.ensure(Rb * sizeof(double));
     qbuf.ensure(Rb * sizeof(double));
+    const bool jk = c->nspin == 1;  // the compressed Coulomb is built for closed shells
+    if (jk) {
+        pJ.ensure(Rb * sizeof(double));
+        qJ.ensure(Rb * sizeof(double));
+        mx.e0_J.ensure(std::max(npairs, 1) * sizeof(double));
+    }
     mx.e0.ensure(std::max(npairs, 1) * sizeof(double));
     mx.pair_w.ensure(std::max(npairs, 1) * sizeof(double));
 
@@ -976,6 +982,13 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
                 pt.d_i.as<int>(), pt.d_j.as<int>(), sd.d_trial.as<double>(), sd.N,
                 pbuf.as<double>() + row_base, qbuf.as<double>() + row_base);
             LOAF_LAUNCH_CHECK();
+            if (jk) {  // i and j exchanged: U row . Phi_i, V row . Phi_j
+                pq_kernel<<<ceil_div(pt.rows, 8), 256, 0, c->stream>>>(
+                    M, pt.rows, pt.d_U.as<double>(), pt.d_V.as<double>(), d_rp.as<int>(),
+                    pt.d_j.as<int>(), pt.d_i.as<int>(), sd.d_trial.as<double>(), sd.N,
+                    pJ.as<double>() + row_base, qJ.as<double>() + row_base);
+                LOAF_LAUNCH_CHECK();
+            }
             LOAF_CUDA(cudaStreamSynchronize(c->stream));  // d_rp goes out of scope
         }
         // e0 per pair (pair offsets are spin-local rows)
@@ -990,6 +1003,12 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
                 pt.npairs, d_off.as<long>(), pt.d_K.as<int>(), pbuf.as<double>(),
                 qbuf.as<double>(), mx.e0.as<double>() + pair_base);
             LOAF_LAUNCH_CHECK();
+            if (jk) {
+                pair_e0_kernel<<<ceil_div(std::max(pt.npairs, 1), 128), 128, 0, c->stream>>>(
+                    pt.npairs, d_off.as<long>(), pt.d_K.as<int>(), pJ.as<double>(), qJ.as<double>(),
+                    mx.e0_J.as<double>() + pair_base);
+                LOAF_LAUNCH_CHECK();
+            }
             LOAF_CUDA(cudaStreamSynchronize(c->stream));
         }
         // pair tiles in 8 x 8 orbital blocks (pairs sharing orbitals run together)
@@ -1029,6 +1048,13 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
                                                                  mx.row_c.as<float4>());
         LOAF_LAUNCH_CHECK();
     }
+    if (jk && R > 0) {
+        mx.row_cJ.ensure((size_t)Rb * sizeof(float4));
+        row_consts_kernel<<<ceil_div(R, 256), 256, 0, c->stream>>>(R, inv_u.as<float>(), inv_v.as<float>(),
+                                                                 pJ.as<double>(), qJ.as<double>(),
+                                                                 mx.row_cJ.as<float4>());
+        LOAF_LAUNCH_CHECK();
+    }
     mx.n_pt = (int)tiles.size();
     mx.pt.ensure(std::max<size_t>(tiles.size(), 1) * sizeof(int4));
     mx.pair_pt0.ensure(std::max(npairs, 1) * sizeof(int));
@@ -1045,6 +1071,32 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     double ek0 = 0.0;
     for (int n = 0; n < npairs; ++n) ek0 += pw[n] * e0[n];
     mx.EK0 = ek0;
+    if (jk) {
+        // E_J = 2 sum_ij d_ij: weight 2 (diagonal) or 4; tiles with the orbitals exchanged
+        std::vector<double> e0J(npairs), pwJ(npairs);
+        if (npairs > 0)
+            LOAF_CUDA(cudaMemcpyAsync(e0J.data(), mx.e0_J.ptr, npairs * sizeof(double), cudaMemcpyDeviceToHost,
+                                      c->stream));
+        std::vector<int4> tJ(tiles);
+        for (int4& t : tJ) t.z = ((t.z & 0xffff) << 16) | (t.z >> 16);
+        mx.pt_J.ensure(std::max<size_t>(tJ.size(), 1) * sizeof(int4));
+        if (!tJ.empty())
+            LOAF_CUDA(cudaMemcpyAsync(mx.pt_J.ptr, tJ.data(), tJ.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                      c->stream));
+        LOAF_CUDA(cudaStreamSynchronize(c->stream));
+        const PairTable& pt0t = c->sp[0].pairs;
+        double ej0 = 0.0;
+        for (int n = 0; n < npairs; ++n) {
+            pwJ[n] = pt0t.i[n] == pt0t.j[n] ? 2.0 : 4.0;
+            ej0 += pwJ[n] * e0J[n];
+        }
+        mx.pw_J.ensure(std::max(npairs, 1) * sizeof(double));
+        if (npairs > 0)
+            LOAF_CUDA(cudaMemcpyAsync(mx.pw_J.ptr, pwJ.data(), npairs * sizeof(double), cudaMemcpyHostToDevice,
+                                      c->stream));
+        LOAF_CUDA(cudaStreamSynchronize(c->stream));
+        mx.EJ0 = ej0;
+    }
     mx.h_tiles = tiles;
     mx.h_pt0 = pt0;
     mx.h_npt = npt;
@@ -1140,7 +1192,7 @@ int lo_max_clusters(loaf_ctx* c) {
 void setup_mixed_operands(loaf_ctx* c, int mode, bool bf16) {
     MixedOps& mx = c->mix[bf16 ? 1 : 0];
     ensure_coulomb_ops(c, mx, bf16);
-    if (mode == LOAF_MODE_LO) ensure_lo_ops(c, mx, bf16);
+    if (mode != LOAF_MODE_FULL) ensure_lo_ops(c, mx, bf16);
 }
 
 void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2* theta,
@@ -1148,7 +1200,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
     const bool bf16 = precision == LOAF_PREC_BF16X3;
     MixedOps& mx = c->mix[bf16 ? 1 : 0];
     if (e_out) ensure_coulomb_ops(c, mx, bf16);
-    if (mode == LOAF_MODE_LO) ensure_lo_ops(c, mx, bf16);
+    if (mode != LOAF_MODE_FULL) ensure_lo_ops(c, mx, bf16);
     mx.r_pad = (c->M + 7) / 8 * 8;
     mx.kflat = (long)c->ntot * mx.r_pad;
 
@@ -1218,7 +1270,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             c->w_red.as<double2>(), e_out, e_out + W);
         LOAF_LAUNCH_CHECK();
     }
-    if (mode == LOAF_MODE_LO) {
+    if (mode != LOAF_MODE_FULL) {
         // ---- LO pair exchange on the tensor cores ----
         double2* ek = e_out ? e_out + 2 * W : nullptr;
         // energies honour the pair screen; pair values are always for every pair
@@ -1230,7 +1282,9 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         const int* list_npt = screened ? mx.s_npt.as<int>() : mx.pair_npt.as<int>();
         const double* list_pw = screened ? mx.s_pw.as<double>() : mx.pair_w.as<double>();
         const double list_ek0 = screened ? mx.s_EK0 : mx.EK0;
-        if (n_pt > 0) {
+        // one launch of the CTA-pair kernel over a tile list with its row constants
+        auto launch_lo = [&](const int4* tiles, int ntiles, const float4* rowc, const char* stage) {
+            if (ntiles <= 0) return;
             LoParams P;
             P.u_hi = mx.Ub_hi.as<uint16_t>();
             P.u_lo = mx.Ub_lo.as<uint16_t>();
@@ -1239,19 +1293,19 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             P.d_hi = c->w_dhi.as<uint16_t>();
             P.d_lo = c->w_dlo.as<uint16_t>();
             P.nrb = dg.nrb;
-            P.pt = tile_list;
-            P.rowc = mx.row_c.as<float4>();
+            P.pt = tiles;
+            P.rowc = rowc;
             P.inv_t = inv_t;
-            P.n_pt = n_pt;
+            P.n_pt = ntiles;
             P.n_wt = n_wt;
             P.W = W;
             P.ldp = Wpad;
             P.nk = dg.nkb;
             P.idesc = idesc;
             P.err = err;
-            c->w_lopart.ensure((size_t)n_pt * Wpad * sizeof(double2));
+            c->w_lopart.ensure((size_t)ntiles * Wpad * sizeof(double2));
             P.part = c->w_lopart.as<double2>();
-            const int units = (n_pt / 2) * n_wt;
+            const int units = (ntiles / 2) * n_wt;
             const int n_cl = std::max(1, std::min({units, lo_max_clusters(c), c->persistent_grid() / 2}));
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
@@ -1265,10 +1319,11 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             cfg.stream = c->stream;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            StageScope lsc(c, "lo_exchange_tc", 1);
+            StageScope lsc(c, stage, 1);
             LOAF_CUDA(cudaLaunchKernelEx(&cfg, lo_exchange_tc_kernel, P));
             LOAF_LAUNCH_CHECK();
-        }
+        };
+        launch_lo(tile_list, n_pt, mx.row_c.as<float4>(), "lo_exchange_tc");
         c->w_lopart.ensure(16);
         StageScope lrs(c, "lo_reduce", ek ? 2 : 1);
         const int nsl = std::max(1, std::min(kRedSlices, mx.n_pairs));
@@ -1280,6 +1335,20 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         if (ek) {
             lo_tc_final_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(W, nsl, list_ek0,
                                                                       c->w_red.as<double2>(), ek);
+            LOAF_LAUNCH_CHECK();
+        }
+        lrs.end();
+        if (mode == LOAF_MODE_LO_JK && e_out) {
+            // E_J from the compressed factors replaces the exact Coulomb term:
+            // the pair's orbitals exchanged, every pair (the screen is for exchange)
+            launch_lo(mx.pt_J.as<int4>(), mx.n_pt, mx.row_cJ.as<float4>(), "lo_coulomb_tc");
+            StageScope jrs(c, "lo_coulomb_reduce", 2);
+            lo_tc_reduce_kernel<<<dim3(ceil_div(W, 32), nsl), 256, 0, c->stream>>>(
+                mx.n_pairs, W, Wpad, mx.pair_pt0.as<int>(), mx.pair_npt.as<int>(), mx.pw_J.as<double>(),
+                mx.e0_J.as<double>(), c->w_lopart.as<double2>(), c->w_red.as<double2>(), nullptr);
+            LOAF_LAUNCH_CHECK();
+            lo_tc_final_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(W, nsl, mx.EJ0, c->w_red.as<double2>(),
+                                                                      e_out + W);
             LOAF_LAUNCH_CHECK();
         }
     } else if (e_out) {

@@ -18,10 +18,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblo_afqmc.so")
 
-MODE_FULL, MODE_LO = 0, 1
+MODE_FULL, MODE_LO, MODE_LO_JK = 0, 1, 2
 PREC_FP64, PREC_FP16X3, PREC_BF16X3 = 0, 1, 2
 PRECISIONS = {"fp64": PREC_FP64, "fp16x3": PREC_FP16X3, "bf16x3": PREC_BF16X3}
-MODES = {"full": MODE_FULL, "lo": MODE_LO}
+MODES = {"full": MODE_FULL, "lo": MODE_LO, "lo_jk": MODE_LO_JK}
 
 STATUS = {0: "LOAF_OK", 1: "LOAF_ERR_ARG", 2: "LOAF_ERR_SHAPE", 3: "LOAF_ERR_CUDA",
           4: "LOAF_ERR_OOM", 5: "LOAF_ERR_SINGULAR", 6: "LOAF_ERR_NOT_READY",
