@@ -512,7 +512,9 @@ constexpr int kGJMaxCols = (LOAF_MAX_NOCC + 15) / 16;  // columns per thread of 
 // block form of Z:
 //   Bt[s][w][2k + ro][2j + ri] = {Zr, -Zi, Zi, Zr}[ri][ro] (j, k) / 2^g_k,
 // the B operand of the Theta GEMM (Theta = [phi_re phi_im] B, column pairs).
-__global__ void __launch_bounds__(256)
+constexpr int kGJThreads = 256;  // update grid: 16 row groups x 16 column groups
+
+__global__ void __launch_bounds__(kGJThreads)
 gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint16_t* __restrict__ Bt,
                     int* __restrict__ col_exp, int* __restrict__ gmax, double2* __restrict__ ld_part,
                     int* __restrict__ st_part) {
@@ -543,7 +545,9 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
         s_swaps = 0;
     }
     __syncthreads();
+    __shared__ float4 s_akk;
     for (int k = 0; k < N && s_flag == 0; ++k) {
+        // phase A (one warp): pivot row p of column k, 1/pivot, the old A[k][k]
         if (tid < 32) {
             float best = -1.f;
             int bi = k;
@@ -561,6 +565,7 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
                 s_p = bi;
                 piv[k] = bi;
                 if (bi != k) s_swaps += 1;
+                s_akk = A[k * N + k];
                 const double2 pv = cdf_to(A[bi * N + k]);
                 if (!(mag2(pv) > s_tol)) {
                     s_flag = 1;
@@ -573,37 +578,42 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
         __syncthreads();
         if (s_flag) break;
         const int p = s_p;
-        if (p != k)
-            for (int c = tid; c < N; c += blockDim.x) {
-                const float4 t = A[k * N + c];
-                A[k * N + c] = A[p * N + c];
-                A[p * N + c] = t;
-            }
-        __syncthreads();
         const float4 inv = s_inv;
-        for (int i = tid; i < N; i += blockDim.x) colk[i] = A[i * N + k];
+        // phase B: exchange rows k and p, scale the new row k (A[k][k] = 1/pivot),
+        // and take column k of the other rows (row p's entry is the old A[k][k])
+        for (int j = tid; j < N; j += blockDim.x) {
+            const float4 rk = A[k * N + j];
+            const float4 rp = p != k ? A[p * N + j] : rk;
+            if (p != k) A[p * N + j] = rk;
+            A[k * N + j] = j == k ? inv : cdf_mul(rp, inv);
+        }
+        for (int i = tid; i < N; i += blockDim.x)
+            if (i != k) colk[i] = i == p ? s_akk : A[i * N + k];
         __syncthreads();
-        // pivot row: A[k][j] *= 1/pv, with A[k][k] = 1/pv
-        for (int j = tid; j < N; j += blockDim.x)
-            A[k * N + j] = j == k ? inv : cdf_mul(A[k * N + j], inv);
-        __syncthreads();
-        // other rows: A[i][j] -= A[i][k] (old) * A[k][j] (new); A[i][k] starts from 0
+        // phase C: other rows, A[i][j] -= A[i][k] (old) * A[k][j] (new); A[i][k]
+        // starts from 0.  Each thread's columns are loaded, updated and stored
+        // as a group so that their independent error-free chains interleave.
         float4 u[kGJMaxCols];
 #pragma unroll
         for (int q = 0; q < kGJMaxCols; ++q) {
             const int j = tj + 16 * q;
             u[q] = j < N ? A[k * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        for (int i = ti; i < N; i += 16) {
+        for (int i = ti; i < N; i += kGJThreads / 16) {
             if (i == k) continue;
             const float4 f = colk[i];
+            float4 v[kGJMaxCols];
 #pragma unroll
             for (int q = 0; q < kGJMaxCols; ++q) {
                 const int j = tj + 16 * q;
-                if (j < N) {
-                    const float4 v = j == k ? make_float4(0.f, 0.f, 0.f, 0.f) : A[i * N + j];
-                    A[i * N + j] = cdf_sub_mul(v, f, u[q]);
-                }
+                v[q] = (j < N && j != k) ? A[i * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < kGJMaxCols; ++q) v[q] = cdf_sub_mul(v[q], f, u[q]);
+#pragma unroll
+            for (int q = 0; q < kGJMaxCols; ++q) {
+                const int j = tj + 16 * q;
+                if (j < N) A[i * N + j] = v[q];
             }
         }
         __syncthreads();
@@ -801,7 +811,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
                                 2 * N * sizeof(int) + 16;
             LOAF_CUDA(cudaFuncSetAttribute(gauss_jordan_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            gauss_jordan_kernel<<<W, 256, smem, c->stream>>>(
+            gauss_jordan_kernel<<<W, kGJThreads, smem, c->stream>>>(
                 N, kpad, W, c->w_oz_S.as<double2>(), Bt + bt_spin * s, cexp(s), gmx(s),
                 c->w_logdet.as<double2>() + (size_t)s * W, c->w_status.as<int>() + (size_t)s * W);
             LOAF_LAUNCH_CHECK();
