@@ -405,10 +405,24 @@ void energy_batch(loaf_ctx* c, int W, const double2* dphi, int mode, int precisi
     }
 }
 
-// walkers per upload chunk for a host array of W walkers (0: one piece)
-int host_chunk(int W) {
-    if (W < 512) return 0;
-    return ceil_div(ceil_div(W, 4), 128) * 128;
+// Upload chunks for a host array of W walkers (empty: one piece).  Uploading a
+// walker takes about two thirds of the time computing it takes, so the chunks
+// start small (computing starts early) and grow by about 1.5x, each uploaded
+// while the previous one computes; sizes are whole 128-walker tiles, the last
+// takes the rest.  Even and odd chunks alternate between two device buffers;
+// any two chunks add up to at most W walkers, so both fit in the workspace.
+std::vector<int> host_chunks(int W) {
+    std::vector<int> v;
+    if (W < 512) return v;
+    int c = ceil_div(ceil_div(W, 8), 128) * 128, rem = W;
+    while (rem > 0) {
+        int take = std::min(c, rem);
+        if (rem - take < 128) take = rem;
+        v.push_back(take);
+        rem -= take;
+        c = ceil_div(c * 3 / 2, 128) * 128;
+    }
+    return v;
 }
 
 }  // namespace
@@ -427,8 +441,8 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
         int* dst = reinterpret_cast<int*>(dld + W);
         int* dflags = dst + W;  // [worst status, timeout]
         LOAF_CUDA(cudaMemsetAsync(dflags, 0, 2 * sizeof(int), c->stream));
-        const int Wc = is_device_ptr(phi) ? 0 : host_chunk(W);
-        if (Wc == 0) {
+        const std::vector<int> chunks = is_device_ptr(phi) ? std::vector<int>{} : host_chunks(W);
+        if (chunks.empty()) {
             const double2* dphi;
             {
                 StageScope sc(c, "h2d_walkers", 0);
@@ -436,8 +450,7 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
             }
             energy_batch(c, W, dphi, mode, precision, de, dld, dst, dflags, dflags + 1);
         } else {
-            // upload chunk k + 1 on the copy stream while chunk k computes; two
-            // device buffers of Wc walkers alternate
+            // upload chunk k + 1 on the copy stream while chunk k computes
             if (!c->copy_stream) {
                 LOAF_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
                 for (cudaEvent_t* e : {&c->ev_start, &c->ev_copied[0], &c->ev_copied[1], &c->ev_free[0],
@@ -446,11 +459,14 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
             }
             const size_t per_w = (size_t)c->M * c->ntot;
             const double2* hphi = static_cast<const double2*>(phi);
-            double2* buf[2] = {c->w_phi.as<double2>(), c->w_phi.as<double2>() + (size_t)Wc * per_w};
+            int even_max = 0;
+            for (size_t k = 0; k < chunks.size(); k += 2) even_max = std::max(even_max, chunks[k]);
+            double2* buf[2] = {c->w_phi.as<double2>(), c->w_phi.as<double2>() + (size_t)even_max * per_w};
             LOAF_CUDA(cudaEventRecord(c->ev_start, c->stream));  // earlier users of w_phi are done
             LOAF_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_start, 0));
-            for (int k = 0, w0 = 0; w0 < W; ++k, w0 += Wc) {
-                const int b = k & 1, Wk = std::min(Wc, W - w0);
+            int w0 = 0;
+            for (size_t k = 0; k < chunks.size(); ++k) {
+                const int b = (int)(k & 1), Wk = chunks[k];
                 if (k >= 2) LOAF_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_free[b], 0));
                 LOAF_CUDA(cudaMemcpyAsync(buf[b], hphi + (size_t)w0 * per_w, (size_t)Wk * per_w * sizeof(double2),
                                           cudaMemcpyHostToDevice, c->copy_stream));
@@ -459,6 +475,7 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
                 energy_batch(c, Wk, buf[b], mode, precision, de + w0, dld + w0, dst + w0, dflags,
                              dflags + 1);
                 LOAF_CUDA(cudaEventRecord(c->ev_free[b], c->stream));
+                w0 += Wk;
             }
         }
         deliver(c, e_out, de, (size_t)W * sizeof(double2));

@@ -129,7 +129,7 @@ def test_naphthalene_scale_long_contractions():
 
 def test_host_walkers_are_uploaded_in_chunks(chain_lo):
     """Host walker arrays of W >= 512 are uploaded chunk by chunk while the previous
-    chunk computes (three chunks of 256, 256 and 8 here).  Per-walker results equal
+    chunk computes (chunks of 128, 256 and 136 here).  Per-walker results equal
     those of one device-resident batch up to the summation order of the Coulomb
     split, which depends on the batch size; the first walkers also match the oracle."""
     import torch
