@@ -106,14 +106,28 @@ __device__ inline unsigned long long abs_key(double v) {
 }
 
 // six balanced base-128 digits of x = v 2^-E (|x| <= 1/4), most significant first
-__device__ inline void digits6(double v, int E, int (&d)[kNS]) {
-    long long X = round_scaled(v, 42 - E);
+__device__ inline void digits_of(long long X, int (&d)[kNS]) {
 #pragma unroll
     for (int s = kNS - 1; s >= 0; --s) {
         const int r = (int)((X + 64) & 127) - 64;
         d[s] = r;
         X = (X - r) >> 7;
     }
+}
+__device__ inline void digits6(double v, int E, int (&d)[kNS]) { digits_of(round_scaled(v, 42 - E), d); }
+
+// round(v 2^s) for a float v, from its bit pattern (|v| 2^s < 2^62)
+__device__ inline long long round_scaled_f(float v, int s) {
+    const int b = __float_as_int(v);
+    const int ex = (b >> 23) & 0xff;
+    if (ex == 0) return 0;  // zero or subnormal
+    const long long m = (b & 0x7fffff) | 0x800000;  // 24-bit significand
+    const int sh = 150 - ex - s;                     // v 2^s = m 2^-sh
+    long long r;
+    if (sh <= 0) r = m << (-sh);
+    else if (sh > 25) r = 0;
+    else r = (m + (1LL << (sh - 1))) >> sh;
+    return b < 0 ? -r : r;
 }
 
 __device__ inline uint16_t h16(int d) { return __half_as_ushort(__int2half_rn(d)); }
@@ -459,6 +473,23 @@ __device__ inline dfl df_from(double x) {
     return r;
 }
 __device__ inline double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
+// hi + lo = x (to about 2^-48 relative) from the bit pattern of x with FP32 and
+// integer operations only: hi keeps the top 24 significand bits (truncated),
+// lo the remaining 29, rounded to a float.  |x| within the float range.
+__device__ inline dfl df_split_bits(double x) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    // fast range: 2^(ex - 1075) (the unit of lo) and hi both normal floats
+    if (ex < 1075 - 126 || ex > 1023 + 127) return df_from(x);
+    const long long m = (b & 0xfffffffffffffLL) | 0x10000000000000LL;  // 53 bits
+    const long long mh = m >> 29, ml = m & ((1LL << 29) - 1);
+    const float sgn = b < 0 ? -1.f : 1.f;
+    // x = (mh 2^29 + ml) 2^(ex - 1075)
+    dfl r;
+    r.hi = sgn * __int_as_float((int)((ex - 1023 + 127) << 23) | (int)(mh & 0x7fffff));
+    r.lo = sgn * __fmul_rn(__int2float_rn((int)ml), __int_as_float((ex - 1075 + 127) << 23));
+    return r;
+}
 __device__ inline dfl df_neg(dfl a) { return dfl{-a.hi, -a.lo}; }
 // c + a b.  The _rn intrinsics are never contracted into FMAs, which would
 // break the error-free sums.
@@ -532,12 +563,16 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
     const int w = blockIdx.x, tid = threadIdx.x;
     const int ti = tid >> 4, tj = tid & 15;  // 16 x 16 grid over the matrix
     double m = 0.0;
+    float mf = 0.f;
+    bool finite = true;
     for (int e = tid; e < N * N; e += blockDim.x) {
         const double2 z = S[(size_t)w * N * N + e];
-        A[e] = cdf_from(z);
-        m = fmax(m, mag2(z));
+        const dfl zr = df_split_bits(z.x), zi = df_split_bits(z.y);
+        A[e] = make_float4(zr.hi, zr.lo, zi.hi, zi.lo);
+        mf = fmaxf(mf, fmaf(zr.hi, zr.hi, zi.hi * zi.hi));
+        finite = finite && isfinite(zr.hi) && isfinite(zi.hi);
     }
-    m = block_max_d(m, red_v);
+    m = block_max_d(finite ? (double)mf : (double)INFINITY, red_v);
     if (tid == 0) {
         const double tol = (double)N * 2.220446049250313e-16 * sqrt(m);
         s_tol = tol * tol;
@@ -662,15 +697,15 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
     // per-column exponents of Z (one warp per column)
     const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     for (int k = wid; k < N; k += nw) {
-        double mm = 0.0;
+        float mm = 0.f;  // leading parts: |z| <= |hi| (1 + 2^-23), within the 2-bit headroom
         if (flag == 0)
             for (int j = lane; j < N; j += 32) {
-                const double2 z = cdf_to(A[j * N + k]);
-                mm = fmax(mm, fmax(fabs(z.x), fabs(z.y)));
+                const float4 z = A[j * N + k];
+                mm = fmaxf(mm, fmaxf(fabsf(z.x), fabsf(z.z)));
             }
-        for (int o = 16; o > 0; o >>= 1) mm = fmax(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+        for (int o = 16; o > 0; o >>= 1) mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
         if (lane == 0) {
-            const int g = slice_exponent(mm);
+            const int g = slice_exponent((double)mm);
             gk[k] = g;
             col_exp[(size_t)w * N + k] = g;
         }
@@ -685,13 +720,16 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
     for (int e = tid; e < twoN * twoN; e += blockDim.x) {
         const int cc = e / twoN, K = e % twoN;  // cc = 2k + ro, K = 2j + ri
         const int k = cc >> 1, ro = cc & 1, j = K >> 1, ri = K & 1;
-        double v = 0.0;
+        long long X = 0;
         if (flag == 0) {
-            const double2 z = cdf_to(A[j * N + k]);
-            v = (ri == ro) ? z.x : (ri ? -z.y : z.y);
+            // digits of hi + lo from the two parts (one more unit of rounding)
+            const float4 z = A[j * N + k];
+            float h = z.x, l = z.y;                                  // Zr
+            if (ri != ro) { h = ri ? -z.z : z.z; l = ri ? -z.w : z.w; }  // -Zi or Zi
+            X = round_scaled_f(h, 42 - gk[k]) + round_scaled_f(l, 42 - gk[k]);
         }
         int d[kNS];
-        digits6(v, gk[k], d);
+        digits_of(X, d);
 #pragma unroll
         for (int s = 0; s < kNS; ++s) Bt[(((size_t)s * W + w) * twoN + cc) * kpad + K] = h16(d[s]);
     }
