@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--tsvd-report", action="store_true",
                     help="the T_SVD sweep on the naphthalene-scale honeycomb instead of the throughput line: "
                          "compression, <M_SVD>, LO-vs-full and mixed-vs-FP64 errors, truncation bound")
+    ap.add_argument("--batch-report", action="store_true",
+                    help="walker-batching curve at pentacene scale instead of the throughput line: "
+                         "walker energies/s against the walkers per call (64 .. 4096)")
     ap.add_argument("--screen-cutoffs", default="1e-6,1e-3,1e-2,1e-1",
                     help="per-pair cutoffs (Ha) of the screen report")
     return ap.parse_args()
@@ -625,9 +628,50 @@ def tsvd_report(args):
                                       "rows": rows}}), flush=True)
 
 
+def batch_report(args):
+    """Throughput against the batch size at pentacene scale (LO, T_SVD = 1e-4,
+    FP16x3, device-resident walkers): one walkers_energy call per batch of W
+    walkers, W = 64 .. 4096 (walkers beyond the 1024 generated ones repeat)."""
+    import torch
+    from paper_2202_00832_b300.lo_afqmc import Context, position_operators
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    wl = synth.PENTACENE_440
+    mol = wl.molecule()
+    walk = wl.walkers(mol, processes=min(16, os.cpu_count() or 1))
+    ctx = Context(0, stream=stream.cuda_stream)
+    ctx.load_molecule(mol)
+    ctx.lo_localize_compress(args.threshold, position_operators(mol), localize=True)
+    rows = []
+    for W in [64, 128, 256, 512, 1024, 2048, 4096]:
+        reps = -(-W // len(walk))
+        phi = torch.from_numpy(np.concatenate([walk] * reps)[:W]).cuda()
+        e = torch.zeros(W, dtype=torch.complex128, device="cuda")
+        for _ in range(3):
+            ctx.walkers_energy(phi, mode="lo", precision=args.precision, e_out=e)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = max(3, 8192 // W)
+        ev0.record(stream)
+        for _ in range(n):
+            ctx.walkers_energy(phi, mode="lo", precision=args.precision, e_out=e)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / n
+        rows.append({"walkers_per_call": W, "ms_per_call": ms, "walker_energies_per_s": W / (ms / 1e3)})
+        del phi, e
+    print(json.dumps({"batch_report": {"workload": wl.name, "precision": args.precision, "rows": rows}}),
+          flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.batch_report:
+        if rank == 0:
+            batch_report(args)
+        return
     if args.tsvd_report:
         if rank == 0:
             tsvd_report(args)
