@@ -167,6 +167,14 @@ def energy_cholesky(h, L, trial_a, trial_b, phi_a, phi_b, e0: float = 0.0):
     return dict(E=e0 + e1 + ej - ek, E1=e1, EJ=ej, EK=ek, J=J, logdet=ld)
 
 
+def mixed_estimate_L(mol, phi: np.ndarray) -> np.ndarray:
+    """<L_g>_w = sum_sigma tr(Lbar^sigma_g Theta^sigma), g < X: the mixed
+    estimate of each Cholesky vector, from which importance sampling shifts the
+    auxiliary fields (the force bias, -sqrt(dtau) <L_g>, Sec. 2.1).  It is the
+    spin-summed trace vector J of energy_cholesky."""
+    return walker_energy(mol, phi)["J"]
+
+
 def split_walker(mol, phi: np.ndarray):
     """(phi_a, phi_b) from a packed walker: closed shell reuses one block."""
     na, nb = mol.n_alpha, mol.n_beta

@@ -190,3 +190,28 @@ def test_planted_mistakes_fail_a_pin(chain60, mistake):
     ref = E.energy_wick_dense(mol.h, V, G, G)[0]
     assert rel(_energy_variant(mol, phi, "none"), ref) < 1e-12
     assert rel(_energy_variant(mol, phi, mistake), ref) > 1e-6
+
+
+def test_mixed_estimate_of_L_at_the_trial_is_the_density_trace(chain60):
+    """At phi = Phi_T, Theta = Phi_T and <L_g> = sum_sigma tr(L_g P^sigma) with the
+    trial density P = Phi_T Phi_T^T (both spins for the closed shell)."""
+    mol, _ = chain60
+    phi = np.ascontiguousarray(mol.trial_a.astype(np.complex128))
+    got = E.mixed_estimate_L(mol, phi)
+    P = mol.trial_a @ mol.trial_a.T
+    ref = 2.0 * np.einsum("gpq,qp->g", mol.L, P)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_mixed_estimate_of_L_is_gauge_invariant(chain60):
+    """<L_g> depends on the walker's span only: phi R gives the same vector, and
+    a Theta formed without the inverse overlap (phi instead of phi S^-1) fails."""
+    mol, walk = chain60
+    rng = np.random.default_rng(5)
+    R = rng.standard_normal((mol.n_alpha, mol.n_alpha)) + 1j * rng.standard_normal((mol.n_alpha, mol.n_alpha))
+    a = E.mixed_estimate_L(mol, walk[3])
+    b = E.mixed_estimate_L(mol, walk[3] @ R)
+    assert np.allclose(a, b, rtol=1e-10, atol=1e-10)
+    Lbar = E.half_rotate(mol.L, mol.trial_a)
+    wrong = lambda ph: 2.0 * np.einsum("gir,ri->g", Lbar, ph)   # planted: no S^-1
+    assert not np.allclose(wrong(walk[3]), wrong(walk[3] @ R), rtol=1e-6)
