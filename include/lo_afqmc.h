@@ -190,6 +190,21 @@ loaf_status walkers_energy_multi(loaf_ctx *const *ctxs, int n, const int *W, con
                                  int *sm_caps);
 
 /*
+ * walkers_force_bias -- the mixed estimate of every Cholesky vector,
+ * <L_g>_w = sum_sigma tr(Lbar^sigma_g Theta^sigma) (g < X), the quantity the
+ * importance-sampled propagation shifts the auxiliary fields by (the force
+ * bias -sqrt(dtau) <L_g>, Sec. 2.1; mean-field subtraction is the caller's).
+ * It is the Coulomb vector of walkers_energy, formed by the same kernels.
+ *   W, phi         as for walkers_energy (host or device)
+ *   precision      LOAF_PREC_FP64 or the split precisions
+ *   lbar_out       W x X complex128 (walker-major), host or device
+ *   logdet_out, walker_status  as for walkers_energy (may be NULL)
+ * Needs ao_load_cholesky only.  Errors as for walkers_energy.
+ */
+loaf_status walkers_force_bias(loaf_ctx *ctx, int W, const void *phi, int precision, void *lbar_out,
+                               void *logdet_out, int *walker_status);
+
+/*
  * walkers_theta -- the first stage alone: Theta = phi (Phi_T^T phi)^-1 and
  * log det, per spin (eq. Q).  theta_out: W x Ntot x M complex128 (orbital-
  * major: theta_out[w][i][r] = Theta_ri), logdet_out: W complex128.  The

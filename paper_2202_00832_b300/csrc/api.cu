@@ -761,6 +761,57 @@ loaf_status walkers_energy_multi(loaf_ctx* const* ctxs, int n, const int* W, con
     return st;
 }
 
+loaf_status walkers_force_bias(loaf_ctx* c, int W, const void* phi, int precision, void* lbar_out,
+                               void* logdet_out, int* walker_status) {
+    if (!c) return LOAF_ERR_ARG;
+    int flags[2] = {0, 0};
+    loaf_status st = guarded(c, [&] {
+        LOAF_CUDA(cudaSetDevice(c->device));
+        check_ready(c, W, phi, LOAF_MODE_FULL, precision);
+        LOAF_REQUIRE(lbar_out != nullptr, LOAF_ERR_ARG, "lbar_out is NULL");
+        ensure_workspace(c, W, LOAF_MODE_FULL);
+        const double2* dphi = stage_walkers(c, W, phi);
+        double2* de = c->w_host_stage.as<double2>();
+        double2* dld = de + W;
+        int* dst = reinterpret_cast<int*>(dld + W);
+        int* dflags = dst + W;
+        LOAF_CUDA(cudaMemsetAsync(dflags, 0, 2 * sizeof(int), c->stream));
+        const size_t X = (size_t)c->X;
+        if (precision == LOAF_PREC_FP64) {
+            stage_theta(c, W, dphi);
+            run_coulomb_fp64(c, W, c->w_theta.as<double2>(), c->w_out.as<double2>());
+            // rows g < X of the [W][X + 1] trace table
+            LOAF_CUDA(cudaMemcpy2DAsync(lbar_out, X * sizeof(double2), c->w_part2.ptr, (X + 1) * sizeof(double2),
+                                        X * sizeof(double2), W, cudaMemcpyDefault, c->stream));
+        } else {
+            run_theta_tc(c, W, dphi, precision);
+            c->w_z.ensure((size_t)W * X * sizeof(double2));
+            run_force_bias_mixed(c, W, precision, c->w_out.as<double2>(), c->w_z.as<double2>());
+            LOAF_CUDA(cudaMemcpyAsync(lbar_out, c->w_z.ptr, (size_t)W * X * sizeof(double2), cudaMemcpyDefault,
+                                      c->stream));
+            flag_or_kernel<<<1, 1, 0, c->stream>>>(c->w_flag.as<int>(), dflags + 1);
+            LOAF_LAUNCH_CHECK();
+        }
+        finalize_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
+            W, c->nspin, c->sp[0].mult, c->nspin > 1 ? c->sp[1].mult : 0.0, c->e0, c->w_logdet.as<double2>(),
+            c->w_status.as<int>(), nullptr, nullptr, nullptr, de, dld, dst, dflags);
+        LOAF_LAUNCH_CHECK();
+        deliver(c, logdet_out, dld, (size_t)W * sizeof(double2));
+        deliver(c, walker_status, dst, (size_t)W * sizeof(int));
+        LOAF_CUDA(cudaMemcpyAsync(flags, dflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        LOAF_CUDA(cudaStreamSynchronize(c->stream));
+    });
+    if (st == LOAF_OK && flags[1]) {
+        c->err = "a tensor-core kernel gave up waiting on a pipeline barrier";
+        return LOAF_ERR_TIMEOUT;
+    }
+    if (st == LOAF_OK && flags[0]) {
+        c->err = "at least one walker overlap is singular or non-finite";
+        return flags[0] == LOAF_WALKER_SINGULAR ? LOAF_ERR_SINGULAR : LOAF_ERR_NAN;
+    }
+    return st;
+}
+
 loaf_status walkers_pair_exchange(loaf_ctx* c, int W, const void* phi, int precision,
                                   void* e_pairs_out) {
     if (!c) return LOAF_ERR_ARG;

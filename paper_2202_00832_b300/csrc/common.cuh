@@ -358,6 +358,8 @@ void run_energy_fp64_lo(loaf_ctx* c, int W, const double2* theta, double2* e_out
 void run_coulomb_fp64(loaf_ctx* c, int W, const double2* theta, double2* e_part);
 // E_J from the compressed pair factors (closed shell): 2 sum_ij (Ubar^T Theta_i).(Vbar Theta_j)
 void run_coulomb_lo_fp64(loaf_ctx* c, int W, const double2* theta, double2* ej_out, double2* scratch);
+// <L_g>_w of the batch whose Delta tiles the tensor-core Theta stage wrote
+void run_force_bias_mixed(loaf_ctx* c, int W, int precision, double2* e_scratch, double2* j_out);
 void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2* theta,
                       double2* e_out, double2* e_pairs);
 void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision);

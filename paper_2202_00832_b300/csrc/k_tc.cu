@@ -774,7 +774,7 @@ __global__ void coulomb_tc_reduce_kernel(int X, int W, int n_split, int ldp,
                                          const float* __restrict__ inv_s,
                                          const float* __restrict__ inv_t,
                                          const double* __restrict__ J0,
-                                         double2* __restrict__ red_out) {
+                                         double2* __restrict__ red_out, double2* __restrict__ j_out) {
     // 32 walkers x 8 row groups
     __shared__ double2 red[8][32];
     const int wl = threadIdx.x & 31, gg = threadIdx.x >> 5;
@@ -793,6 +793,7 @@ __global__ void coulomb_tc_reduce_kernel(int X, int W, int n_split, int ldp,
             }
             const double f = (double)inv_s[g] * it;
             const double2 J = make_double2(J0[g] + re * f, im * f);
+            if (j_out) j_out[(size_t)w * X + g] = J;
             acc = cadd(acc, cmul(J, J));
         }
     }
@@ -1187,7 +1188,62 @@ int lo_max_clusters(loaf_ctx* c) {
     return n;
 }
 
+// One-body energy and Coulomb on the tensor cores from the Delta tiles of
+// this batch: e_out[0..W) = E1, e_out[W..2W) = E_J; j_out (optional, W x X)
+// receives <L_g>_w = sum_sigma tr(Lbar^sigma_g Theta^sigma).
+void coulomb_mixed(loaf_ctx* c, MixedOps& mx, int W, bool bf16, const float* inv_t, int* err,
+                   double2* e_out, double2* j_out) {
+    const DeltaGeom dg = delta_geom(c->M, c->ntot, W);
+    // ---- Coulomb + one-body on the tensor cores ----
+    CoulParams P;
+    P.a_hi = mx.Lb_hi.as<uint16_t>();
+    P.a_lo = mx.Lb_lo.as<uint16_t>();
+    P.b_hi = c->w_dhi.as<uint16_t>();
+    P.b_lo = c->w_dlo.as<uint16_t>();
+    P.nkb = dg.nkb;
+    P.nrb = dg.nrb;
+    P.rows = c->X + 1;
+    P.n_mt = mx.n_mt;
+    P.n_wt = ceil_div(2L * W, kCBN);
+    P.nk = c->ntot * dg.nkb;
+    const int tiles = P.n_mt * P.n_wt;
+    // the split fixes the chain boundaries of the FP32 accumulation, so it depends
+    // on the device only (not on an SM budget): results do not depend on scheduling
+    P.n_split = std::max(1, std::min(ceil_div(P.nk, kCGroup), (3 * c->sm_count + tiles - 1) / tiles));
+    P.ldp = P.n_wt * kCBN;
+    P.idesc = tc::idesc_f16(kBM, kCBN, bf16);
+    P.err = err;
+    c->w_cpart.ensure((size_t)P.n_split * P.rows * P.ldp * sizeof(double));
+    P.part = c->w_cpart.as<double>();
+    const int units = tiles * P.n_split;
+    LOAF_CUDA(cudaFuncSetAttribute(coulomb_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kCoulSmem));
+    StageScope csc(c, "coulomb_tc", 1);
+    coulomb_tc_kernel<<<std::min(units, c->persistent_grid()), kCThreads, kCoulSmem, c->stream>>>(P);
+    LOAF_LAUNCH_CHECK();
+    csc.end();
+    StageScope rsc(c, "coulomb_reduce", 2);
+    c->w_red.ensure((size_t)kRedSlices * W * sizeof(double2));
+    coulomb_tc_reduce_kernel<<<dim3(ceil_div(W, 32), kRedSlices), 256, 0, c->stream>>>(
+        c->X, W, P.n_split, P.ldp, P.part, mx.L_inv.as<float>(), inv_t, mx.J0.as<double>(),
+        c->w_red.as<double2>(), j_out);
+    LOAF_LAUNCH_CHECK();
+    coulomb_tc_final_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
+        c->X, W, P.n_split, P.ldp, kRedSlices, P.part, mx.L_inv.as<float>(), inv_t, mx.E1_0,
+        c->w_red.as<double2>(), e_out, e_out + W);
+    LOAF_LAUNCH_CHECK();
+}
+
 }  // namespace
+
+void run_force_bias_mixed(loaf_ctx* c, int W, int precision, double2* e_scratch, double2* j_out) {
+    const bool bf16 = precision == LOAF_PREC_BF16X3;
+    MixedOps& mx = c->mix[bf16 ? 1 : 0];
+    ensure_coulomb_ops(c, mx, bf16);
+    float* inv_t = c->w_dscale.as<float>();
+    c->w_flag.ensure(16);
+    coulomb_mixed(c, mx, W, bf16, inv_t, c->w_flag.as<int>(), e_scratch, j_out);
+}
 
 void setup_mixed_operands(loaf_ctx* c, int mode, bool bf16) {
     MixedOps& mx = c->mix[bf16 ? 1 : 0];
@@ -1232,44 +1288,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
     }
     const uint32_t idesc = tc::idesc_f16(2 * kBM, kBN, bf16);  // pair MMA: M = 256
 
-    if (e_out) {
-        // ---- Coulomb + one-body on the tensor cores ----
-        CoulParams P;
-        P.a_hi = mx.Lb_hi.as<uint16_t>();
-        P.a_lo = mx.Lb_lo.as<uint16_t>();
-        P.b_hi = c->w_dhi.as<uint16_t>();
-        P.b_lo = c->w_dlo.as<uint16_t>();
-        P.nkb = dg.nkb;
-        P.nrb = dg.nrb;
-        P.rows = c->X + 1;
-        P.n_mt = mx.n_mt;
-        P.n_wt = ceil_div(2L * W, kCBN);
-        P.nk = c->ntot * dg.nkb;
-        const int tiles = P.n_mt * P.n_wt;
-        P.n_split = std::max(1, std::min(ceil_div(P.nk, kCGroup), (3 * c->persistent_grid() + tiles - 1) / tiles));
-        P.ldp = P.n_wt * kCBN;
-        P.idesc = tc::idesc_f16(kBM, kCBN, bf16);
-        P.err = err;
-        c->w_cpart.ensure((size_t)P.n_split * P.rows * P.ldp * sizeof(double));
-        P.part = c->w_cpart.as<double>();
-        const int units = tiles * P.n_split;
-        LOAF_CUDA(cudaFuncSetAttribute(coulomb_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kCoulSmem));
-        StageScope csc(c, "coulomb_tc", 1);
-        coulomb_tc_kernel<<<std::min(units, c->persistent_grid()), kCThreads, kCoulSmem, c->stream>>>(P);
-        LOAF_LAUNCH_CHECK();
-        csc.end();
-        StageScope rsc(c, "coulomb_reduce", 2);
-        c->w_red.ensure((size_t)kRedSlices * W * sizeof(double2));
-        coulomb_tc_reduce_kernel<<<dim3(ceil_div(W, 32), kRedSlices), 256, 0, c->stream>>>(
-            c->X, W, P.n_split, P.ldp, P.part, mx.L_inv.as<float>(), inv_t, mx.J0.as<double>(),
-            c->w_red.as<double2>());
-        LOAF_LAUNCH_CHECK();
-        coulomb_tc_final_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
-            c->X, W, P.n_split, P.ldp, kRedSlices, P.part, mx.L_inv.as<float>(), inv_t, mx.E1_0,
-            c->w_red.as<double2>(), e_out, e_out + W);
-        LOAF_LAUNCH_CHECK();
-    }
+    if (e_out) coulomb_mixed(c, mx, W, bf16, inv_t, err, e_out, nullptr);
     if (mode != LOAF_MODE_FULL) {
         // ---- LO pair exchange on the tensor cores ----
         double2* ek = e_out ? e_out + 2 * W : nullptr;

@@ -41,6 +41,7 @@ SIGNATURES = [
     ("walkers_energy", _I, [_P, _I, _P, _I, _I, _P, _P, _P]),
     ("walkers_energy_multi", _I, [_P, _I, _P, _P, _I, _I, _P, _P, _P, _I, _P]),
     ("walkers_theta", _I, [_P, _I, _P, _P, _P, _P]),
+    ("walkers_force_bias", _I, [_P, _I, _P, _I, _P, _P, _P]),
     ("walkers_pair_exchange", _I, [_P, _I, _P, _I, _P]),
     ("loaf_num_pairs", _I, [_P]),
     ("lo_get_localized_trial", _I, [_P, _I, _P]),
@@ -239,6 +240,22 @@ class Context:
             return e_out, logdet_out, walker_status
         self._check(code, "walkers_energy")
         return e_out, logdet_out, walker_status
+
+    def walkers_force_bias(self, phi, precision="fp64", out=None, logdet_out=None,
+                           walker_status=None):
+        """<L_g>_w = sum_sigma tr(Lbar^sigma_g Theta^sigma), W x X complex128."""
+        _check_dtype(phi, "c16")
+        W = int(phi.shape[0])
+        if out is None:
+            out = np.zeros((W, self.X), dtype=np.complex128)
+        if logdet_out is None and isinstance(phi, np.ndarray):
+            logdet_out = np.zeros(W, dtype=np.complex128)
+        if walker_status is None and isinstance(phi, np.ndarray):
+            walker_status = np.zeros(W, dtype=np.int32)
+        self._check(self._lib.walkers_force_bias(self._h, W, _ptr(phi), PRECISIONS.get(precision, precision),
+                                                 _ptr(out), _ptr(logdet_out), _ptr(walker_status)),
+                    "walkers_force_bias")
+        return out, logdet_out, walker_status
 
     def walkers_theta(self, phi, theta_out=None, logdet_out=None, walker_status=None,
                       raise_on_singular: bool = True):
