@@ -175,6 +175,14 @@ def mixed_estimate_L(mol, phi: np.ndarray) -> np.ndarray:
     return walker_energy(mol, phi)["J"]
 
 
+def propagator_operator(mol, x: np.ndarray) -> np.ndarray:
+    """V = sum_g x_g L_g (M x M): the one-body operator of the Hubbard-Stratonovich
+    propagator for one walker's fields x (X complex values; the paper's
+    B = sum_alpha x_alpha L_alpha, with sqrt(dtau) and the force-bias shift
+    already in x)."""
+    return np.einsum("g,gpq->pq", x, mol.L, optimize=True)
+
+
 def split_walker(mol, phi: np.ndarray):
     """(phi_a, phi_b) from a packed walker: closed shell reuses one block."""
     na, nb = mol.n_alpha, mol.n_beta

@@ -215,3 +215,26 @@ def test_mixed_estimate_of_L_is_gauge_invariant(chain60):
     Lbar = E.half_rotate(mol.L, mol.trial_a)
     wrong = lambda ph: 2.0 * np.einsum("gir,ri->g", Lbar, ph)   # planted: no S^-1
     assert not np.allclose(wrong(walk[3]), wrong(walk[3] @ R), rtol=1e-6)
+
+
+def test_propagator_operator_pins(chain60):
+    """V = sum_g x_g L_g: a unit field picks out L_g; V is linear in x and
+    symmetric (every L_g is); a real x gives a real V."""
+    mol, _ = chain60
+    X = mol.X
+    e = np.zeros(X, dtype=np.complex128)
+    e[7] = 1.0
+    assert np.array_equal(E.propagator_operator(mol, e), mol.L[7].astype(np.complex128))
+    rng = np.random.default_rng(9)
+    x1 = rng.standard_normal(X) + 1j * rng.standard_normal(X)
+    x2 = rng.standard_normal(X) + 1j * rng.standard_normal(X)
+    v1, v2 = E.propagator_operator(mol, x1), E.propagator_operator(mol, x2)
+    assert np.allclose(E.propagator_operator(mol, 2.0 * x1 - 3j * x2), 2.0 * v1 - 3j * v2, atol=1e-10)
+    assert np.allclose(v1, v1.T, atol=1e-12)
+    vr = E.propagator_operator(mol, x1.real.astype(np.complex128))
+    assert np.abs(vr.imag).max() == 0.0
+    # an explicit loop over the fields
+    ref = np.zeros((mol.M, mol.M), dtype=np.complex128)
+    for g in range(X):
+        ref += x1[g] * mol.L[g]
+    assert np.allclose(v1, ref, rtol=1e-12, atol=1e-12)
