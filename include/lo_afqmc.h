@@ -205,6 +205,22 @@ loaf_status walkers_force_bias(loaf_ctx *ctx, int W, const void *phi, int precis
                                void *logdet_out, int *walker_status);
 
 /*
+ * walkers_propagator -- the one-body operator of each walker's propagator,
+ * V_w = sum_g x_wg L_g (M x M; the B = sum_alpha x_alpha L_alpha formation of
+ * the propagation step, Sec. 2.1 and Sec. 5), for fields x that already hold
+ * sqrt(dtau) and the force-bias shift.
+ *   W          >= 1 walkers
+ *   x          W x X complex128 fields (walker-major), host or device
+ *   precision  LOAF_PREC_FP64 (cuBLAS DGEMMs) or a split precision (one
+ *              tensor-core contraction over g with 16-bit hi + lo tiles)
+ *   v_out      W x M x M complex128 (v_out[w][p][q]), host or device
+ * Needs ao_load_cholesky only; L must be kept by the context (it is).  The
+ * split-precision operand tiles of L are built on the first call.
+ * Errors: LOAF_ERR_NOT_READY, LOAF_ERR_ARG, LOAF_ERR_OOM, LOAF_ERR_TIMEOUT.
+ */
+loaf_status walkers_propagator(loaf_ctx *ctx, int W, const void *x, int precision, void *v_out);
+
+/*
  * walkers_theta -- the first stage alone: Theta = phi (Phi_T^T phi)^-1 and
  * log det, per spin (eq. Q).  theta_out: W x Ntot x M complex128 (orbital-
  * major: theta_out[w][i][r] = Theta_ri), logdet_out: W complex128.  The

@@ -255,7 +255,7 @@ loaf_status loaf_destroy(loaf_ctx* c) {
                             &c->w_status, &c->w_out, &c->w_part, &c->w_part2, &c->w_dhi,
                             &c->w_dlo, &c->w_dscale, &c->w_host_stage, &c->w_cpart,
                             &c->w_lopart, &c->w_red, &c->w_flag, &c->d_keep, &c->w_oz_at, &c->w_oz_bs,
-                            &c->w_oz_bt, &c->w_oz_S, &c->w_oz_int})
+                            &c->w_oz_bt, &c->w_oz_S, &c->w_oz_int, &c->w_prop_x, &c->w_prop_part})
         b->release();
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     for (cudaEvent_t e : {c->ev_start, c->ev_copied[0], c->ev_copied[1], c->ev_free[0], c->ev_free[1]})
@@ -810,6 +810,41 @@ loaf_status walkers_force_bias(loaf_ctx* c, int W, const void* phi, int precisio
         return flags[0] == LOAF_WALKER_SINGULAR ? LOAF_ERR_SINGULAR : LOAF_ERR_NAN;
     }
     return st;
+}
+
+loaf_status walkers_propagator(loaf_ctx* c, int W, const void* x, int precision, void* v_out) {
+    if (!c) return LOAF_ERR_ARG;
+    return guarded(c, [&] {
+        LOAF_CUDA(cudaSetDevice(c->device));
+        LOAF_REQUIRE(c->loaded, LOAF_ERR_NOT_READY, "ao_load_cholesky has not been called");
+        LOAF_REQUIRE(W >= 1, LOAF_ERR_ARG, "W must be >= 1");
+        LOAF_REQUIRE(x != nullptr && v_out != nullptr, LOAF_ERR_ARG, "x or v_out is NULL");
+        LOAF_REQUIRE(precision == LOAF_PREC_FP64 || precision == LOAF_PREC_FP16X3 ||
+                         precision == LOAF_PREC_BF16X3,
+                     LOAF_ERR_ARG, "unknown precision");
+        const size_t xb = (size_t)W * c->X * sizeof(double2);
+        const size_t vb = (size_t)W * c->M * c->M * sizeof(double2);
+        const double2* dx = static_cast<const double2*>(x);
+        if (!is_device_ptr(x)) {
+            c->w_phi.ensure(xb);
+            LOAF_CUDA(cudaMemcpyAsync(c->w_phi.ptr, x, xb, cudaMemcpyHostToDevice, c->stream));
+            dx = c->w_phi.as<double2>();
+        }
+        double2* dv = static_cast<double2*>(v_out);
+        const bool v_host = !is_device_ptr(v_out);
+        if (v_host) {
+            c->w_theta.ensure(vb);
+            dv = c->w_theta.as<double2>();
+        }
+        run_propagator(c, W, dx, precision, dv);
+        if (v_host) LOAF_CUDA(cudaMemcpyAsync(v_out, dv, vb, cudaMemcpyDeviceToHost, c->stream));
+        int timeout = 0;
+        if (precision != LOAF_PREC_FP64)
+            LOAF_CUDA(cudaMemcpyAsync(&timeout, c->w_flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        LOAF_CUDA(cudaStreamSynchronize(c->stream));
+        prof_collect(c);
+        LOAF_REQUIRE(!timeout, LOAF_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on a pipeline barrier");
+    });
 }
 
 loaf_status walkers_pair_exchange(loaf_ctx* c, int W, const void* phi, int precision,

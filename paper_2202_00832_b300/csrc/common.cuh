@@ -229,12 +229,17 @@ struct MixedOps {
     // per-pair trial parts, weights 2 (1 or 2) and their trial sum
     DevBuf pt_J, row_cJ, e0_J, pw_J;
     double EJ0 = 0.0;
+    // propagator operator: L^T tiles [mt][kb] (rows pq, per-row scale)
+    bool prop_ready = false;
+    int prop_nkb = 0, prop_nmt = 0;
+    DevBuf Lt_hi, Lt_lo, Lt_inv;
     void release() {
         for (DevBuf* b : {&L_hi, &L_lo, &L_inv, &J0, &U_hi, &U_lo, &V_hi, &V_lo, &row_c, &pt,
                           &pair_pt0, &pair_npt, &pair_w, &e0, &s_pt, &s_pt0, &s_npt, &s_pw,
-                          &Lb_hi, &Lb_lo, &Ub_hi, &Ub_lo, &Vb_hi, &Vb_lo, &pt_J, &row_cJ, &e0_J, &pw_J})
+                          &Lb_hi, &Lb_lo, &Ub_hi, &Ub_lo, &Vb_hi, &Vb_lo, &pt_J, &row_cJ, &e0_J, &pw_J,
+                          &Lt_hi, &Lt_lo, &Lt_inv})
             b->release();
-        coul_ready = lo_ready = false;
+        coul_ready = lo_ready = prop_ready = false;
         screen_built = -1;
         h_tiles.clear(); h_pt0.clear(); h_npt.clear(); h_order.clear(); h_pw.clear(); h_e0.clear();
         n_pt = n_pairs = 0;
@@ -296,7 +301,7 @@ struct loaf_ctx {
     int ws_W = 0;
     loaf::DevBuf w_phi, w_theta, w_z, w_lu, w_perm, w_logdet, w_status, w_out, w_part,
         w_part2, w_dhi, w_dlo, w_dscale, w_host_stage, w_cpart, w_lopart, w_red, w_flag, w_oz_at, w_oz_bs,
-        w_oz_bt, w_oz_S, w_oz_int;
+        w_oz_bt, w_oz_S, w_oz_int, w_prop_x, w_prop_part;
     int trial_version = 0;  // bumped whenever a trial (canonical or localized) is loaded
 
     // per-stage CUDA-event timers (loaf_profile); stage kernels are bracketed
@@ -358,6 +363,14 @@ void run_energy_fp64_lo(loaf_ctx* c, int W, const double2* theta, double2* e_out
 void run_coulomb_fp64(loaf_ctx* c, int W, const double2* theta, double2* e_part);
 // E_J from the compressed pair factors (closed shell): 2 sum_ij (Ubar^T Theta_i).(Vbar Theta_j)
 void run_coulomb_lo_fp64(loaf_ctx* c, int W, const double2* theta, double2* ej_out, double2* scratch);
+// part[row][col] = sum_k A[row][k] B[col][k] over 16-bit hi/lo tiles (A tiles
+// [mt][kb], B tiles [rb][kb], 128 x 64 each, three products, 128-term chains
+// folded in double-float), FP64 out, rows x (n_wt * 128) with leading dim ldp
+void tc_split_gemm(loaf_ctx* c, const uint16_t* a_hi, const uint16_t* a_lo, int rows, int n_mt,
+                   const uint16_t* b_hi, const uint16_t* b_lo, int nrb, int n_wt, int nkb, bool bf16,
+                   double* part, int ldp, int* err);
+// V_w = sum_g x_wg L_g for W walkers (x: W x X, V: W x M x M, device)
+void run_propagator(loaf_ctx* c, int W, const double2* x, int precision, double2* V);
 // <L_g>_w of the batch whose Delta tiles the tensor-core Theta stage wrote
 void run_force_bias_mixed(loaf_ctx* c, int W, int precision, double2* e_scratch, double2* j_out);
 void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2* theta,

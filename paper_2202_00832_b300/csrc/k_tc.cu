@@ -23,6 +23,7 @@
 // All mbarrier waits are bounded (tc_ptx.cuh); a timeout raises an error flag
 // the host turns into LOAF_ERR_TIMEOUT.
 #include "common.cuh"
+#include "split16.cuh"
 #include "tc_ptx.cuh"
 
 
@@ -37,51 +38,6 @@ constexpr int kBM = 128;             // MMA rows per CTA
 constexpr int kBNW = 128;            // walkers per LO tile
 constexpr int kBN = 2 * kBNW;        // LO MMA columns: (walker, re/im) interleaved
 
-// ---------------------------------------------------------------------------
-// 16-bit split helpers
-// ---------------------------------------------------------------------------
-template <bool BF16> struct Half16;
-template <> struct Half16<false> {
-    __device__ static uint16_t from(double v, double& back) {
-        const __half h = __double2half(v);
-        back = (double)__half2float(h);
-        return __half_as_ushort(h);
-    }
-};
-template <> struct Half16<true> {
-    __device__ static uint16_t from(double v, double& back) {
-        const __nv_bfloat16 h = __double2bfloat16(v);
-        back = (double)__bfloat162float(h);
-        return __bfloat16_as_ushort(h);
-    }
-};
-
-template <bool BF16>
-__device__ inline void split16(double v, uint16_t& hi, uint16_t& lo) {
-    double b;
-    hi = Half16<BF16>::from(v, b);
-    double b2;
-    lo = Half16<BF16>::from(v - b, b2);
-}
-
-// power-of-two scale putting the largest |value| in [2^13, 2^14)
-__device__ inline double pow2_scale(double maxabs) {
-    if (!(maxabs > 0.0) || !isfinite(maxabs)) return 1.0;
-    int e;
-    frexp(maxabs, &e);  // maxabs = f * 2^e, f in [0.5, 1)
-    return ldexp(1.0, 14 - e);
-}
-
-__device__ inline double block_max(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    double m = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, red[k]);
-    return m;
-}
 
 __device__ inline double block_sum(double v, double* red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1235,6 +1191,31 @@ void coulomb_mixed(loaf_ctx* c, MixedOps& mx, int W, bool bf16, const float* inv
 }
 
 }  // namespace
+
+void tc_split_gemm(loaf_ctx* c, const uint16_t* a_hi, const uint16_t* a_lo, int rows, int n_mt,
+                   const uint16_t* b_hi, const uint16_t* b_lo, int nrb, int n_wt, int nkb, bool bf16,
+                   double* part, int ldp, int* err) {
+    CoulParams P;
+    P.a_hi = a_hi;
+    P.a_lo = a_lo;
+    P.b_hi = b_hi;
+    P.b_lo = b_lo;
+    P.nkb = nkb;
+    P.nrb = nrb;
+    P.rows = rows;
+    P.n_mt = n_mt;
+    P.n_wt = n_wt;
+    P.nk = nkb;  // one orbital block: K = nkb tiles of 64
+    P.n_split = 1;
+    P.ldp = ldp;
+    P.idesc = tc::idesc_f16(kBM, kCBN, bf16);
+    P.err = err;
+    P.part = part;
+    LOAF_CUDA(cudaFuncSetAttribute(coulomb_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kCoulSmem));
+    coulomb_tc_kernel<<<std::min(n_mt * n_wt, c->persistent_grid()), kCThreads, kCoulSmem, c->stream>>>(P);
+    LOAF_LAUNCH_CHECK();
+}
 
 void run_force_bias_mixed(loaf_ctx* c, int W, int precision, double2* e_scratch, double2* j_out) {
     const bool bf16 = precision == LOAF_PREC_BF16X3;

@@ -42,6 +42,7 @@ SIGNATURES = [
     ("walkers_energy_multi", _I, [_P, _I, _P, _P, _I, _I, _P, _P, _P, _I, _P]),
     ("walkers_theta", _I, [_P, _I, _P, _P, _P, _P]),
     ("walkers_force_bias", _I, [_P, _I, _P, _I, _P, _P, _P]),
+    ("walkers_propagator", _I, [_P, _I, _P, _I, _P]),
     ("walkers_pair_exchange", _I, [_P, _I, _P, _I, _P]),
     ("loaf_num_pairs", _I, [_P]),
     ("lo_get_localized_trial", _I, [_P, _I, _P]),
@@ -240,6 +241,16 @@ class Context:
             return e_out, logdet_out, walker_status
         self._check(code, "walkers_energy")
         return e_out, logdet_out, walker_status
+
+    def walkers_propagator(self, x, precision="fp64", out=None):
+        """V_w = sum_g x_wg L_g for fields x (W x X complex128): W x M x M complex128."""
+        _check_dtype(x, "c16")
+        W = int(x.shape[0])
+        if out is None:
+            out = np.zeros((W, self.M, self.M), dtype=np.complex128)
+        self._check(self._lib.walkers_propagator(self._h, W, _ptr(x), PRECISIONS.get(precision, precision),
+                                                 _ptr(out)), "walkers_propagator")
+        return out
 
     def walkers_force_bias(self, phi, precision="fp64", out=None, logdet_out=None,
                            walker_status=None):
