@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--batch-report", action="store_true",
                     help="walker-batching curve at pentacene scale instead of the throughput line: "
                          "walker energies/s against the walkers per call (64 .. 4096)")
+    ap.add_argument("--propagator-report", action="store_true",
+                    help="propagator operator V_w = sum_g x_wg L_g at pentacene scale instead of the "
+                         "throughput line: time per 1024 walkers (split precision and FP64) and its roofline")
     ap.add_argument("--screen-cutoffs", default="1e-6,1e-3,1e-2,1e-1",
                     help="per-pair cutoffs (Ha) of the screen report")
     return ap.parse_args()
@@ -665,9 +668,58 @@ def batch_report(args):
           flush=True)
 
 
+def propagator_report(args):
+    """V_w = sum_g x_wg L_g for W = 1024 pentacene-scale walkers (M 440, X 1800),
+    fields and outputs resident in HBM (3.2 GB of V): time per batch in the split
+    precision, algorithmic work 4 W X M^2 flops (complex field times real L),
+    and the FP64 (cuBLAS) path on 64 walkers for comparison."""
+    import torch
+    from paper_2202_00832_b300.lo_afqmc import Context
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    mol = synth.PENTACENE_440.molecule()
+    ctx = Context(0, stream=stream.cuda_stream)
+    ctx.load_molecule(mol)
+    rng = np.random.default_rng(4)
+    out = {"workload": synth.PENTACENE_440.name, "M": mol.M, "X": mol.X}
+
+    def timed(W, precision, reps):
+        x = torch.from_numpy(rng.standard_normal((W, mol.X)) * 0.1
+                             + 1j * rng.standard_normal((W, mol.X)) * 0.05).cuda()
+        v = torch.zeros((W, mol.M, mol.M), dtype=torch.complex128, device="cuda")
+        ctx.walkers_propagator(x, precision=precision, out=v)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            ctx.walkers_propagator(x, precision=precision, out=v)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        del x, v
+        return ms
+
+    W = 1024
+    ms = timed(W, args.precision, 5)
+    flops = 4.0 * W * mol.X * mol.M ** 2
+    peaks = load_peaks()
+    out[args.precision] = {"walkers": W, "ms_per_batch": ms, "walkers_per_s": W / (ms / 1e3),
+                           "algorithmic_tflops": flops / (ms / 1e3) / 1e12,
+                           "frac_of_bf16_sustained": flops / (ms / 1e3) / 1e12 / peaks["bf16_tflops_sustained"]}
+    ms64 = timed(64, "fp64", 2)
+    out["fp64"] = {"walkers": 64, "ms_per_batch": ms64, "walkers_per_s": 64 / (ms64 / 1e3),
+                   "tflops": 4.0 * 64 * mol.X * mol.M ** 2 / (ms64 / 1e3) / 1e12}
+    print(json.dumps({"propagator_report": out}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.propagator_report:
+        if rank == 0:
+            propagator_report(args)
+        return
     if args.batch_report:
         if rank == 0:
             batch_report(args)

@@ -365,10 +365,13 @@ void run_coulomb_fp64(loaf_ctx* c, int W, const double2* theta, double2* e_part)
 void run_coulomb_lo_fp64(loaf_ctx* c, int W, const double2* theta, double2* ej_out, double2* scratch);
 // part[row][col] = sum_k A[row][k] B[col][k] over 16-bit hi/lo tiles (A tiles
 // [mt][kb], B tiles [rb][kb], 128 x 64 each, three products, 128-term chains
-// folded in double-float), FP64 out, rows x (n_wt * 128) with leading dim ldp
+// folded in double-float), FP64 out, rows x (n_wt * 128) with leading dim ldp;
+// with out set, columns (2w, 2w + 1) go to out[w][row] as one complex value,
+// scaled by inv_row[row] * inv_col[col] (w < out_W, leading dim out_ld)
 void tc_split_gemm(loaf_ctx* c, const uint16_t* a_hi, const uint16_t* a_lo, int rows, int n_mt,
                    const uint16_t* b_hi, const uint16_t* b_lo, int nrb, int n_wt, int nkb, bool bf16,
-                   double* part, int ldp, int* err);
+                   double* part, int ldp, int* err, double2* out, const float* inv_row,
+                   const float* inv_col, long out_ld, int out_W);
 // V_w = sum_g x_wg L_g for W walkers (x: W x X, V: W x M x M, device)
 void run_propagator(loaf_ctx* c, int W, const double2* x, int precision, double2* V);
 // <L_g>_w of the batch whose Delta tiles the tensor-core Theta stage wrote

@@ -8,8 +8,8 @@
 //   part[pq][2w + ri] = sum_g L^T[pq][g] x_ri[w][g],
 // with L^T (rows pq, per-row power-of-two scale) tiled once per molecule and
 // the fields (rows (w, re/im), per-row scale) tiled per call, both as 16-bit
-// hi + lo pre-swizzled 128 x 64 tiles; the result is unscaled and transposed
-// to the walker-major output.  FP64: two cuBLAS DGEMMs (re and im of x).
+// hi + lo pre-swizzled 128 x 64 tiles; the contraction's epilogue unscales and
+// writes the walker-major output.  FP64: two cuBLAS DGEMMs (re and im of x).
 #include "common.cuh"
 #include "split16.cuh"
 
@@ -76,33 +76,6 @@ __global__ void x_tiles_kernel(int X, int nkb, const double2* __restrict__ x, ui
         const size_t o = ((size_t)rb * nkb + (g >> 6)) * kTileElems + sw128_elem(r, g & 63);
         hi[o] = h;
         lo[o] = l;
-    }
-}
-
-// V[w][pq] = (part[pq][2w], part[pq][2w + 1]) unscaled, through 32 x 32 shared tiles
-__global__ void prop_out_kernel(long MM, int W, int ldp, const double* __restrict__ part,
-                                const float* __restrict__ inv_l, const float* __restrict__ inv_x,
-                                double2* __restrict__ V) {
-    __shared__ double2 t[32][33];
-    const long p0 = (long)blockIdx.x * 32;
-    const int w0 = blockIdx.y * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-    for (int k = ty; k < 32; k += 8) {
-        const long pq = p0 + k;
-        const int w = w0 + tx;
-        double2 v = make_double2(0.0, 0.0);
-        if (pq < MM && w < W) {
-            const double2 a = *reinterpret_cast<const double2*>(part + (size_t)pq * ldp + 2 * w);
-            const double il = (double)inv_l[pq];
-            v = make_double2(a.x * il * (double)inv_x[2 * w], a.y * il * (double)inv_x[2 * w + 1]);
-        }
-        t[k][tx] = v;
-    }
-    __syncthreads();
-    for (int k = ty; k < 32; k += 8) {
-        const int w = w0 + k;
-        const long pq = p0 + tx;
-        if (pq < MM && w < W) V[(size_t)w * MM + pq] = t[tx][k];
     }
 }
 
@@ -186,20 +159,17 @@ void run_propagator(loaf_ctx* c, int W, const double2* x, int precision, double2
     uint16_t* x_hi = c->w_prop_x.as<uint16_t>();
     uint16_t* x_lo = x_hi + xb / 2;
     float* inv_x = reinterpret_cast<float*>(c->w_prop_x.as<uint8_t>() + 2 * xb);
-    c->w_prop_part.ensure((size_t)MM * ldp * sizeof(double));
     c->w_flag.ensure(16);
     LOAF_CUDA(cudaMemsetAsync(c->w_flag.ptr, 0, sizeof(int), c->stream));
-    StageScope sc(c, "propagator_tc", 3);
+    StageScope sc(c, "propagator_tc", 2);
     if (bf16)
         x_tiles_kernel<true><<<2 * W, 256, 0, c->stream>>>(c->X, nkb, x, x_hi, x_lo, inv_x);
     else
         x_tiles_kernel<false><<<2 * W, 256, 0, c->stream>>>(c->X, nkb, x, x_hi, x_lo, inv_x);
     LOAF_LAUNCH_CHECK();
+    // the contraction's epilogue writes V[w][pq] directly (scaled), no FP64 table
     tc_split_gemm(c, mx.Lt_hi.as<uint16_t>(), mx.Lt_lo.as<uint16_t>(), (int)MM, mx.prop_nmt, x_hi, x_lo, nrb,
-                  n_wt, nkb, bf16, c->w_prop_part.as<double>(), ldp, c->w_flag.as<int>());
-    prop_out_kernel<<<dim3((unsigned)ceil_div(MM, 32), ceil_div(W, 32)), 256, 0, c->stream>>>(
-        MM, W, ldp, c->w_prop_part.as<double>(), mx.Lt_inv.as<float>(), inv_x, V);
-    LOAF_LAUNCH_CHECK();
+                  n_wt, nkb, bf16, nullptr, ldp, c->w_flag.as<int>(), V, mx.Lt_inv.as<float>(), inv_x, MM, W);
 }
 
 }  // namespace loaf

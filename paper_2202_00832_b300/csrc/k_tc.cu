@@ -294,6 +294,16 @@ struct CoulParams {
     const uint16_t* b_hi;  // Delta tiles [c][rb][kb]
     const uint16_t* b_lo;
     double* part;      // [split][rows][ldp] FP64 partial sums
+    // optional direct output instead of part (one split): out[w][row] =
+    // (col 2w, col 2w + 1) * inv_row[row] * (inv_col[2w], inv_col[2w + 1])
+    double2* out;
+    const float* inv_row;
+    const float* inv_col;
+    long out_ld;
+    int out_W;
+    // unit order: row tiles fastest (the column operand is the large one, as
+    // for the Coulomb energy) or column tiles fastest (the row operand is)
+    int wt_fast;
     int rows;          // X + 1
     int n_mt, n_wt, n_split, nk, ldp;
     int nkb, nrb;      // basis blocks per orbital, Delta row blocks
@@ -342,7 +352,8 @@ coulomb_tc_kernel(CoulParams P) {
         int s = 0;
         uint32_t ph = 0, filled = 0, last_par = 0;
         for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
-            const int mt = u % P.n_mt, wt = (u / P.n_mt) % P.n_wt, sp = u / (P.n_mt * P.n_wt);
+            const int mt = P.wt_fast ? (u / P.n_wt) % P.n_mt : u % P.n_mt,
+                      wt = P.wt_fast ? u % P.n_wt : (u / P.n_mt) % P.n_wt, sp = u / (P.n_mt * P.n_wt);
             const int k0 = (int)((long)sp * P.nk / P.n_split), k1 = (int)((long)(sp + 1) * P.nk / P.n_split);
             for (int kc = k0; kc < k1; ++kc) {
                 if (!tc::mbar_wait(&sh.empty[s], ph ^ 1, abort)) break;
@@ -415,7 +426,8 @@ coulomb_tc_kernel(CoulParams P) {
         uint32_t gcount = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < n_units && ok && !*abort; u += gridDim.x) {
-            const int mt = u % P.n_mt, wt = (u / P.n_mt) % P.n_wt, sp = u / (P.n_mt * P.n_wt);
+            const int mt = P.wt_fast ? (u / P.n_wt) % P.n_mt : u % P.n_mt,
+                      wt = P.wt_fast ? u % P.n_wt : (u / P.n_mt) % P.n_wt, sp = u / (P.n_mt * P.n_wt);
             const int k0 = (int)((long)sp * P.nk / P.n_split), k1 = (int)((long)(sp + 1) * P.nk / P.n_split);
             // hi in registers, lo in shared memory ([column][epilogue thread])
             float hi[32];
@@ -442,7 +454,23 @@ coulomb_tc_kernel(CoulParams P) {
             }
             if (!ok) break;
             const int g = mt * kBM + q * 32 + lane;
-            if (g < P.rows) {
+            if (P.out) {
+                // columns (2w, 2w + 1) are walker w's real and imaginary part: a warp
+                // writes 32 consecutive rows of one walker (512 contiguous bytes)
+                if (g < P.rows) {
+                    const double ir = (double)P.inv_row[g];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int w = wt * (kCBN / 2) + h * 16 + k;
+                        if (w < P.out_W)
+                            P.out[(size_t)w * P.out_ld + g] = make_double2(
+                                ((double)hi[2 * k] + (double)lo[(2 * k) * kCEpiWarps * 32]) * ir *
+                                    (double)P.inv_col[2 * w],
+                                ((double)hi[2 * k + 1] + (double)lo[(2 * k + 1) * kCEpiWarps * 32]) * ir *
+                                    (double)P.inv_col[2 * w + 1]);
+                    }
+                }
+            } else if (g < P.rows) {
                 double2* dst = reinterpret_cast<double2*>(
                     P.part + ((size_t)sp * P.rows + g) * P.ldp + (size_t)wt * kCBN + h * 32);
 #pragma unroll
@@ -1152,6 +1180,8 @@ void coulomb_mixed(loaf_ctx* c, MixedOps& mx, int W, bool bf16, const float* inv
     const DeltaGeom dg = delta_geom(c->M, c->ntot, W);
     // ---- Coulomb + one-body on the tensor cores ----
     CoulParams P;
+    P.out = nullptr;
+    P.wt_fast = 0;
     P.a_hi = mx.Lb_hi.as<uint16_t>();
     P.a_lo = mx.Lb_lo.as<uint16_t>();
     P.b_hi = c->w_dhi.as<uint16_t>();
@@ -1194,8 +1224,15 @@ void coulomb_mixed(loaf_ctx* c, MixedOps& mx, int W, bool bf16, const float* inv
 
 void tc_split_gemm(loaf_ctx* c, const uint16_t* a_hi, const uint16_t* a_lo, int rows, int n_mt,
                    const uint16_t* b_hi, const uint16_t* b_lo, int nrb, int n_wt, int nkb, bool bf16,
-                   double* part, int ldp, int* err) {
+                   double* part, int ldp, int* err, double2* out, const float* inv_row,
+                   const float* inv_col, long out_ld, int out_W) {
     CoulParams P;
+    P.out = out;
+    P.inv_row = inv_row;
+    P.inv_col = inv_col;
+    P.out_ld = out_ld;
+    P.out_W = out_W;
+    P.wt_fast = 1;  // the row operand (rows x K) is the large one
     P.a_hi = a_hi;
     P.a_lo = a_lo;
     P.b_hi = b_hi;
