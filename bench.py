@@ -80,6 +80,27 @@ def dist_env():
     return rank, world, local
 
 
+def walker_first(rank: int, W: int) -> int:
+    """Each rank evaluates its own W walkers: walker seeds rank*W .. rank*W + W - 1
+    (weak scaling: no data-path collective)."""
+    return rank * W
+
+
+def max_over_ranks(x: float, dist) -> float:
+    """The slowest rank's time (the job is done when every rank is)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, W: int, steps: int, seconds: float) -> float:
+    """Walker energies per second of all ranks together."""
+    return world * W * steps / seconds
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
 
@@ -228,7 +249,7 @@ def run_ours(args, rank, world, local):
     W = args.walkers or wl.W
     t_gen = time.perf_counter()
     mol = wl.molecule()
-    walk = wl.walkers(mol, W=W, first=rank * W, processes=min(16, os.cpu_count() or 1))
+    walk = wl.walkers(mol, W=W, first=walker_first(rank, W), processes=min(16, os.cpu_count() or 1))
     t_gen = time.perf_counter() - t_gen
 
     stream = torch.cuda.current_stream()
@@ -272,11 +293,8 @@ def run_ours(args, rank, world, local):
     ms = ev0.elapsed_time(ev1)
     prof = ctx.profile_read()
     ctx.profile(False)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * W * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, dist)
+    value = whole_job_rate(world, W, args.steps, ms / 1e3)
 
     # ---- end to end through the public API with pinned host buffers ----
     phi_h = torch.from_numpy(walk).pin_memory()
@@ -292,13 +310,9 @@ def run_ours(args, rank, world, local):
         ctx.walkers_energy(phi_h, mode="lo", precision=args.precision, e_out=e_h,
                            logdet_out=ld_h, walker_status=st_h)
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([t_e2e], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = world * W * args.steps / t_e2e
-    h2d = W * mol.M * mol.n_alpha * 16
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist)
+    e2e = whole_job_rate(world, W, args.steps, t_e2e)
+    h2d = W * mol.M * (mol.n_alpha if mol.closed_shell else mol.n_alpha + mol.n_beta) * 16
     d2h = W * (16 + 16 + 4)
 
     if rank != 0:
