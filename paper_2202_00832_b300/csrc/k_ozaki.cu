@@ -526,6 +526,18 @@ __device__ inline float4 cdf_sub_mul(float4 v, float4 f, float4 u) {
     im = df_fma(df_neg(fi), ur, im);
     return make_float4(re.hi, re.lo, im.hi, im.lo);
 }
+// 1 / z (complex): |z|^2 in double-float, its reciprocal from the FP32 one and
+// one double-float Newton correction r0 (2 - |z|^2 r0), then conj(z) / |z|^2
+__device__ inline float4 cdf_recip(float4 z) {
+    const dfl re{z.x, z.y}, im{z.z, z.w};
+    const dfl n2 = df_fma(im, im, df_mul(re, re));
+    const dfl r0{__frcp_rn(n2.hi), 0.f};
+    const dfl e = df_fma(df_neg(n2), r0, dfl{1.f, 0.f});  // 1 - |z|^2 r0
+    const dfl r = df_fma(r0, e, r0);
+    const dfl a = df_mul(re, r), b = df_mul(df_neg(im), r);
+    return make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
 // x y (complex)
 __device__ inline float4 cdf_mul(float4 x, float4 y) {
     const dfl xr{x.x, x.y}, xi{x.z, x.w}, yr{y.x, y.y}, yi{y.z, y.w};
@@ -552,7 +564,7 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
     extern __shared__ __align__(16) unsigned char sm[];
     float4* A = reinterpret_cast<float4*>(sm);    // N x N complex double-float
     float4* colk = A + N * N;                     // N
-    double2* pivv = reinterpret_cast<double2*>(colk + N);  // N pivots (FP64)
+    float4* pivv = colk + N;                      // N pivots (double-float)
     int* piv = reinterpret_cast<int*>(pivv + N);  // N
     int* gk = piv + N;                            // N
     __shared__ double red_v[32];
@@ -601,12 +613,13 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
                 piv[k] = bi;
                 if (bi != k) s_swaps += 1;
                 s_akk = A[k * N + k];
-                const double2 pv = cdf_to(A[bi * N + k]);
-                if (!(mag2(pv) > s_tol)) {
+                const float4 pv = A[bi * N + k];
+                // |pivot|^2 of the leading parts against the tolerance (FP64: no underflow)
+                if (!((double)pv.x * pv.x + (double)pv.z * pv.z > s_tol)) {
                     s_flag = 1;
                 } else {
                     pivv[k] = pv;
-                    s_inv = cdf_from(cdiv(make_double2(1.0, 0.0), pv));
+                    s_inv = cdf_recip(pv);
                 }
             }
         }
@@ -672,7 +685,7 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
     double2 lp = make_double2(0.0, 0.0);
     if (flag == 0)
         for (int k = tid; k < N; k += blockDim.x) {
-            const double2 d = pivv[k];
+            const double2 d = cdf_to(pivv[k]);
             lp.x += log(hypot(d.x, d.y));
             lp.y += atan2(d.y, d.x);
         }
