@@ -456,7 +456,6 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
 // ---------------------------------------------------------------------------
 // Gauss-Jordan inversion with partial pivoting (FP64), log-det, S^-1 slices
 // ---------------------------------------------------------------------------
-__device__ inline double mag2(double2 a) { return a.x * a.x + a.y * a.y; }
 
 // ---- double-float arithmetic (a value is hi + lo, two FP32 numbers) ----
 // B300 issues FP32 about 64x faster than FP64; an error-free product (FMA) and
@@ -509,10 +508,6 @@ __device__ inline dfl df_fma(dfl a, dfl b, dfl c) {
     return r;
 }
 __device__ inline dfl df_mul(dfl a, dfl b) { return df_fma(a, b, dfl{0.f, 0.f}); }
-__device__ inline float4 cdf_from(double2 z) {
-    const dfl r = df_from(z.x), i = df_from(z.y);
-    return make_float4(r.hi, r.lo, i.hi, i.lo);
-}
 __device__ inline double2 cdf_to(float4 z) {
     return make_double2(df_to(dfl{z.x, z.y}), df_to(dfl{z.z, z.w}));
 }
