@@ -189,29 +189,44 @@ __global__ void slice_trial_kernel(int M, int N, int p_pad, const double* __rest
 // with one exponent per walker and spin.  64 basis rows per step through
 // shared memory (transpose for Bs).
 constexpr int kSliceRows = 64;
+// Largest |phi| of each walker's spin block: kMaxSplit CTAs per walker over
+// row ranges, integer maxima of the absolute bit patterns (key[w] starts at 0).
+constexpr int kMaxSplit = 4;
 __global__ void __launch_bounds__(256)
-slice_phi_kernel(int M, int N, int ntot, int col0, int p_pad, int kpad, int W,
-                 const double2* __restrict__ phi, uint16_t* __restrict__ At, uint16_t* __restrict__ Bs,
-                 int* __restrict__ wexp) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    signed char* dg = reinterpret_cast<signed char*>(sm);  // [kNS][kSliceRows][2N]
+phi_max_kernel(int M, int N, int ntot, int col0, const double2* __restrict__ phi,
+               unsigned long long* __restrict__ key) {
     __shared__ unsigned long long red[32];
-    const int w = blockIdx.x;
+    const int w = blockIdx.x / kMaxSplit, part = blockIdx.x % kMaxSplit;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const double2* pw = phi + (size_t)w * M * ntot + col0;
-    // walker exponent: warps over rows p, lanes over orbitals j (integer max of |v|)
+    const int p0 = (int)((long)part * M / kMaxSplit), p1 = (int)((long)(part + 1) * M / kMaxSplit);
     unsigned long long m = 0;
-    for (int p = warp; p < M; p += nwarp)
+    for (int p = p0 + warp; p < p1; p += nwarp)
         for (int j = lane; j < N; j += 32) {
             const double2 v = pw[(size_t)p * ntot + j];
             m = max(m, max(abs_key(v.x), abs_key(v.y)));
         }
-    const int E = slice_exponent(__longlong_as_double((long long)block_max_key(m, red)));
-    if (threadIdx.x == 0) wexp[w] = E;
+    m = block_max_key(m, red);
+    if (threadIdx.x == 0) atomicMax(key + w, m);
+}
+
+// One (walker, 64-row chunk) per CTA: the chunk's digits in both layouts, with
+// the walker's exponent from its maximum key.
+__global__ void __launch_bounds__(256)
+slice_phi_kernel(int M, int N, int ntot, int col0, int p_pad, int kpad, int W,
+                 const double2* __restrict__ phi, const unsigned long long* __restrict__ key,
+                 uint16_t* __restrict__ At, uint16_t* __restrict__ Bs, int* __restrict__ wexp) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    signed char* dg = reinterpret_cast<signed char*>(sm);  // [kNS][kSliceRows][2N]
+    const int w = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const double2* pw = phi + (size_t)w * M * ntot + col0;
+    const int E = slice_exponent(__longlong_as_double((long long)key[w]));
+    if (blockIdx.y == 0 && threadIdx.x == 0) wexp[w] = E;
     const int twoN = 2 * N;
-    for (int p0 = 0; p0 < p_pad; p0 += kSliceRows) {
+    {
+        const int p0 = blockIdx.y * kSliceRows;
         const int np = min(kSliceRows, p_pad - p0);
-        __syncthreads();
         // digits of (re, im) of phi[p][j]: K = 2j, 2j + 1 stored together
         for (int pp = warp; pp < np; pp += nwarp) {
             const int p = p0 + pp;
@@ -764,18 +779,19 @@ __global__ void delta_scale_kernel(int W, int nspin, const int* __restrict__ wex
 
 void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
     const int M = c->M;
-    const int p_pad = (M + 7) / 8 * 8;
+    const int p_pad = (M + 15) / 16 * 16;  // 32-byte rows: whole L2 sectors
     const int r_pad = p_pad;
     const bool bf16 = precision == LOAF_PREC_BF16X3;
     int nmax = 0;
     for (int s = 0; s < c->nspin; ++s) nmax = std::max(nmax, c->sp[s].N);
-    const int kpad_max = (2 * nmax + 7) / 8 * 8;
+    const int kpad_max = (2 * nmax + 15) / 16 * 16;
     const size_t at_spin = (size_t)kNS * W * M * kpad_max;        // 16-bit entries per spin
     const size_t bt_spin = (size_t)kNS * W * 2 * nmax * kpad_max;
     c->w_oz_at.ensure(at_spin * c->nspin * 2);
     c->w_oz_bt.ensure(bt_spin * c->nspin * 2);
     c->w_oz_bs.ensure((size_t)kNS * 2 * nmax * W * p_pad * 2);
     c->w_oz_S.ensure((size_t)W * nmax * nmax * sizeof(double2));
+    c->w_oz_key.ensure((size_t)W * sizeof(unsigned long long));
     c->w_oz_int.ensure((size_t)(2 * W * (2 + nmax) + W) * sizeof(int) + 256);
     const DeltaGeom dg = delta_geom(M, c->ntot, W);
     c->w_dhi.ensure_zeroed(dg.plane * 2, c->stream);
@@ -801,7 +817,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
     // phase 1, per spin: slices of phi, S = Phi_T^T phi, Z = S^-1 (FP64) and its slices
     for (int s = 0; s < c->nspin; ++s) {
         SpinData& sd = c->sp[s];
-        const int N = sd.N, twoN = 2 * N, kpad = (twoN + 7) / 8 * 8;
+        const int N = sd.N, twoN = 2 * N, kpad = (twoN + 15) / 16 * 16;
         if (sd.oz_trial_version != c->trial_version) {
             sd.oz_trialT.ensure((size_t)kNS * N * p_pad * 2);
             sd.oz_rowexp.ensure((size_t)N * sizeof(int));
@@ -816,13 +832,17 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
             sd.oz_trial_version = c->trial_version;
         }
         {
-            StageScope sc(c, "theta_slice", 1);
+            StageScope sc(c, "theta_slice", 2);
             const size_t smem = (size_t)kNS * twoN * kSliceRows;
             LOAF_CUDA(cudaFuncSetAttribute(slice_phi_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            slice_phi_kernel<<<W, 256, smem, c->stream>>>(M, N, c->ntot, sd.col0, p_pad, kpad, W, phi,
-                                                         At + at_spin * s, c->w_oz_bs.as<uint16_t>(),
-                                                         wexp(s));
+            unsigned long long* key = c->w_oz_key.as<unsigned long long>();
+            LOAF_CUDA(cudaMemsetAsync(key, 0, (size_t)W * sizeof(unsigned long long), c->stream));
+            phi_max_kernel<<<W * kMaxSplit, 256, 0, c->stream>>>(M, N, c->ntot, sd.col0, phi, key);
+            LOAF_LAUNCH_CHECK();
+            slice_phi_kernel<<<dim3(W, ceil_div(p_pad, kSliceRows)), 256, smem, c->stream>>>(
+                M, N, c->ntot, sd.col0, p_pad, kpad, W, phi, key, At + at_spin * s, c->w_oz_bs.as<uint16_t>(),
+                wexp(s));
             LOAF_LAUNCH_CHECK();
         }
         {
@@ -870,7 +890,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
     // phase 3, per spin: Theta = phi Z on the tensor cores -> Delta planes
     for (int s = 0; s < c->nspin; ++s) {
         SpinData& sd = c->sp[s];
-        const int N = sd.N, twoN = 2 * N, kpad = (twoN + 7) / 8 * 8;
+        const int N = sd.N, twoN = 2 * N, kpad = (twoN + 15) / 16 * 16;
         StageScope sc(c, "theta_tc", 1);
         CUtensorMap mA, mB;
         map_slices(&mA, At + at_spin * s, twoN, kpad, M, W, kOBM);
