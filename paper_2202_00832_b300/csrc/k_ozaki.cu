@@ -105,13 +105,27 @@ __device__ inline unsigned long long abs_key(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
 }
 
-// six balanced base-128 digits of x = v 2^-E (|x| <= 1/4), most significant first
+// low 7 bits of x as a signed value in [-64, 63]
+__device__ inline int sext7(int x) { return (int)((unsigned)x << 25) >> 25; }
+
+// six balanced base-128 digits of x = v 2^-E (|x| <= 1/4), most significant first.
+// X = hi 2^21 + lo with lo in [0, 2^21); the three low digits come from lo in
+// 32-bit arithmetic and leave a carry of 0 or 1 for hi -- the same digits as
+// taking all six from X one after another (digit = low 7 bits read as signed,
+// then X <- (X + 64) >> 7).
 __device__ inline void digits_of(long long X, int (&d)[kNS]) {
+    int lo = (int)(X & 0x1fffff);
+    int hi = (int)(X >> 21);
 #pragma unroll
-    for (int s = kNS - 1; s >= 0; --s) {
-        const int r = (int)((X + 64) & 127) - 64;
-        d[s] = r;
-        X = (X - r) >> 7;
+    for (int s = kNS - 1; s >= kNS / 2; --s) {
+        d[s] = sext7(lo);
+        lo = (lo + 64) >> 7;
+    }
+    hi += lo;
+#pragma unroll
+    for (int s = kNS / 2 - 1; s >= 0; --s) {
+        d[s] = sext7(hi);
+        hi = (hi + 64) >> 7;
     }
 }
 __device__ inline void digits6(double v, int E, int (&d)[kNS]) { digits_of(round_scaled(v, 42 - E), d); }
@@ -131,6 +145,19 @@ __device__ inline long long round_scaled_f(float v, int s) {
 }
 
 __device__ inline uint16_t h16(int d) { return __half_as_ushort(__int2half_rn(d)); }
+
+// FP16 bit patterns of two digits a, b in [-64, 63], a in the low half: 1536 + d
+// is exact in FP16 (spacing 1 on [1024, 2048), pattern 0x6600 + d), and one
+// packed FP16 subtraction of 1536 leaves d exactly -- no conversion instructions.
+__device__ inline uint32_t h16x2(int a, int b) {
+    const uint32_t u = (uint32_t)(a + 0x6600) | ((uint32_t)(b + 0x6600) << 16);
+    __half2 v;
+    memcpy(&v, &u, 4);
+    v = __hsub2(v, __half2half2(__ushort_as_half((unsigned short)0x6600)));
+    uint32_t r;
+    memcpy(&r, &v, 4);
+    return r;
+}
 
 __device__ inline unsigned long long block_max_key(unsigned long long v, unsigned long long* red) {
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -211,7 +238,9 @@ phi_max_kernel(int M, int N, int ntot, int col0, const double2* __restrict__ phi
 }
 
 // One (walker, 64-row chunk) per CTA: the chunk's digits in both layouts, with
-// the walker's exponent from its maximum key.
+// the walker's exponent from its maximum key.  The (row, orbital) elements of
+// the chunk are spread over all threads (row-major, so the reads of phi and the
+// writes of At stay coalesced).
 __global__ void __launch_bounds__(256)
 slice_phi_kernel(int M, int N, int ntot, int col0, int p_pad, int kpad, int W,
                  const double2* __restrict__ phi, const unsigned long long* __restrict__ key,
@@ -224,42 +253,49 @@ slice_phi_kernel(int M, int N, int ntot, int col0, int p_pad, int kpad, int W,
     const int E = slice_exponent(__longlong_as_double((long long)key[w]));
     if (blockIdx.y == 0 && threadIdx.x == 0) wexp[w] = E;
     const int twoN = 2 * N;
-    {
-        const int p0 = blockIdx.y * kSliceRows;
-        const int np = min(kSliceRows, p_pad - p0);
-        // digits of (re, im) of phi[p][j]: K = 2j, 2j + 1 stored together
-        for (int pp = warp; pp < np; pp += nwarp) {
-            const int p = p0 + pp;
-            for (int j = lane; j < N; j += 32) {
-                double2 z = make_double2(0.0, 0.0);
-                if (p < M) z = pw[(size_t)p * ntot + j];
-                int dr[kNS], di[kNS];
-                digits6(z.x, E, dr);
-                digits6(z.y, E, di);
+    const int p0 = blockIdx.y * kSliceRows;
+    const int np = min(kSliceRows, p_pad - p0);
+    const size_t at_s = (size_t)W * M * kpad;  // At slice stride
+    // digits of (re, im) of phi[p][j]: K = 2j, 2j + 1 stored together
+    const int dpp = blockDim.x / N, dj = blockDim.x - dpp * N;
+    int pp = threadIdx.x / N, j = threadIdx.x - pp * N;
+    while (pp < np) {
+        const int p = p0 + pp;
+        double2 z = make_double2(0.0, 0.0);
+        if (p < M) z = pw[(size_t)p * ntot + j];
+        int dr[kNS], di[kNS];
+        digits6(z.x, E, dr);
+        digits6(z.y, E, di);
+        uint32_t* at = reinterpret_cast<uint32_t*>(At + ((size_t)w * M + p) * kpad + 2 * j);
+        signed char* d2 = dg + (size_t)pp * twoN + 2 * j;
 #pragma unroll
-                for (int s = 0; s < kNS; ++s) {
-                    char2 c2;
-                    c2.x = (signed char)dr[s];
-                    c2.y = (signed char)di[s];
-                    *reinterpret_cast<char2*>(dg + ((size_t)s * kSliceRows + pp) * twoN + 2 * j) = c2;
-                    if (p < M)
-                        *reinterpret_cast<uint32_t*>(At + (((size_t)s * W + w) * M + p) * kpad + 2 * j) =
-                            (uint32_t)h16(dr[s]) | ((uint32_t)h16(di[s]) << 16);
-                }
-            }
+        for (int s = 0; s < kNS; ++s) {
+            char2 c2;
+            c2.x = (signed char)dr[s];
+            c2.y = (signed char)di[s];
+            *reinterpret_cast<char2*>(d2 + (size_t)s * kSliceRows * twoN) = c2;
+            if (p < M) at[s * at_s / 2] = h16x2(dr[s], di[s]);
         }
-        __syncthreads();
-        // transpose: one warp per (slice, ri, j) row of Bs, two basis rows per lane
-        for (int row = warp; row < kNS * twoN; row += nwarp) {
-            const int s = row / twoN, col = row - s * twoN;  // col = ri * N + j
-            const int ri = col >= N ? 1 : 0, j = col - ri * N;
-            const signed char* src = dg + (size_t)s * kSliceRows * twoN + 2 * j + ri;
-            uint16_t* dst = Bs + ((size_t)s * 2 * N * W + (size_t)(2 * w + ri) * N + j) * p_pad + p0;
-            const int pp = 2 * lane;
-            if (pp < np) {
-                const uint32_t lo = h16(src[(size_t)pp * twoN]);
-                const uint32_t hi = pp + 1 < np ? h16(src[(size_t)(pp + 1) * twoN]) : 0u;
-                *reinterpret_cast<uint32_t*>(dst + pp) = lo | (hi << 16);
+        pp += dpp;
+        j += dj;
+        if (j >= N) {
+            j -= N;
+            ++pp;
+        }
+    }
+    __syncthreads();
+    // transpose: one warp per (slice, ri, j) row of Bs, two basis rows per lane
+    const int q = 2 * lane;
+    if (q < np) {
+        for (int s = 0; s < kNS; ++s) {
+            const signed char* src_s = dg + ((size_t)s * kSliceRows + q) * twoN;
+            uint16_t* dst_s = Bs + ((size_t)s * 2 * N * W + (size_t)2 * w * N) * p_pad + p0 + q;
+            for (int col = warp; col < twoN; col += nwarp) {  // col = ri N + j
+                const int ri = col >= N ? 1 : 0, jj = col - ri * N;
+                const signed char* src = src_s + 2 * jj + ri;
+                const int a = src[0];
+                const int b = q + 1 < np ? src[twoN] : 0;
+                *reinterpret_cast<uint32_t*>(dst_s + (size_t)col * p_pad) = h16x2(a, b);
             }
         }
     }
@@ -740,21 +776,28 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
         gmax[w] = g;
     }
     const int twoN = 2 * N;
-    for (int e = tid; e < twoN * twoN; e += blockDim.x) {
-        const int cc = e / twoN, K = e % twoN;  // cc = 2k + ro, K = 2j + ri
-        const int k = cc >> 1, ro = cc & 1, j = K >> 1, ri = K & 1;
-        long long X = 0;
+    // row cc = 2k + ro of Bt, columns K = 2j (ri = 0) and 2j + 1 (ri = 1): the
+    // real form [[Zr, -Zi], [Zi, Zr]] of the complex column k
+    for (int e = tid; e < twoN * N; e += blockDim.x) {
+        const int cc = e / N, j = e - cc * N;
+        const int k = cc >> 1, ro = cc & 1;
+        long long X0 = 0, X1 = 0;
         if (flag == 0) {
             // digits of hi + lo from the two parts (one more unit of rounding)
             const float4 z = A[j * N + k];
-            float h = z.x, l = z.y;                                  // Zr
-            if (ri != ro) { h = ri ? -z.z : z.z; l = ri ? -z.w : z.w; }  // -Zi or Zi
-            X = round_scaled_f(h, 42 - gk[k]) + round_scaled_f(l, 42 - gk[k]);
+            const int sh = 42 - gk[k];
+            const long long xr = round_scaled_f(z.x, sh) + round_scaled_f(z.y, sh);
+            const long long xi = round_scaled_f(z.z, sh) + round_scaled_f(z.w, sh);
+            X0 = ro ? xi : xr;   // ri = 0: Zr (ro = 0) or Zi (ro = 1)
+            X1 = ro ? xr : -xi;  // ri = 1: -Zi (ro = 0) or Zr (ro = 1)
         }
-        int d[kNS];
-        digits_of(X, d);
+        int d0[kNS], d1[kNS];
+        digits_of(X0, d0);
+        digits_of(X1, d1);
+        uint32_t* bt = reinterpret_cast<uint32_t*>(Bt + (((size_t)w * twoN + cc) * kpad + 2 * j));
+        const size_t bt_s = (size_t)W * twoN * kpad / 2;
 #pragma unroll
-        for (int s = 0; s < kNS; ++s) Bt[(((size_t)s * W + w) * twoN + cc) * kpad + K] = h16(d[s]);
+        for (int s = 0; s < kNS; ++s) bt[s * bt_s] = h16x2(d0[s], d1[s]);
     }
 }
 
