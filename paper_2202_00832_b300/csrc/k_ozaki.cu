@@ -14,10 +14,12 @@
 //   value = 2^(e_row + e_col - 49) * sum_D acc_D * 2^(7 (7 - D)).
 // Omitting s + t >= 8 leaves an error near 2^-49 of the operands' scale.
 // Only the O(N^3) part -- Gauss-Jordan inversion of S with partial pivoting
-// and the log-determinant -- stays FP64 (one CTA per walker and spin).
+// and the log-determinant -- runs on the CUDA cores, in double-float (pairs of
+// FP32 numbers) with the log-determinant summed in FP64 (one CTA per walker
+// and spin).
 //
-// Stages per spin: slice phi (two layouts) -> S GEMM (A = Phi_T^T slices,
-// B = phi slices) -> Gauss-Jordan (Z = S^-1, log det, Z slices) -> Delta scale
+// Stages per spin: slice phi (two layouts) -> S GEMM (A = phi slices,
+// B = Phi_T^T slices: S^T) -> Gauss-Jordan (Z = S^-1, log det, Z slices) -> Delta scale
 // -> Theta GEMM (A = phi slices, B = Z slices) whose epilogue writes
 // Delta = Theta - Phi_T as the 16-bit hi/lo planes the Coulomb and LO kernels read.
 #include "common.cuh"
@@ -311,7 +313,7 @@ struct OzParams {
     int mode;  // 0: overlap S, 1: Theta -> Delta planes
     int M, N, ntot, col0, r_pad, W, rows_valid, cols_valid;
     int nrb, nkb;         // mode 1: Delta tile geometry
-    const int* row_exp;   // mode 0: exponent of each Phi_T^T row
+    const int* row_exp;   // mode 0: exponent of each Phi_T^T row i (column i of the GEMM)
     const int* wexp;      // exponent of each walker's phi block
     const int* col_exp;   // mode 1: [W][N] exponent of each column of S^-1
     double* S_out;        // mode 0: [W][N][N] complex as (re, im) doubles
@@ -463,6 +465,14 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
             if (!tc::mbar_wait(&sh.tmem_full, tph, abort)) break;
             tc::tc_fence_after();
             const int row = rt * kOBM + q * 32 + lane;
+            // mode 0: row = (2w + ri) N + j of the walker slices
+            int w0 = 0, ri0 = 0, j0 = 0;
+            if (P.mode == 0) {
+                w0 = row / (2 * P.N);
+                const int rem = row - w0 * 2 * P.N;
+                ri0 = rem >= P.N ? 1 : 0;
+                j0 = rem - ri0 * P.N;
+            }
 #pragma unroll 1
             for (int c0 = h * 8; c0 < kOBN; c0 += 32) {
                 float v[kND][8];
@@ -479,11 +489,9 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
                     const int col = ct * kOBN + c0 + c;
                     if (row >= P.rows_valid || col >= P.cols_valid) continue;
                     if (P.mode == 0) {
-                        // S_w[i][j], column col = (2w + ri) N + j
-                        const int w = col / (2 * P.N), rem = col % (2 * P.N);
-                        const int ri = rem / P.N, j = rem % P.N;
-                        P.S_out[(((size_t)w * P.N + row) * P.N + j) * 2 + ri] =
-                            (double)z * pow2d(P.row_exp[row] + P.wexp[w] - 49);
+                        // S_w[i][j] (part ri) for column col = i of Phi_T
+                        P.S_out[(((size_t)w0 * P.N + col) * P.N + j0) * 2 + ri0] =
+                            (double)z * pow2d(P.row_exp[col] + P.wexp[w0] - 49);
                     } else {
                         const int w = b, k = col >> 1;
                         store_delta(P, w, row, col, z, P.wexp[w] + P.col_exp[(size_t)w * P.N + k] - 49,
@@ -505,7 +513,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
 }
 
 // ---------------------------------------------------------------------------
-// Gauss-Jordan inversion with partial pivoting (FP64), log-det, S^-1 slices
+// Gauss-Jordan inversion with partial pivoting (double-float), log-det, S^-1 slices
 // ---------------------------------------------------------------------------
 
 // ---- double-float arithmetic (a value is hi + lo, two FP32 numbers) ----
@@ -857,7 +865,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
     LOAF_CUDA(cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kOSmem));
 
-    // phase 1, per spin: slices of phi, S = Phi_T^T phi, Z = S^-1 (FP64) and its slices
+    // phase 1, per spin: slices of phi, S = Phi_T^T phi, Z = S^-1 (double-float) and its slices
     for (int s = 0; s < c->nspin; ++s) {
         SpinData& sd = c->sp[s];
         const int N = sd.N, twoN = 2 * N, kpad = (twoN + 15) / 16 * 16;
@@ -889,14 +897,16 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
             LOAF_LAUNCH_CHECK();
         }
         {
-            // S = Phi_T^T phi: rows i, columns (2w + ri) N + j, K = basis
+            // S = Phi_T^T phi computed as its transpose: rows (2w + ri) N + j of the
+            // walker slices (128-row tiles, all used), columns i of Phi_T (80-wide
+            // tiles, little padding for N <= 80), K = basis
             StageScope sc(c, "overlap_tc", 1);
             CUtensorMap mA, mB;
-            map_slices(&mA, sd.oz_trialT.ptr, p_pad, p_pad, N, 1, kOBM);
-            map_slices(&mB, c->w_oz_bs.ptr, p_pad, p_pad, (uint64_t)twoN * W, 1, kOBN);
+            map_slices(&mA, c->w_oz_bs.ptr, p_pad, p_pad, (uint64_t)twoN * W, 1, kOBM);
+            map_slices(&mB, sd.oz_trialT.ptr, p_pad, p_pad, N, 1, kOBN);
             OzParams P{};
-            P.n_rt = ceil_div(N, kOBM);
-            P.n_ct = ceil_div((long)twoN * W, kOBN);
+            P.n_rt = ceil_div((long)twoN * W, kOBM);
+            P.n_ct = ceil_div(N, kOBN);
             P.n_b = 1;
             P.nk = ceil_div(p_pad, kOBK);
             P.a_batched = 0;
@@ -905,8 +915,8 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
             P.mode = 0;
             P.M = M; P.N = N; P.ntot = c->ntot; P.col0 = sd.col0; P.r_pad = r_pad; P.W = W;
             P.nrb = dg.nrb; P.nkb = dg.nkb;
-            P.rows_valid = N;
-            P.cols_valid = twoN * W;
+            P.rows_valid = twoN * W;
+            P.cols_valid = N;
             P.row_exp = sd.oz_rowexp.as<int>();
             P.wexp = wexp(s);
             P.S_out = c->w_oz_S.as<double>();
