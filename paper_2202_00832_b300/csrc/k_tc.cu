@@ -488,6 +488,212 @@ coulomb_tc_kernel(CoulParams P) {
     if (threadIdx.x == 0 && sh.abort) atomicExch(P.err, 1);
 }
 
+// ---- Coulomb on CTA pairs ----
+// The same contraction with a cta_group::2 MMA of M = 256 (row tiles 2m and
+// 2m + 1: one per CTA) and N = 128: each CTA stages its own 128 operand rows
+// and half of the 128 Delta rows (the first or second 8 KB of a Delta tile,
+// itself a 64-row swizzled image), 48 KB per k-chunk instead of 64 KB, so
+// three k-chunks are in flight per SM.  TMEM per CTA and the epilogue are
+// those of coulomb_tc_kernel.  The row tiles are padded to an even count
+// (a zero tile).
+constexpr int kCPStages = 3;
+constexpr uint32_t kCPStageBytes = 2 * kTileBytes + kTileBytes;  // A hi, A lo, B hi half, B lo half
+
+struct CoulPairShared {
+    uint64_t full[kCPStages];       // even CTA: own bytes + the odd CTA's forward
+    uint64_t empty[kCPStages];      // both: the pair MMA's commit (multicast)
+    uint64_t acc_full[kCBufs];      // both: the pair MMA's commit (multicast)
+    uint64_t acc_empty[kCBufs];     // even CTA: 16 local + 16 remote epilogue warps
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+// units (row-tile pair, walker tile, split), row-tile pairs fastest; P.n_mt is
+// the padded (even) row-tile count
+__global__ void __launch_bounds__(kCThreads, 1)
+coulomb_tc_pair_kernel(CoulParams P) {
+    extern __shared__ uint8_t dyn_smem[];
+    __shared__ CoulPairShared sh;
+    uint8_t* base = align1024(dyn_smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = tc::cluster_ctarank();
+    const bool even = rank == 0;
+    const int cid = blockIdx.x >> 1, n_cl = gridDim.x >> 1;
+    const int n_mp = P.n_mt >> 1;
+    const int n_units = n_mp * P.n_wt * P.n_split;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kCPStages; ++s) {
+            tc::mbar_init(&sh.full[s], even ? 2 : 1);
+            tc::mbar_init(&sh.empty[s], 1);
+        }
+        for (int b = 0; b < kCBufs; ++b) {
+            tc::mbar_init(&sh.acc_full[b], 1);
+            tc::mbar_init(&sh.acc_empty[b], 2 * kCEpiWarps);
+        }
+        tc::mbar_init(&sh.drain, 1);
+        sh.abort = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc_pair(&sh.tmem_base, kCBufs * kCBN);
+        tc::tmem_relinquish_pair();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::cluster_sync();  // both CTAs' barriers initialised before any remote arrive
+    tc::tc_fence_after();
+    const uint32_t tmem = sh.tmem_base;
+    volatile int* abort = &sh.abort;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- bulk-copy producer (both CTAs) ----------------
+        int s = 0;
+        uint32_t ph = 0, filled = 0, last_par = 0;
+        for (int u = cid; u < n_units && !*abort; u += n_cl) {
+            const int mp = u % n_mp, wt = (u / n_mp) % P.n_wt, sp = u / (n_mp * P.n_wt);
+            const int mt = 2 * mp + (int)rank;
+            const int k0 = (int)((long)sp * P.nk / P.n_split), k1 = (int)((long)(sp + 1) * P.nk / P.n_split);
+            for (int kc = k0; kc < k1; ++kc) {
+                if (!tc::mbar_wait_cluster(&sh.empty[s], ph ^ 1, abort)) break;
+                uint8_t* st = base + s * kCPStageBytes;
+                tc::mbar_arrive_expect_tx(&sh.full[s], kCPStageBytes);
+                const int cc = kc / P.nkb, kb = kc - cc * P.nkb;
+                const size_t ao = ((size_t)mt * P.nk + kc) * kTileElems;
+                const size_t bo = (((size_t)cc * P.nrb + wt) * P.nkb + kb) * kTileElems + rank * (kTileElems / 2);
+                tc::bulk_load(st, P.a_hi + ao, kTileBytes, &sh.full[s]);
+                tc::bulk_load(st + kTileBytes, P.a_lo + ao, kTileBytes, &sh.full[s]);
+                tc::bulk_load(st + 2 * kTileBytes, P.b_hi + bo, kTileBytes / 2, &sh.full[s]);
+                tc::bulk_load(st + 2 * kTileBytes + kTileBytes / 2, P.b_lo + bo, kTileBytes / 2, &sh.full[s]);
+                filled |= 1u << s;
+                last_par = (last_par & ~(1u << s)) | (ph << s);
+                if (++s == kCPStages) { s = 0; ph ^= 1; }
+            }
+        }
+        if (*abort) {
+            // every copy issued has landed once its phase completes; bounded waits
+            for (int q = 0; q < kCPStages; ++q)
+                if (filled & (1u << q)) {
+                    volatile int never = 0;
+                    if (even)
+                        tc::mbar_wait_cluster(&sh.full[q], (last_par >> q) & 1, &never);
+                    else
+                        tc::mbar_wait(&sh.full[q], (last_par >> q) & 1, &never);
+                }
+        }
+    } else if (warp == 1 && lane == 0 && !even) {
+        // ---------------- forwarder (odd CTA) ----------------
+        const uint32_t peer_full0 = tc::mapa_shared(&sh.full[0], 0);
+        int s = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        for (int u = cid; u < n_units && ok && !*abort; u += n_cl) {
+            const int sp = u / (n_mp * P.n_wt);
+            const int k0 = (int)((long)sp * P.nk / P.n_split), k1 = (int)((long)(sp + 1) * P.nk / P.n_split);
+            for (int kc = k0; kc < k1; ++kc) {
+                if (!tc::mbar_wait(&sh.full[s], ph, abort)) { ok = false; break; }
+                tc::mbar_arrive_remote(peer_full0 + s * (uint32_t)sizeof(uint64_t));
+                if (++s == kCPStages) { s = 0; ph ^= 1; }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- pair MMA issuer (even CTA) ----------------
+        int s = 0;
+        uint32_t ph = 0, gcount = 0;
+        bool ok = true;
+        for (int u = cid; u < n_units && ok && !*abort; u += n_cl) {
+            const int sp = u / (n_mp * P.n_wt);
+            const int k0 = (int)((long)sp * P.nk / P.n_split), k1 = (int)((long)(sp + 1) * P.nk / P.n_split);
+            for (int g0 = k0; g0 < k1 && ok; g0 += kCGroup, ++gcount) {
+                const uint32_t b = gcount % kCBufs, use = gcount / kCBufs;
+                if (!tc::mbar_wait_cluster(&sh.acc_empty[b], (use & 1) ^ 1, abort)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint32_t d = tmem + b * kCBN;
+                const int g1 = min(g0 + kCGroup, k1);
+                for (int kc = g0; kc < g1; ++kc) {
+                    if (!tc::mbar_wait_cluster(&sh.full[s], ph, abort)) { ok = false; break; }
+                    tc::tc_fence_after();
+                    const uint32_t st = tc::smem_u32(base + s * kCPStageBytes);
+#pragma unroll
+                    for (int kk = 0; kk < kTileK / 16; ++kk) {
+                        const uint32_t off = kk * 32;
+                        const uint64_t ahi = tc::smem_desc(st + off, 128);
+                        const uint64_t alo = tc::smem_desc(st + kTileBytes + off, 128);
+                        const uint64_t bhi = tc::smem_desc(st + 2 * kTileBytes + off, 128);
+                        const uint64_t blo = tc::smem_desc(st + 2 * kTileBytes + kTileBytes / 2 + off, 128);
+                        const uint32_t acc = (kc > g0 || kk > 0) ? 1u : 0u;
+                        tc::mma_f16_pair(d, ahi, bhi, P.idesc, acc);
+                        tc::mma_f16_pair(d, ahi, blo, P.idesc, 1u);
+                        tc::mma_f16_pair(d, alo, bhi, P.idesc, 1u);
+                    }
+                    tc::mma_commit_pair(&sh.empty[s], 0x3);
+                    if (++s == kCPStages) { s = 0; ph ^= 1; }
+                }
+                if (!ok) break;
+                tc::mma_commit_pair(&sh.acc_full[b], 0x3);
+            }
+        }
+        tc::mma_commit_pair(&sh.drain, 0x1);
+        volatile int never = 0;
+        tc::mbar_wait(&sh.drain, 0, &never);
+    } else if (warp >= 2) {
+        // ---------------- epilogue (both CTAs): as in coulomb_tc_kernel ----------------
+        const int q = warp & 3;          // TMEM lane quarter
+        const int h = (warp - 2) >> 2;   // column block: 32 columns per warp
+        const uint32_t even_acc_empty0 = tc::mapa_shared(&sh.acc_empty[0], 0);
+        uint32_t gcount = 0;
+        bool ok = true;
+        for (int u = cid; u < n_units && ok && !*abort; u += n_cl) {
+            const int mp = u % n_mp, wt = (u / n_mp) % P.n_wt, sp = u / (n_mp * P.n_wt);
+            const int mt = 2 * mp + (int)rank;
+            const int k0 = (int)((long)sp * P.nk / P.n_split), k1 = (int)((long)(sp + 1) * P.nk / P.n_split);
+            // hi in registers, lo in shared memory ([column][epilogue thread])
+            float hi[32];
+            float* lo = reinterpret_cast<float*>(base + kCPStages * kCPStageBytes) + (threadIdx.x - 64);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) { hi[k] = 0.f; lo[k * kCEpiWarps * 32] = 0.f; }
+            for (int g0 = k0; g0 < k1; g0 += kCGroup, ++gcount) {
+                const uint32_t b = gcount % kCBufs, use = gcount / kCBufs;
+                if (!tc::mbar_wait_cluster(&sh.acc_full[b], use & 1, abort)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + b * kCBN + h * 32;
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+                    float v[16];
+                    tc::tmem_ld16(taddr + part * 16, v);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        two_sum_acc(hi[part * 16 + k], lo[(part * 16 + k) * kCEpiWarps * 32], v[k]);
+                }
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive_remote(even_acc_empty0 + b * (uint32_t)sizeof(uint64_t));
+            }
+            if (!ok) break;
+            const int g = mt * kBM + q * 32 + lane;
+            if (g < P.rows) {
+                double2* dst = reinterpret_cast<double2*>(
+                    P.part + ((size_t)sp * P.rows + g) * P.ldp + (size_t)wt * kCBN + h * 32);
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    dst[k] = make_double2((double)hi[2 * k] + (double)lo[(2 * k) * kCEpiWarps * 32],
+                                          (double)hi[2 * k + 1] +
+                                              (double)lo[(2 * k + 1) * kCEpiWarps * 32]);
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    // the even CTA's MMAs read the odd CTA's shared memory and write its TMEM,
+    // and both CTAs arrive on each other's barriers: neither leaves early
+    tc::cluster_sync();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc_pair(tmem, kCBufs * kCBN);
+    if (threadIdx.x == 0 && sh.abort) atomicExch(P.err, 1);
+}
+
 struct LoParams {
     const uint16_t* u_hi;  // operand tiles [tile][kb]
     const uint16_t* u_lo;
@@ -885,9 +1091,15 @@ void ensure_coulomb_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     // operand tiles [mt][c][kb]; the row-major staging planes are then dropped
     mx.nkb = ceil_div(c->M, kTileK);
     mx.n_mt = ceil_div(rows, kTileRows);
-    const size_t tiles_bytes = (size_t)mx.n_mt * c->ntot * mx.nkb * kTileBytes;
+    // an even number of row tiles for the CTA-pair kernel: the last one may be zeros
+    const size_t tile_set = (size_t)c->ntot * mx.nkb * kTileBytes;  // one row tile
+    const size_t tiles_bytes = (size_t)((mx.n_mt + 1) & ~1) * tile_set;
     mx.Lb_hi.ensure(tiles_bytes);
     mx.Lb_lo.ensure(tiles_bytes);
+    if (mx.n_mt & 1) {
+        LOAF_CUDA(cudaMemsetAsync(mx.Lb_hi.as<uint8_t>() + mx.n_mt * tile_set, 0, tile_set, c->stream));
+        LOAF_CUDA(cudaMemsetAsync(mx.Lb_lo.as<uint8_t>() + mx.n_mt * tile_set, 0, tile_set, c->stream));
+    }
     const dim3 tg(mx.n_mt * c->ntot, mx.nkb);
     coul_tiles_kernel<<<tg, 256, 0, c->stream>>>(mx.L_hi.as<uint16_t>(), rows, c->ntot, mx.r_pad, mx.nkb,
                                                 mx.Lb_hi.as<uint16_t>());
@@ -1144,6 +1356,55 @@ void ensure_screened_tiles(loaf_ctx* c, MixedOps& mx) {
 constexpr size_t kCoulSmem =
     kCStages * 4 * kTileBytes + 32 * kCEpiWarps * 32 * sizeof(float) + 1024;
 constexpr size_t kLoSmem = kLSlots * kLSlotBytes + 1024;
+constexpr size_t kCoulPairSmem =
+    kCPStages * kCPStageBytes + 32 * kCEpiWarps * 32 * sizeof(float) + 1024;
+
+// CTA pairs of a cluster kernel that fit on the GPU at once
+int max_pair_clusters(const void* kernel, int threads, size_t smem, int sm_count) {
+    LOAF_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * (sm_count / 2));
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    LOAF_CUDA(cudaOccupancyMaxActiveClusters(&n, kernel, &cfg));
+    return n;
+}
+
+int coul_max_clusters(loaf_ctx* c) {
+    static int cached[64] = {0};
+    int dev = 0;
+    LOAF_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && cached[dev] > 0) return cached[dev];
+    const int n = max_pair_clusters((const void*)coulomb_tc_pair_kernel, kCThreads, kCoulPairSmem, c->sm_count);
+    LOAF_REQUIRE(n > 0, LOAF_ERR_CUDA, "the Coulomb kernel's CTA pair does not fit on an SM pair");
+    if (dev < 64) cached[dev] = n;
+    return n;
+}
+
+// k-splits of a contraction with `tiles` output tiles dealt round-robin to
+// `slots` persistent workers: the fewest that fill the last round to >= 90 %
+// (the split fixes the FP32 chain boundaries, so slots must not depend on an
+// SM budget)
+int wave_splits(int tiles, int max_split, int slots) {
+    int best = 1;
+    double best_eff = 0.0;
+    for (int sp = 1; sp <= max_split; ++sp) {
+        const long units = (long)tiles * sp;
+        const long rounds = (units + slots - 1) / slots;
+        const double eff = (double)units / (double)(rounds * slots);
+        if (units >= slots && eff >= 0.9) return sp;
+        if (eff > best_eff + 1e-12) { best_eff = eff; best = sp; }
+    }
+    return best;
+}
 
 // CTA pairs of the LO kernel that fit on the GPU at once (the persistent grid):
 // clusters sit inside a GPC, so this can be below half the SM count
@@ -1189,23 +1450,34 @@ void coulomb_mixed(loaf_ctx* c, MixedOps& mx, int W, bool bf16, const float* inv
     P.nkb = dg.nkb;
     P.nrb = dg.nrb;
     P.rows = c->X + 1;
-    P.n_mt = mx.n_mt;
+    P.n_mt = (mx.n_mt + 1) & ~1;  // row-tile pairs (the padding tile is zeros)
     P.n_wt = ceil_div(2L * W, kCBN);
     P.nk = c->ntot * dg.nkb;
-    const int tiles = P.n_mt * P.n_wt;
+    const int tiles = (P.n_mt / 2) * P.n_wt;
     // the split fixes the chain boundaries of the FP32 accumulation, so it depends
     // on the device only (not on an SM budget): results do not depend on scheduling
-    P.n_split = std::max(1, std::min(ceil_div(P.nk, kCGroup), (3 * c->sm_count + tiles - 1) / tiles));
+    P.n_split = wave_splits(tiles, std::min(16, ceil_div(P.nk, kCGroup)), c->sm_count / 2);
     P.ldp = P.n_wt * kCBN;
-    P.idesc = tc::idesc_f16(kBM, kCBN, bf16);
+    P.idesc = tc::idesc_f16(2 * kBM, kCBN, bf16);  // pair MMA: M = 256, N = 128
     P.err = err;
     c->w_cpart.ensure((size_t)P.n_split * P.rows * P.ldp * sizeof(double));
     P.part = c->w_cpart.as<double>();
     const int units = tiles * P.n_split;
-    LOAF_CUDA(cudaFuncSetAttribute(coulomb_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kCoulSmem));
+    const int n_cl = std::max(1, std::min({units, coul_max_clusters(c), c->persistent_grid() / 2}));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * n_cl);
+    cfg.blockDim = dim3(kCThreads);
+    cfg.dynamicSmemBytes = kCoulPairSmem;
+    cfg.stream = c->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     StageScope csc(c, "coulomb_tc", 1);
-    coulomb_tc_kernel<<<std::min(units, c->persistent_grid()), kCThreads, kCoulSmem, c->stream>>>(P);
+    LOAF_CUDA(cudaLaunchKernelEx(&cfg, coulomb_tc_pair_kernel, P));
     LOAF_LAUNCH_CHECK();
     csc.end();
     StageScope rsc(c, "coulomb_reduce", 2);
