@@ -179,7 +179,7 @@ struct SpinData {
     double E1_0 = 0.0;     // sum_ir hbar_ir Phi_ri
     PairTable pairs;
     DevBuf oz_trialT, oz_rowexp;   // digit slices of Phi_T^T (tensor-core Theta)
-    DevBuf oz_trial_cm;            // Phi_T column-major (N x M, FP64): coalesced epilogue reads
+    DevBuf oz_trial_cm;            // Phi_T column-major (N x M, int64 units of 2^-56): coalesced epilogue reads
     int oz_trial_version = -1;
     void release() {
         oz_trialT.release(); oz_rowexp.release(); oz_trial_version = -1;

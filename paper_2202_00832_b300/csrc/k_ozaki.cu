@@ -185,14 +185,29 @@ __device__ inline double block_max_d(double v, double* red) {
 // slicing
 // ---------------------------------------------------------------------------
 
-// Phi_T (M x N, row-major) -> column-major copy (N x M)
+// Phi_T (M x N, row-major) -> column-major copy (N x M) in fixed point,
+// round(t 2^56) (the trial's columns are orthonormal: |t| <= 1)
+constexpr int kTrialFx = 56;
 __global__ void transpose_trial_kernel(int M, int N, const double* __restrict__ trial,
-                                       double* __restrict__ out) {
+                                       long long* __restrict__ out) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < M * N) {
         const int k = e / M, r = e - k * M;
-        out[e] = trial[(size_t)r * N + k];
+        out[e] = __double2ll_rn(ldexp(trial[(size_t)r * N + k], kTrialFx));
     }
+}
+
+// round(T 2^-sh) of a fixed-point integer, ties upward
+__device__ inline long long fx_round(long long T, int sh) {
+    if (sh >= 63) return 0;
+    if (sh <= 0) return T << (-sh);
+    return (T + (1LL << (sh - 1))) >> sh;
+}
+
+// a 64-bit integer as a float from two 32-bit conversions (within two units in
+// the last place; avoids the 64-bit conversion, which runs on the FP64 pipe)
+__device__ inline float ll_to_float(long long D) {
+    return fmaf(__int2float_rn((int)(D >> 32)), 4294967296.f, __uint2float_rn((unsigned)(D & 0xffffffffLL)));
 }
 
 // Phi_T^T rows i (per-row exponent), K = basis p: A_S[s][i][p_pad]
@@ -317,7 +332,7 @@ struct OzParams {
     const int* wexp;      // exponent of each walker's phi block
     const int* col_exp;   // mode 1: [W][N] exponent of each column of S^-1
     double* S_out;        // mode 0: [W][N][N] complex as (re, im) doubles
-    const double* trial_cm;  // mode 1: Phi_T column-major, N x M
+    const long long* trial_fx;  // mode 1: Phi_T column-major, N x M, in units of 2^-56
     const int* texp;      // mode 1: per-walker Delta scale exponent (scale = 2^texp)
     uint16_t* dhi;
     uint16_t* dlo;
@@ -342,11 +357,12 @@ __device__ inline uint8_t* align1k(uint8_t* p) {
 // 16-bit hi/lo pair of the Delta planes; cc = 2k + ro of this spin
 // Delta = z 2^e - Phi_T (the trial is real: only the real part ro = 0 moves),
 // formed exactly in integer units of 2^e, then scaled by the walker's 2^te
-__device__ inline void store_delta(const OzParams& P, int w, int r, int cc, long long z, int e, int te) {
+__device__ inline void store_delta(const OzParams& P, int w, int r, int cc, long long z, int e, int te,
+                                   long long tfx) {
     const int k = cc >> 1, ro = cc & 1;
     long long D = z;
-    if (!ro) D -= round_scaled(P.trial_cm[(size_t)k * P.M + r], -e);
-    const float f = __ll2float_rn(D) * pow2f(e + te);
+    if (!ro) D -= fx_round(tfx, kTrialFx + e);
+    const float f = ll_to_float(D) * pow2f(e + te);
     uint16_t h, l;
     if (P.bf16) {
         const __nv_bfloat16 a = __float2bfloat16(f);
@@ -473,8 +489,24 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
                 ri0 = rem >= P.N ? 1 : 0;
                 j0 = rem - ri0 * P.N;
             }
+            const int wexp_b = P.mode == 1 ? P.wexp[b] : 0, texp_b = P.mode == 1 ? P.texp[b] : 0;
 #pragma unroll 1
             for (int c0 = h * 8; c0 < kOBN; c0 += 32) {
+                // mode 1: the chunk's four orbitals k: exponents and trial values,
+                // fetched before the accumulators are read
+                int ek[4] = {0, 0, 0, 0};
+                long long tk[4] = {0, 0, 0, 0};
+                if (P.mode == 1) {
+                    const int kb0 = (ct * kOBN + c0) >> 1;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const int k = kb0 + m;
+                        if (k < P.N) {
+                            ek[m] = P.col_exp[(size_t)b * P.N + k];
+                            if (row < P.M) tk[m] = P.trial_fx[(size_t)k * P.M + row];
+                        }
+                    }
+                }
                 float v[kND][8];
 #pragma unroll
                 for (int D = 0; D < kND; ++D)
@@ -493,9 +525,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
                         P.S_out[(((size_t)w0 * P.N + col) * P.N + j0) * 2 + ri0] =
                             (double)z * pow2d(P.row_exp[col] + P.wexp[w0] - 49);
                     } else {
-                        const int w = b, k = col >> 1;
-                        store_delta(P, w, row, col, z, P.wexp[w] + P.col_exp[(size_t)w * P.N + k] - 49,
-                                    P.texp[w]);
+                        store_delta(P, b, row, col, z, wexp_b + ek[c >> 1] - 49, texp_b, tk[c >> 1]);
                     }
                 }
             }
@@ -876,9 +906,9 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
                                                        sd.oz_trialT.as<uint16_t>(),
                                                        sd.oz_rowexp.as<int>());
             LOAF_LAUNCH_CHECK();
-            sd.oz_trial_cm.ensure((size_t)N * M * sizeof(double));
+            sd.oz_trial_cm.ensure((size_t)N * M * sizeof(long long));
             transpose_trial_kernel<<<ceil_div(M * N, 256), 256, 0, c->stream>>>(
-                M, N, sd.d_trial.as<double>(), sd.oz_trial_cm.as<double>());
+                M, N, sd.d_trial.as<double>(), sd.oz_trial_cm.as<long long>());
             LOAF_LAUNCH_CHECK();
             sd.oz_trial_version = c->trial_version;
         }
@@ -963,7 +993,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
         P.cols_valid = twoN;
         P.wexp = wexp(s);
         P.col_exp = cexp(s);
-        P.trial_cm = sd.oz_trial_cm.as<double>();
+        P.trial_fx = sd.oz_trial_cm.as<long long>();
         P.texp = texp;
         P.dhi = c->w_dhi.as<uint16_t>();
         P.dlo = c->w_dlo.as<uint16_t>();
