@@ -641,6 +641,7 @@ constexpr int kGJMaxCols = (LOAF_MAX_NOCC + 15) / 16;  // columns per thread of 
 // the B operand of the Theta GEMM (Theta = [phi_re phi_im] B, column pairs).
 constexpr int kGJThreads = 256;  // update grid: 16 row groups x 16 column groups
 
+template <int MAXC>  // column slots per thread: ceil(N / 16)
 __global__ void __launch_bounds__(kGJThreads)
 gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint16_t* __restrict__ Bt,
                     int* __restrict__ col_exp, int* __restrict__ gmax, double2* __restrict__ ld_part,
@@ -725,25 +726,25 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
         // phase C: other rows, A[i][j] -= A[i][k] (old) * A[k][j] (new); A[i][k]
         // starts from 0.  Each thread's columns are loaded, updated and stored
         // as a group so that their independent error-free chains interleave.
-        float4 u[kGJMaxCols];
+        float4 u[MAXC];
 #pragma unroll
-        for (int q = 0; q < kGJMaxCols; ++q) {
+        for (int q = 0; q < MAXC; ++q) {
             const int j = tj + 16 * q;
             u[q] = j < N ? A[k * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         for (int i = ti; i < N; i += kGJThreads / 16) {
             if (i == k) continue;
             const float4 f = colk[i];
-            float4 v[kGJMaxCols];
+            float4 v[MAXC];
 #pragma unroll
-            for (int q = 0; q < kGJMaxCols; ++q) {
+            for (int q = 0; q < MAXC; ++q) {
                 const int j = tj + 16 * q;
                 v[q] = (j < N && j != k) ? A[i * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
-            for (int q = 0; q < kGJMaxCols; ++q) v[q] = cdf_sub_mul(v[q], f, u[q]);
+            for (int q = 0; q < MAXC; ++q) v[q] = cdf_sub_mul(v[q], f, u[q]);
 #pragma unroll
-            for (int q = 0; q < kGJMaxCols; ++q) {
+            for (int q = 0; q < MAXC; ++q) {
                 const int j = tj + 16 * q;
                 if (j < N) A[i * N + j] = v[q];
             }
@@ -958,11 +959,22 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
             StageScope sc(c, "inverse_df", 1);
             const size_t smem = (size_t)N * N * sizeof(double2) + (size_t)2 * N * sizeof(double2) +
                                 2 * N * sizeof(int) + 16;
-            LOAF_CUDA(cudaFuncSetAttribute(gauss_jordan_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            gauss_jordan_kernel<<<W, kGJThreads, smem, c->stream>>>(
-                N, kpad, W, c->w_oz_S.as<double2>(), Bt + bt_spin * s, cexp(s), gmx(s),
-                c->w_logdet.as<double2>() + (size_t)s * W, c->w_status.as<int>() + (size_t)s * W);
+            // as many column slots per thread as N needs: empty slots would still
+            // be computed (on zeros) in every elimination step
+            auto launch = [&](auto kern) {
+                LOAF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                kern<<<W, kGJThreads, smem, c->stream>>>(
+                    N, kpad, W, c->w_oz_S.as<double2>(), Bt + bt_spin * s, cexp(s), gmx(s),
+                    c->w_logdet.as<double2>() + (size_t)s * W, c->w_status.as<int>() + (size_t)s * W);
+            };
+            switch (ceil_div(N, 16)) {
+                case 1: launch(gauss_jordan_kernel<1>); break;
+                case 2: launch(gauss_jordan_kernel<2>); break;
+                case 3: launch(gauss_jordan_kernel<3>); break;
+                case 4: launch(gauss_jordan_kernel<4>); break;
+                case 5: launch(gauss_jordan_kernel<5>); break;
+                default: launch(gauss_jordan_kernel<kGJMaxCols>); break;
+            }
             LOAF_LAUNCH_CHECK();
         }
     }
