@@ -204,10 +204,13 @@ __device__ inline long long fx_round(long long T, int sh) {
     return (T + (1LL << (sh - 1))) >> sh;
 }
 
-// a 64-bit integer as a float from two 32-bit conversions (within two units in
-// the last place; avoids the 64-bit conversion, which runs on the FP64 pipe)
+// a 64-bit integer as a float from two 32-bit conversions of its magnitude
+// (|D| < 2^32: correctly rounded; above, within one unit in the last place;
+// avoids the 64-bit conversion, which runs on the FP64 pipe)
 __device__ inline float ll_to_float(long long D) {
-    return fmaf(__int2float_rn((int)(D >> 32)), 4294967296.f, __uint2float_rn((unsigned)(D & 0xffffffffLL)));
+    const unsigned long long a = D < 0 ? 0ull - (unsigned long long)D : (unsigned long long)D;
+    const float f = fmaf(__uint2float_rn((unsigned)(a >> 32)), 4294967296.f, __uint2float_rn((unsigned)(a & 0xffffffffull)));
+    return D < 0 ? -f : f;
 }
 
 // Phi_T^T rows i (per-row exponent), K = basis p: A_S[s][i][p_pad]

@@ -311,6 +311,18 @@ struct CoulParams {
     int* err;
 };
 
+// the FP64 value of a float from its bit pattern with integer operations only
+// (the conversion instruction runs on the FP64 pipe, 1/64 of the FP32 rate);
+// exact for normal floats and infinities, 0 for zero and subnormal floats
+__device__ __forceinline__ double f2d_bits(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned long long ex = e == 0xffu ? 0x7ffull : (unsigned long long)(e + (1023u - 127u));
+    const unsigned long long bits = ((unsigned long long)(b >> 31) << 63) | (ex << 52) |
+                                    ((unsigned long long)(b & 0x7fffffu) << 29);
+    return e == 0 ? 0.0 : __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
     const float s = hi + x;
     const float bp = s - hi;
@@ -475,9 +487,9 @@ coulomb_tc_kernel(CoulParams P) {
                     P.part + ((size_t)sp * P.rows + g) * P.ldp + (size_t)wt * kCBN + h * 32);
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    dst[k] = make_double2((double)hi[2 * k] + (double)lo[(2 * k) * kCEpiWarps * 32],
-                                          (double)hi[2 * k + 1] +
-                                              (double)lo[(2 * k + 1) * kCEpiWarps * 32]);
+                    dst[k] = make_double2(f2d_bits(hi[2 * k]) + f2d_bits(lo[(2 * k) * kCEpiWarps * 32]),
+                                          f2d_bits(hi[2 * k + 1]) +
+                                              f2d_bits(lo[(2 * k + 1) * kCEpiWarps * 32]));
             }
         }
     }
@@ -678,9 +690,9 @@ coulomb_tc_pair_kernel(CoulParams P) {
                     P.part + ((size_t)sp * P.rows + g) * P.ldp + (size_t)wt * kCBN + h * 32);
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    dst[k] = make_double2((double)hi[2 * k] + (double)lo[(2 * k) * kCEpiWarps * 32],
-                                          (double)hi[2 * k + 1] +
-                                              (double)lo[(2 * k + 1) * kCEpiWarps * 32]);
+                    dst[k] = make_double2(f2d_bits(hi[2 * k]) + f2d_bits(lo[(2 * k) * kCEpiWarps * 32]),
+                                          f2d_bits(hi[2 * k + 1]) +
+                                              f2d_bits(lo[(2 * k + 1) * kCEpiWarps * 32]));
             }
         }
     }
@@ -910,29 +922,32 @@ lo_exchange_tc_kernel(LoParams P) {
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive_remote(even_tmem_empty);
                 }
+                // per rank and walker: p db + q da + it da db with da, db in units of
+                // the walker's power-of-two Delta scale it; the overall factor it
+                // is applied once after the sum over ranks (exact)
                 float v[32];
 #pragma unroll
                 for (int m = 0; m < 16; ++m) {
                     const int w = wt * kBNW + ch * 16 + m;
-                    const float it = w < P.W ? __ldg(P.inv_t + w) : 0.f;
+                    const float itq = cq * (w < P.W ? __ldg(P.inv_t + w) : 0.f);
                     const float ar = va[2 * m], ai = va[2 * m + 1];
                     const float br = vb[2 * m], bi = vb[2 * m + 1];
                     const float lr = fmaf(cb, br, ca * ar), li = fmaf(cb, bi, ca * ai);
-                    const float qr = cq * fmaf(ar, br, -ai * bi), qi = cq * fmaf(ar, bi, ai * br);
-                    v[2 * m] = it * fmaf(it, qr, lr);
-                    v[2 * m + 1] = it * fmaf(it, qi, li);
+                    v[2 * m] = fmaf(itq, fmaf(ar, br, -ai * bi), lr);
+                    v[2 * m + 1] = fmaf(itq, fmaf(ar, bi, ai * br), li);
                 }
                 const float r = tc::warp_transpose_sum(v, lane);
-                sh.red[q][ch * 32 + lane] = r;
+                const int wl = wt * kBNW + ch * 16 + (lane >> 1);  // this lane's sum: walker wl
+                sh.red[q][ch * 32 + lane] = r * (wl < P.W ? __ldg(P.inv_t + wl) : 0.f);
             }
             tph ^= 1;
             asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
             if (ep_tid < kBNW) {
                 const int w = wt * kBNW + ep_tid;
-                const double re = (double)sh.red[0][2 * ep_tid] + sh.red[1][2 * ep_tid] +
-                                  sh.red[2][2 * ep_tid] + sh.red[3][2 * ep_tid];
-                const double im = (double)sh.red[0][2 * ep_tid + 1] + sh.red[1][2 * ep_tid + 1] +
-                                  sh.red[2][2 * ep_tid + 1] + sh.red[3][2 * ep_tid + 1];
+                const double re = f2d_bits(sh.red[0][2 * ep_tid]) + f2d_bits(sh.red[1][2 * ep_tid]) +
+                                  f2d_bits(sh.red[2][2 * ep_tid]) + f2d_bits(sh.red[3][2 * ep_tid]);
+                const double im = f2d_bits(sh.red[0][2 * ep_tid + 1]) + f2d_bits(sh.red[1][2 * ep_tid + 1]) +
+                                  f2d_bits(sh.red[2][2 * ep_tid + 1]) + f2d_bits(sh.red[3][2 * ep_tid + 1]);
                 if (w < P.W) P.part[(size_t)pti * P.ldp + w] = make_double2(re, im);
             }
             asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
@@ -1456,7 +1471,9 @@ void coulomb_mixed(loaf_ctx* c, MixedOps& mx, int W, bool bf16, const float* inv
     const int tiles = (P.n_mt / 2) * P.n_wt;
     // the split fixes the chain boundaries of the FP32 accumulation, so it depends
     // on the device only (not on an SM budget): results do not depend on scheduling
-    P.n_split = wave_splits(tiles, std::min(16, ceil_div(P.nk, kCGroup)), c->sm_count / 2);
+    // at least 64 k-chunks (32 chains) per unit: every unit ends in an FP64 write of
+    // its partial sums, whose cost does not shrink with the unit
+    P.n_split = wave_splits(tiles, std::max(1, std::min(16, P.nk / 64)), c->sm_count / 2);
     P.ldp = P.n_wt * kCBN;
     P.idesc = tc::idesc_f16(2 * kBM, kCBN, bf16);  // pair MMA: M = 256, N = 128
     P.err = err;
