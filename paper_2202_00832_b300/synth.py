@@ -315,3 +315,77 @@ def small_case(M: int, N: int, X: int, W: int, seed: int = 7, eps: float = 0.1,
     mol = make_molecule(f"small_M{M}_N{N}_X{X}", M, X, N, nb, geometry, seed)
     walk = make_walkers(mol, W, eps, seed * 1000 + 1)
     return mol, walk
+
+
+# ---------------------------------------------------------------------------
+# multi-determinant (CAS) trial
+# ---------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class CASTrial:
+    """A closed-shell multi-determinant trial sum_d c_d |Phi_d>.
+
+    C holds the n_inact inactive orbitals followed by the n_act active ones
+    (orthonormal columns).  Every determinant occupies N = n_inact + n_occ_act
+    spatial orbitals, listed by slot: the reference occupies orbitals 0..N-1 in
+    slot order, and an excited determinant puts each new active orbital in the
+    slot of the reference orbital it replaces.  dets[0] is the reference.
+    """
+
+    C: np.ndarray                 # (M, n_inact + n_act)
+    n_inact: int
+    n_act: int
+    N: int                        # occupied orbitals per spin (both spins alike)
+    dets: List[List[int]]         # per determinant: orbital index of each slot
+    coeffs: np.ndarray            # (n_det,) float64
+
+    @property
+    def n_det(self) -> int:
+        return len(self.dets)
+
+    @property
+    def max_excitation(self) -> int:
+        ref = self.dets[0]
+        return max(sum(1 for a, b in zip(d, ref) if a != b) for d in self.dets)
+
+
+def make_cas_trial(mol: Molecule, n_inact: int, n_act: int, n_det: int, max_exc: int,
+                   seed: int) -> CASTrial:
+    """A seeded CAS-like expansion on the lowest eigenvectors of h.
+
+    Orbitals: the lowest n_inact + n_act eigenvectors of h.  The reference
+    occupies the lowest N = mol.n_alpha of them; the other determinants replace
+    1..max_exc of the reference's active orbitals by virtual active ones, drawn
+    without repetition (seeded).  Coefficients: c_0 = 1, the rest N(0, 1)
+    scaled by 0.3 / (1 + rank).  Closed shell only.
+    """
+    if mol.n_alpha != mol.n_beta:
+        raise ValueError("the CAS trial is built for closed shells")
+    N = mol.n_alpha
+    if not (0 <= n_inact < N < n_inact + n_act <= mol.M):
+        raise ValueError("need n_inact < N < n_inact + n_act <= M")
+    evals, evecs = np.linalg.eigh(mol.h)
+    C = np.ascontiguousarray(evecs[:, :n_inact + n_act])
+    ref = list(range(N))
+    occ_act = list(range(n_inact, N))          # active orbitals occupied in the reference
+    virt_act = list(range(N, n_inact + n_act))  # active orbitals empty in the reference
+    rng = np.random.default_rng(seed)
+    dets, seen = [ref], {tuple(ref)}
+    kmax = min(max_exc, len(occ_act), len(virt_act))
+    tries = 0
+    while len(dets) < n_det and tries < 100 * n_det:
+        tries += 1
+        k = int(rng.integers(1, kmax + 1))
+        out = sorted(rng.choice(occ_act, size=k, replace=False).tolist())
+        inn = rng.choice(virt_act, size=k, replace=False).tolist()
+        d = list(ref)
+        for o, a in zip(out, inn):
+            d[ref.index(o)] = int(a)
+        if tuple(d) not in seen:
+            seen.add(tuple(d))
+            dets.append(d)
+    coeffs = np.empty(len(dets))
+    coeffs[0] = 1.0
+    coeffs[1:] = rng.standard_normal(len(dets) - 1) * 0.3 / (1.0 + np.arange(1, len(dets)))
+    return CASTrial(C=C, n_inact=n_inact, n_act=n_act, N=N, dets=dets, coeffs=coeffs)
