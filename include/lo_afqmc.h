@@ -221,6 +221,37 @@ loaf_status walkers_force_bias(loaf_ctx *ctx, int W, const void *phi, int precis
 loaf_status walkers_propagator(loaf_ctx *ctx, int W, const void *x, int precision, void *v_out);
 
 /*
+ * walkers_energy_cas -- mixed-estimate local energy with a multi-determinant
+ * (CAS) trial sum_d c_d |Phi_d>, through Sherman-Morrison-Woodbury updates of
+ * the reference determinant (Sec. 3.1.2: eqs. Q_SMW_reg, Q_SMW, BigQ and
+ * 2e_HR_RCAS).  FP64.  The context holds the CAS orbitals as its trial:
+ * ao_load_cholesky with a closed shell of n_alpha = n_beta = n_cas orbitals
+ * (inactive orbitals first, localized as the caller wants them), then
+ * lo_localize_compress(localize = 0) for the factors of every CAS orbital pair.
+ * Every determinant is closed shell and occupies N of the CAS orbitals.
+ *   W, N       walkers; occupied orbitals per spin (1 <= N <= min(64, n_cas))
+ *   phi        W x M x N complex128 walkers (both spins alike), host or device
+ *   n_det      number of determinants (>= 1)
+ *   dets       n_det x N int32 (host): the CAS orbital in each slot; dets[0] is
+ *              the reference, and every other determinant keeps the reference's
+ *              orbital in all but at most 8 slots
+ *   coeffs     n_det doubles (host): c_d
+ *   e_out      W complex128: sum_d c_d <Phi_d|phi> E_d / sum_d c_d <Phi_d|phi>
+ *   logov_out  W complex128 or NULL: log sum_d c_d <Phi_d|phi> (both spins)
+ *   walker_status  W ints (LOAF_WALKER_*) or NULL
+ * A determinant whose overlap with a walker is exactly zero gets weight 0.
+ * Workspace on the device grows with W (X + 1) n_cas N and W (sum of kept
+ * ranks) N complex values.  Errors: LOAF_ERR_NOT_READY without
+ * lo_localize_compress or for an open shell; LOAF_ERR_SHAPE for N or an
+ * excitation rank beyond the limits; LOAF_ERR_ARG for an orbital index outside
+ * 0..n_cas-1 or repeated within a determinant; LOAF_ERR_SINGULAR /
+ * LOAF_ERR_NAN when a reference overlap is singular / not finite (the other
+ * walkers are still evaluated).
+ */
+loaf_status walkers_energy_cas(loaf_ctx *ctx, int W, int N, const void *phi, int n_det, const int *dets,
+                               const double *coeffs, void *e_out, void *logov_out, int *walker_status);
+
+/*
  * walkers_theta -- the first stage alone: Theta = phi (Phi_T^T phi)^-1 and
  * log det, per spin (eq. Q).  theta_out: W x Ntot x M complex128 (orbital-
  * major: theta_out[w][i][r] = Theta_ri), logdet_out: W complex128.  The

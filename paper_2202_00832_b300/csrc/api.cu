@@ -847,6 +847,53 @@ loaf_status walkers_propagator(loaf_ctx* c, int W, const void* x, int precision,
     });
 }
 
+loaf_status walkers_energy_cas(loaf_ctx* c, int W, int N, const void* phi, int n_det, const int* dets,
+                               const double* coeffs, void* e_out, void* logov_out, int* walker_status) {
+    if (!c) return LOAF_ERR_ARG;
+    int bad = 0;
+    loaf_status st = guarded(c, [&] {
+        LOAF_CUDA(cudaSetDevice(c->device));
+        LOAF_REQUIRE(c->loaded, LOAF_ERR_NOT_READY, "ao_load_cholesky has not been called");
+        LOAF_REQUIRE(c->compressed, LOAF_ERR_NOT_READY, "lo_localize_compress has not been called");
+        LOAF_REQUIRE(c->closed && c->nspin == 1, LOAF_ERR_NOT_READY, "the CAS orbitals must be loaded as a closed shell");
+        LOAF_REQUIRE(W >= 1, LOAF_ERR_ARG, "W must be >= 1");
+        LOAF_REQUIRE(phi && dets && coeffs && e_out, LOAF_ERR_ARG, "phi, dets, coeffs or e_out is NULL");
+        cas_check_dets(N, c->sp[0].N, n_det, dets);
+        const size_t bytes = (size_t)W * c->M * N * sizeof(double2);
+        const double2* dphi;
+        if (is_device_ptr(phi)) {
+            dphi = static_cast<const double2*>(phi);
+        } else {
+            c->w_phi.ensure(bytes);
+            LOAF_CUDA(cudaMemcpyAsync(c->w_phi.ptr, phi, bytes, cudaMemcpyHostToDevice, c->stream));
+            dphi = c->w_phi.as<double2>();
+        }
+        c->w_out.ensure((size_t)2 * W * sizeof(double2) + (size_t)W * sizeof(int));
+        double2* de = c->w_out.as<double2>();
+        double2* dlo = de + W;
+        int* dst = reinterpret_cast<int*>(dlo + W);
+        run_energy_cas(c, W, N, dphi, n_det, dets, coeffs, de, dlo, dst);
+        deliver(c, e_out, de, (size_t)W * sizeof(double2));
+        deliver(c, logov_out, dlo, (size_t)W * sizeof(double2));
+        std::vector<int> hst(W);
+        LOAF_CUDA(cudaMemcpyAsync(hst.data(), dst, (size_t)W * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        LOAF_CUDA(cudaStreamSynchronize(c->stream));
+        if (walker_status) {
+            if (is_device_ptr(walker_status))
+                LOAF_CUDA(cudaMemcpy(walker_status, dst, (size_t)W * sizeof(int), cudaMemcpyDeviceToDevice));
+            else
+                std::copy(hst.begin(), hst.end(), walker_status);
+        }
+        for (int v : hst)
+            if (v != LOAF_WALKER_OK && bad == 0) bad = v;
+    });
+    if (st == LOAF_OK && bad) {
+        c->err = "at least one walker's reference overlap is singular or non-finite";
+        return bad == LOAF_WALKER_SINGULAR ? LOAF_ERR_SINGULAR : LOAF_ERR_NAN;
+    }
+    return st;
+}
+
 loaf_status walkers_pair_exchange(loaf_ctx* c, int W, const void* phi, int precision,
                                   void* e_pairs_out) {
     if (!c) return LOAF_ERR_ARG;

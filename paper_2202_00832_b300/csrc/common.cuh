@@ -297,6 +297,7 @@ struct loaf_ctx {
     int d_keep_version = -1;
     double feat_mu[8] = {0}, feat_sd[8] = {1, 1, 1, 1, 1, 1, 1, 1}, tgt_mu = 0.0, tgt_sd = 1.0;
 
+    loaf::DevBuf w_cas;                // multi-determinant (CAS) energy workspace
     // workspace for walkers_energy (grown to the largest W seen)
     int ws_W = 0;
     loaf::DevBuf w_phi, w_theta, w_z, w_lu, w_perm, w_logdet, w_status, w_out, w_part,
@@ -374,6 +375,10 @@ void tc_split_gemm(loaf_ctx* c, const uint16_t* a_hi, const uint16_t* a_lo, int 
                    const float* inv_col, long out_ld, int out_W);
 // V_w = sum_g x_wg L_g for W walkers (x: W x X, V: W x M x M, device)
 void run_propagator(loaf_ctx* c, int W, const double2* x, int precision, double2* V);
+// multi-determinant (CAS) trial: argument checks (host) and the FP64 energy
+void cas_check_dets(int N, int Nc, int n_det, const int* dets);
+void run_energy_cas(loaf_ctx* c, int W, int N, const double2* phi, int n_det, const int* h_dets,
+                    const double* h_coeffs, double2* e_dev, double2* logov_dev, int* status_dev);
 // <L_g>_w of the batch whose Delta tiles the tensor-core Theta stage wrote
 void run_force_bias_mixed(loaf_ctx* c, int W, int precision, double2* e_scratch, double2* j_out);
 void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2* theta,

@@ -43,6 +43,7 @@ SIGNATURES = [
     ("walkers_theta", _I, [_P, _I, _P, _P, _P, _P]),
     ("walkers_force_bias", _I, [_P, _I, _P, _I, _P, _P, _P]),
     ("walkers_propagator", _I, [_P, _I, _P, _I, _P]),
+    ("walkers_energy_cas", _I, [_P, _I, _I, _P, _I, _P, _P, _P, _P, _P]),
     ("walkers_pair_exchange", _I, [_P, _I, _P, _I, _P]),
     ("loaf_num_pairs", _I, [_P]),
     ("lo_get_localized_trial", _I, [_P, _I, _P]),
@@ -251,6 +252,25 @@ class Context:
         self._check(self._lib.walkers_propagator(self._h, W, _ptr(x), PRECISIONS.get(precision, precision),
                                                  _ptr(out)), "walkers_propagator")
         return out
+
+    def walkers_energy_cas(self, phi, dets, coeffs, e_out=None, logov_out=None, walker_status=None):
+        """Mixed-estimate energy with a CAS trial (the context's trial = the CAS
+        orbitals): phi W x M x N complex128, dets n_det x N int32 (dets[0] the
+        reference), coeffs n_det float64.  Returns (E, log overlap, status)."""
+        _check_dtype(phi, "c16")
+        W, N = int(phi.shape[0]), int(phi.shape[2])
+        dets = np.ascontiguousarray(dets, dtype=np.int32)
+        coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+        if e_out is None:
+            e_out = np.zeros(W, dtype=np.complex128)
+        if logov_out is None and isinstance(phi, np.ndarray):
+            logov_out = np.zeros(W, dtype=np.complex128)
+        if walker_status is None and isinstance(phi, np.ndarray):
+            walker_status = np.zeros(W, dtype=np.int32)
+        self._check(self._lib.walkers_energy_cas(self._h, W, N, _ptr(phi), int(dets.shape[0]), _ptr(dets),
+                                                 _ptr(coeffs), _ptr(e_out), _ptr(logov_out),
+                                                 _ptr(walker_status)), "walkers_energy_cas")
+        return e_out, logov_out, walker_status
 
     def walkers_force_bias(self, phi, precision="fp64", out=None, logdet_out=None,
                            walker_status=None):
