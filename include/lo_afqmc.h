@@ -240,8 +240,8 @@ loaf_status walkers_propagator(loaf_ctx *ctx, int W, const void *x, int precisio
  *   logov_out  W complex128 or NULL: log sum_d c_d <Phi_d|phi> (both spins)
  *   walker_status  W ints (LOAF_WALKER_*) or NULL
  * A determinant whose overlap with a walker is exactly zero gets weight 0.
- * Workspace on the device grows with W (X + 1) n_cas N and W (sum of kept
- * ranks) N complex values.  Errors: LOAF_ERR_NOT_READY without
+ * Workspace on the device grows with W (X + 1) n_cas C and W (sum of kept
+ * ranks) C complex values, C = 1 + the number of slots some determinant changes.  Errors: LOAF_ERR_NOT_READY without
  * lo_localize_compress or for an open shell; LOAF_ERR_SHAPE for N or an
  * excitation rank beyond the limits; LOAF_ERR_ARG for an orbital index outside
  * 0..n_cas-1 or repeated within a determinant; LOAF_ERR_SINGULAR /

@@ -201,30 +201,48 @@ __global__ void cas_theta_kernel(int M, int N, const double2* __restrict__ phi, 
     th0[(size_t)w * M * N + e] = acc;
 }
 
-// out[w * out_stride + row N + s] = sum_r F[row][r] Theta^0[w][r][s] for `rows`
-// real rows of length M (packed factor rows, hbar rows, Lbar rows)
-__global__ void cas_project_kernel(int M, int N, long rows, const double* __restrict__ F,
+// Projections of the reference columns, only those a determinant can use
+// (eq. BigQ and the intermediates table): column 0 is the fixed slot of the
+// row's orbital (the slot it holds in every determinant, if any; else zeros),
+// columns 1..nv the variable slots (those some determinant changes).
+//   out[w * out_stride + row C + c] = sum_r F[row][r] Theta^0[w][r][slot(row, c)]
+// The row's orbital: mode 0, orbital b of its pair (Ubar rows), mode 1,
+// orbital a (Vbar rows), mode 2, row mod Nc (Lbar and hbar rows).
+__global__ void cas_project_kernel(int M, int N, int C, long rows, const double* __restrict__ F,
                                    const double2* __restrict__ th0, double2* __restrict__ out,
-                                   size_t out_stride) {
+                                   size_t out_stride, int mode, int Nc, const int* __restrict__ row_pair,
+                                   const int* __restrict__ pa, const int* __restrict__ pb,
+                                   const int* __restrict__ fixed_slot, const int* __restrict__ var_slot) {
     const int w = blockIdx.y;
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= rows * N) return;
-    const long row = e / N;
-    const int s = (int)(e - row * N);
-    const double* f = F + row * M;
-    const double2* t = th0 + (size_t)w * M * N + s;
+    if (e >= rows * C) return;
+    const long row = e / C;
+    const int c = (int)(e - row * C);
+    int s;
+    if (c > 0) {
+        s = var_slot[c - 1];
+    } else {
+        const int orb = mode == 0 ? pb[row_pair[row]] : mode == 1 ? pa[row_pair[row]] : (int)(row % Nc);
+        s = fixed_slot[orb];
+    }
     double2 acc = make_double2(0.0, 0.0);
-    for (int r = 0; r < M; ++r) {
-        const double c = f[r];
-        const double2 v = t[(size_t)r * N];
-        acc.x = fma(c, v.x, acc.x);
-        acc.y = fma(c, v.y, acc.y);
+    if (s >= 0) {
+        const double* f = F + row * M;
+        const double2* t = th0 + (size_t)w * M * N + s;
+        for (int r = 0; r < M; ++r) {
+            const double cf = f[r];
+            const double2 v = t[(size_t)r * N];
+            acc.x = fma(cf, v.x, acc.x);
+            acc.y = fma(cf, v.y, acc.y);
+        }
     }
     out[(size_t)w * out_stride + e] = acc;
 }
 
 struct CasParams {
     int M, N, Nc, X, n_det;
+    int C;                      // projected columns: fixed slot + variable slots
+    const int* slot_col;        // N: column of each slot (0 for fixed slots)
     long R;                     // packed factor rows
     const int* dets;            // n_det x N
     const int* pair_id;         // Nc x Nc: pair index of (min, max)
@@ -232,9 +250,9 @@ struct CasParams {
     const long* off;            // per pair
     const double2* B;           // [W][Nc][N]
     const double2* Ainv;        // [W][N][N]
-    const double2* PL;          // [W][R][N]
-    const double2* PR;          // [W][R][N]
-    const double2* PJ;          // [W][X + 1][Nc][N]; plane X: hbar Theta^0
+    const double2* PL;          // [W][R][C]
+    const double2* PR;          // [W][R][C]
+    const double2* PJ;          // [W][X + 1][Nc][C]; plane X: hbar Theta^0
     double e0;
     double2* Ed;                // [W][n_det]
     double2* rd;                // [W][n_det]
@@ -329,30 +347,35 @@ __global__ void __launch_bounds__(kCasThreads) cas_det_energy_kernel(CasParams P
         return;
     }
     // column s of Q^d projected by a row: ref[row][s] - sum_e ref[row][slot_e] S[e][s]
+    // (projections stored by column: slot_col maps a slot to its column)
+    const int* scol = P.slot_col;
     auto qcol = [&](const double2* rowp, int s) {
-        double2 v = rowp[s];
-        for (int e = 0; e < k; ++e) v = zsub(v, zmul(rowp[slot[e]], S[e][s]));
+        double2 v = rowp[scol[s]];
+        for (int e = 0; e < k; ++e) v = zsub(v, zmul(rowp[scol[slot[e]]], S[e][s]));
         return v;
     };
-    const size_t plane = (size_t)Nc * N;
+    const int Cc = P.C;
+    const size_t plane = (size_t)Nc * Cc;
     const double2* PJw = P.PJ + (size_t)w * (P.X + 1) * plane;
     // one-body: 2 sum_s hbar[occ_s] . Q^d_s
     double2 e1 = make_double2(0.0, 0.0);
-    for (int s = tid; s < N; s += blockDim.x) e1 = zadd(e1, qcol(PJw + (size_t)P.X * plane + (size_t)occ[s] * N, s));
+    for (int s = tid; s < N; s += blockDim.x) e1 = zadd(e1, qcol(PJw + (size_t)P.X * plane + (size_t)occ[s] * Cc, s));
     e1 = zscale(block_sum2(e1, red), 2.0);
     // Coulomb: J_g = 2 sum_s Lbar_g[occ_s] . Q^d_s, E_J = 1/2 sum_g J_g^2
     double2 ej = make_double2(0.0, 0.0);
     for (int g = tid; g < P.X; g += blockDim.x) {
         double2 J = make_double2(0.0, 0.0);
-        for (int s = 0; s < N; ++s) J = zadd(J, qcol(PJw + (size_t)g * plane + (size_t)occ[s] * N, s));
+        for (int s = 0; s < N; ++s) J = zadd(J, qcol(PJw + (size_t)g * plane + (size_t)occ[s] * Cc, s));
         J = zscale(J, 2.0);
         ej = zadd(ej, zmul(J, J));
     }
     ej = zscale(block_sum2(ej, red), 0.5);
     // exchange: sum_{s,t} (Ubar^[ij]T Q_t) . (Vbar^[ij] Q_s), (i, j) = (occ_s, occ_t);
-    // for i > j the [ji] factors with U and V exchanged (Y^[ij] = Y^[ji]T)
-    const double2* PLw = P.PL + (size_t)w * P.R * N;
-    const double2* PRw = P.PR + (size_t)w * P.R * N;
+    // for i > j the [ji] factors with U and V exchanged (Y^[ij] = Y^[ji]T).  In
+    // both cases the Ubar rows of the stored pair (a, b) = (min, max) meet the
+    // column of b's slot and the Vbar rows that of a's slot.
+    const double2* PLw = P.PL + (size_t)w * P.R * Cc;
+    const double2* PRw = P.PR + (size_t)w * P.R * Cc;
     double2 ek = make_double2(0.0, 0.0);
     for (int e = tid; e < N * N; e += blockDim.x) {
         const int s = e / N, t = e - s * N;
@@ -363,8 +386,8 @@ __global__ void __launch_bounds__(kCasThreads) cas_det_energy_kernel(CasParams P
         const long o = P.off[n];
         const int K = P.K[n];
         for (int kk = 0; kk < K; ++kk) {
-            const double2 qL = qcol(Lside + (size_t)(o + kk) * N, t);
-            const double2 qR = qcol(Rside + (size_t)(o + kk) * N, s);
+            const double2 qL = qcol(Lside + (size_t)(o + kk) * Cc, t);
+            const double2 qR = qcol(Rside + (size_t)(o + kk) * Cc, s);
             ek = zmad(ek, qL, qR);
         }
     }
@@ -427,30 +450,59 @@ void run_energy_cas(loaf_ctx* c, int W, int N, const double2* phi, int n_det, co
     PairTable& pt = sp.pairs;
     const int M = c->M, X = c->X, Nc = sp.N;
     const long R = pt.rows;
-    // pair index of (min, max)
+    // pair index of (min, max); packed row -> pair
     std::vector<int> pid((size_t)Nc * Nc, 0);
     for (int n = 0; n < pt.npairs; ++n) pid[(size_t)pt.i[n] * Nc + pt.j[n]] = n;
-    const size_t per_w = (size_t)Nc * N + (size_t)N * N + (size_t)M * N + 2 * (size_t)R * N +
-                         (size_t)(X + 1) * Nc * N + 2 * (size_t)n_det + 1;
-    c->w_cas.ensure((size_t)W * per_w * sizeof(double2) + (size_t)n_det * N * sizeof(int) +
-                    (size_t)n_det * sizeof(double) + pid.size() * sizeof(int) + 4096);
+    std::vector<int> row_pair(std::max<long>(R, 1), 0);
+    for (int n = 0; n < pt.npairs; ++n)
+        for (int k = 0; k < pt.K[n]; ++k) row_pair[pt.off[n] + k] = n;
+    // variable slots (changed by some determinant) and the fixed slot of each orbital
+    std::vector<char> var(N, 0);
+    for (int d = 1; d < n_det; ++d)
+        for (int s = 0; s < N; ++s)
+            if (h_dets[(size_t)d * N + s] != h_dets[s]) var[s] = 1;
+    std::vector<int> var_slot, slot_col(N, 0), fixed_slot(Nc, -1);
+    for (int s = 0; s < N; ++s) {
+        if (var[s]) {
+            slot_col[s] = 1 + (int)var_slot.size();
+            var_slot.push_back(s);
+        } else {
+            fixed_slot[h_dets[s]] = s;
+        }
+    }
+    const int C = 1 + (int)var_slot.size();
+    const size_t per_w = (size_t)Nc * N + (size_t)N * N + (size_t)M * N + 2 * (size_t)R * C +
+                         (size_t)(X + 1) * Nc * C + 2 * (size_t)n_det + 1;
+    const size_t n_int = (size_t)n_det * N + 1 + pid.size() + row_pair.size() + var_slot.size() + N + Nc + 8;
+    c->w_cas.ensure((size_t)W * per_w * sizeof(double2) + (size_t)n_det * sizeof(double) + n_int * sizeof(int) +
+                    4096);
     double2* B = c->w_cas.as<double2>();
     double2* Ainv = B + (size_t)W * Nc * N;
     double2* th0 = Ainv + (size_t)W * N * N;
     double2* PL = th0 + (size_t)W * M * N;
-    double2* PR = PL + (size_t)W * R * N;
-    double2* PJ = PR + (size_t)W * R * N;
-    double2* Ed = PJ + (size_t)W * (X + 1) * Nc * N;
+    double2* PR = PL + (size_t)W * R * C;
+    double2* PJ = PR + (size_t)W * R * C;
+    double2* Ed = PJ + (size_t)W * (X + 1) * Nc * C;
     double2* rd = Ed + (size_t)W * n_det;
     double2* ldA = rd + (size_t)W * n_det;
-    int* d_dets = reinterpret_cast<int*>(ldA + W);
-    double* d_coeffs = reinterpret_cast<double*>(d_dets + (size_t)n_det * N + ((n_det * N) & 1));
-    int* d_pid = reinterpret_cast<int*>(d_coeffs + n_det);
-    LOAF_CUDA(cudaMemcpyAsync(d_dets, h_dets, (size_t)n_det * N * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    LOAF_CUDA(cudaMemcpyAsync(d_coeffs, h_coeffs, (size_t)n_det * sizeof(double), cudaMemcpyHostToDevice,
-                              c->stream));
-    LOAF_CUDA(cudaMemcpyAsync(d_pid, pid.data(), pid.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    StageScope sc(c, "cas_energy", 7);
+    double* d_coeffs = reinterpret_cast<double*>(ldA + W);
+    int* d_dets = reinterpret_cast<int*>(d_coeffs + n_det);
+    int* d_pid = d_dets + (size_t)n_det * N;
+    int* d_row_pair = d_pid + pid.size();
+    int* d_var = d_row_pair + row_pair.size();
+    int* d_slot_col = d_var + std::max<size_t>(var_slot.size(), 1);
+    int* d_fixed = d_slot_col + N;
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        if (bytes) LOAF_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    };
+    up(d_coeffs, h_coeffs, (size_t)n_det * sizeof(double));
+    up(d_dets, h_dets, (size_t)n_det * N * sizeof(int));
+    up(d_pid, pid.data(), pid.size() * sizeof(int));
+    up(d_row_pair, row_pair.data(), row_pair.size() * sizeof(int));
+    up(d_var, var_slot.data(), var_slot.size() * sizeof(int));
+    up(d_slot_col, slot_col.data(), (size_t)N * sizeof(int));
+    up(d_fixed, fixed_slot.data(), (size_t)Nc * sizeof(int));
+    StageScope sc(c, "cas_energy", R > 0 ? 9 : 7);
     cas_overlap_kernel<<<dim3(W, Nc), 64, 0, c->stream>>>(M, Nc, N, sp.d_trial.as<double>(), phi, B);
     LOAF_LAUNCH_CHECK();
     const size_t smem = (size_t)(N * N + N) * sizeof(double2);
@@ -459,24 +511,28 @@ void run_energy_cas(loaf_ctx* c, int W, int N, const double2* phi, int n_det, co
     LOAF_LAUNCH_CHECK();
     cas_theta_kernel<<<dim3(W, ceil_div((long)M * N, 256)), 256, 0, c->stream>>>(M, N, phi, Ainv, th0);
     LOAF_LAUNCH_CHECK();
+    const int* pa = pt.d_i.as<int>();
+    const int* pb = pt.d_j.as<int>();
     if (R > 0) {
-        cas_project_kernel<<<dim3(ceil_div(R * N, 256), W), 256, 0, c->stream>>>(
-            M, N, R, pt.d_U.as<double>(), th0, PL, (size_t)R * N);
+        cas_project_kernel<<<dim3(ceil_div(R * C, 256), W), 256, 0, c->stream>>>(
+            M, N, C, R, pt.d_U.as<double>(), th0, PL, (size_t)R * C, 0, Nc, d_row_pair, pa, pb, d_fixed, d_var);
         LOAF_LAUNCH_CHECK();
-        cas_project_kernel<<<dim3(ceil_div(R * N, 256), W), 256, 0, c->stream>>>(
-            M, N, R, pt.d_V.as<double>(), th0, PR, (size_t)R * N);
+        cas_project_kernel<<<dim3(ceil_div(R * C, 256), W), 256, 0, c->stream>>>(
+            M, N, C, R, pt.d_V.as<double>(), th0, PR, (size_t)R * C, 1, Nc, d_row_pair, pa, pb, d_fixed, d_var);
         LOAF_LAUNCH_CHECK();
     }
     // planes g < X: Lbar_g Theta^0 (the X Nc Lbar rows are contiguous); plane X: hbar Theta^0
-    const size_t pj_stride = (size_t)(X + 1) * Nc * N;
-    cas_project_kernel<<<dim3(ceil_div((long)X * Nc * N, 256), W), 256, 0, c->stream>>>(
-        M, N, (long)X * Nc, sp.d_Lbar.as<double>(), th0, PJ, pj_stride);
+    const size_t pj_stride = (size_t)(X + 1) * Nc * C;
+    cas_project_kernel<<<dim3(ceil_div((long)X * Nc * C, 256), W), 256, 0, c->stream>>>(
+        M, N, C, (long)X * Nc, sp.d_Lbar.as<double>(), th0, PJ, pj_stride, 2, Nc, d_row_pair, pa, pb, d_fixed,
+        d_var);
     LOAF_LAUNCH_CHECK();
-    cas_project_kernel<<<dim3(ceil_div((long)Nc * N, 256), W), 256, 0, c->stream>>>(
-        M, N, Nc, sp.d_hbar.as<double>(), th0, PJ + (size_t)X * Nc * N, pj_stride);
+    cas_project_kernel<<<dim3(ceil_div((long)Nc * C, 256), W), 256, 0, c->stream>>>(
+        M, N, C, Nc, sp.d_hbar.as<double>(), th0, PJ + (size_t)X * Nc * C, pj_stride, 2, Nc, d_row_pair, pa, pb,
+        d_fixed, d_var);
     LOAF_LAUNCH_CHECK();
     CasParams P;
-    P.M = M; P.N = N; P.Nc = Nc; P.X = X; P.n_det = n_det; P.R = R;
+    P.M = M; P.N = N; P.Nc = Nc; P.X = X; P.n_det = n_det; P.R = R; P.C = C; P.slot_col = d_slot_col;
     P.dets = d_dets; P.pair_id = d_pid; P.K = pt.d_K.as<int>(); P.off = pt.d_off.as<long>();
     P.B = B; P.Ainv = Ainv; P.PL = PL; P.PR = PR; P.PJ = PJ; P.e0 = c->e0; P.Ed = Ed; P.rd = rd;
     cas_det_energy_kernel<<<dim3(n_det, W), kCasThreads, 0, c->stream>>>(P);
