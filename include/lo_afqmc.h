@@ -46,7 +46,7 @@ typedef enum {
     LOAF_ERR_NOT_READY = 6,   /* required setup call has not been made */
     LOAF_ERR_TIMEOUT = 7,     /* a bounded device wait gave up */
     LOAF_ERR_NAN = 8,         /* non-finite input or result */
-    LOAF_ERR_UNSUPPORTED = 9  /* valid request this build does not provide */
+    LOAF_ERR_UNSUPPORTED = 9  /* valid request this library does not provide */
 } loaf_status;
 
 enum { LOAF_MODE_FULL = 0, LOAF_MODE_LO = 1, LOAF_MODE_LO_JK = 2 };
@@ -67,7 +67,7 @@ enum { LOAF_PREC_FP64 = 0, LOAF_PREC_FP16X3 = 1, LOAF_PREC_BF16X3 = 2 };
 /* Per-walker status codes written to walker_status[] */
 enum { LOAF_WALKER_OK = 0, LOAF_WALKER_SINGULAR = 1, LOAF_WALKER_NAN = 2 };
 
-/* Supported limits of this build. */
+/* Supported limits of this library. */
 #define LOAF_MAX_NOCC 96      /* occupied orbitals per spin (LU held in shared memory) */
 #define LOAF_MAX_BASIS 1536
 
