@@ -99,3 +99,31 @@ def test_cas_argument_checks():
     # the context still answers afterwards
     e, _, st = ctx.walkers_energy_cas(walk, cas.dets, cas.coeffs)
     assert np.all(st == 0) and np.all(np.isfinite(e))
+
+
+def test_cas_no_inactive_orbitals_one_walker():
+    mol, walk, cas = _system(M=20, N=5, X=40, W=1, n_inact=0, n_act=10, n_det=9, max_exc=3, seed=23)
+    prep = MD.prepare_cas(mol, cas, 0.0)
+    ctx, _ = _context(mol, prep.C, 0.0)
+    e, _, st = ctx.walkers_energy_cas(walk, cas.dets, cas.coeffs)
+    assert np.all(st == 0)
+    ref = MD.energy_multidet_lo(mol, cas, prep, walk[0])[0]
+    assert abs(e[0] - ref) <= TOL_E * abs(ref)
+
+
+def test_cas_largest_excitation_and_limit():
+    mol, walk, _ = _system(M=30, N=9, X=40, W=2, n_inact=1, n_act=20, n_det=2, max_exc=1, seed=29)
+    C = np.linalg.eigh(mol.h)[1][:, :21]
+    ref = list(range(9))
+    eight = [0] + list(range(9, 17))        # slots 1..8 changed
+    nine = list(range(9, 18))               # all nine slots changed
+    cas = synth.CASTrial(C, 1, 20, 9, [ref, eight], np.array([1.0, 0.4]))
+    prep = MD.prepare_cas(mol, cas, 0.0)
+    ctx, _ = _context(mol, prep.C, 0.0)
+    e, _, st = ctx.walkers_energy_cas(walk, cas.dets, cas.coeffs)
+    assert np.all(st == 0)
+    for w, phi in enumerate(walk):
+        r = MD.energy_multidet_lo(mol, cas, prep, phi)[0]
+        assert abs(e[w] - r) <= TOL_E * abs(r)
+    with pytest.raises(LoafError, match="SHAPE"):
+        ctx.walkers_energy_cas(walk, np.array([ref, nine], dtype=np.int32), np.array([1.0, 0.4]))
