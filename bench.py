@@ -331,10 +331,16 @@ def run_ours(args, rank, world, local):
     per_launch_ms = {k: v[0] / max(v[1], 1) for k, v in kernels.items()}
     # algorithmic work per launch (one launch covers the W-walker batch)
     lo_flops = 8.0 * M * sum_k * W                      # a = Ubar^T Theta_j, b = Vbar Theta_i
-    # issued MMA flops: pairs padded to an even number of 128-row tiles, 64-deep
-    # basis blocks, 256-column walker tiles, a and b sides, three hi/lo products
-    n_tiles = sum(2 * (((int(k) + 127) // 128 + 1) // 2) for k in msvd)
-    lo_issued = (n_tiles * 128 * 2 * 3 * 2 * (64 * ((M + 63) // 64))
+    # issued MMA flops: each pair's ranks in balanced chunks of at most 256
+    # rounded up to 16 (the MMA's N), 64-deep basis blocks, 256 walker rows
+    # (re/im) per 128 walkers, a and b sides, three hi/lo products
+    def chunk_cols(k):
+        if k <= 0:
+            return 0
+        nch = (k + 255) // 256
+        return nch * (((k + nch - 1) // nch + 15) // 16 * 16)
+    rank_cols = sum(chunk_cols(int(k)) for k in msvd)
+    lo_issued = (rank_cols * 2 * 3 * 2 * (64 * ((M + 63) // 64))
                  * (256 * ((W + 127) // 128)))
     coul_flops = 4.0 * (X + 1) * N * M * W            # dJ_g = sum_ir Lbar_gir Delta_ri (complex)
     theta_flops = (4.0 * N * N * M + 8.0 / 3.0 * N ** 3 + 8.0 * M * N * N) * W

@@ -148,13 +148,24 @@ __device__ void write_tile(const uint16_t* __restrict__ src, long ld, long row0,
     }
 }
 
-// LO operand tiles: tile t (list entry {row0, nvalid, -, block}) x basis block kb
+// LO weight half-tiles: list entry t = {row0, nvalid | H << 16, -, element offset};
+// its basis block kb holds H rows x 64 (swizzled image of H rows) at
+// offset + kb H 64, rows [row0, row0 + nvalid) of the plane, zero elsewhere
 __global__ void lo_tiles_kernel(const uint16_t* __restrict__ plane, int r_pad, int nkb,
                                 const int4* __restrict__ tiles, uint16_t* __restrict__ out) {
     const int4 t = tiles[blockIdx.x];
     const int kb = blockIdx.y;
-    write_tile(plane, r_pad, t.x, t.y, (long)kb * kTileK, r_pad - kb * kTileK,
-               out + ((size_t)t.w * nkb + kb) * kTileElems);
+    const int nvalid = t.y & 0xffff, H = t.y >> 16;
+    const long col0 = (long)kb * kTileK;
+    const int kvalid = r_pad - kb * kTileK;
+    uint16_t* dst = out + (size_t)(unsigned)t.w + (size_t)kb * H * kTileK;
+    for (int q = threadIdx.x; q < H * 8; q += blockDim.x) {
+        const int row = q >> 3, j = q & 7;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (row < nvalid && j * 8 < kvalid)
+            v = *reinterpret_cast<const uint4*>(plane + ((long)t.x + row) * r_pad + col0 + j * 8);
+        *reinterpret_cast<uint4*>(dst + sw128_elem(row, j * 8)) = v;
+    }
 }
 
 // Coulomb operand tiles [mt][c][kb] from the (X+1) x (ntot r_pad) plane
@@ -714,28 +725,28 @@ struct LoParams {
     const uint16_t* d_hi;  // Delta tiles [c][rb][kb]
     const uint16_t* d_lo;
     int nrb;
-    const int4* pt;       // pair tiles {row0, nvalid, ci << 16 | cj, tile block}
+    const int4* pt;       // half-tiles {row0, nvalid | H << 16, ci << 16 | cj, element offset}
     const float4* rowc;   // per packed row {inv_su, inv_sv, p, q}
     const float* inv_t;   // per walker inverse Delta scale
-    double2* part;        // [n_pt][ldp] per pair tile and walker
+    double2* part;        // [n_pt / 2][ldp] per rank chunk and walker
     int n_pt, n_wt, W, ldp, nk;
     uint32_t idesc;
     int* err;
 };
 
-// ---- LO exchange kernel: one CTA pair per (two tiles of a pair, 128 walkers) ----
-// The pair tile list gives every pair an even number of 128-row tiles; tiles
-// 2s and 2s+1 (same pair [ij]) form the 256 MMA rows of a cta_group::2 MMA:
-// the even CTA holds rows 0-127 (tile 2s), the odd CTA rows 128-255 (tile
-// 2s+1), and each holds half of the 256 walker columns of Delta.  Per CTA a
-// k-step of 32 basis functions then moves 64 KB (own weight tiles + half the
-// Delta tiles) instead of 96 KB for a single-CTA 128 x 256 tile.
-// The a (U, Delta_j) and b (V, Delta_i) products are independent GEMMs: the
-// TMA ring holds half-stages of one side each, 64 basis functions deep
-// (128-byte rows: 2 x 16 KB weight tiles + 2 x 16 KB Delta half-tiles = 64 KB),
-// three of them, consumed a, b, a, b, ...
+// ---- LO exchange kernel: one CTA pair per (rank chunk of a pair, 128 walkers) ----
+// A cta_group::2 MMA of M = 256 Delta rows (128 walkers x re/im; the even CTA
+// holds walkers 0-63 of the block, the odd CTA walkers 64-127) by N = the
+// chunk's ranks (at most 256, a multiple of 16; each CTA holds one half-tile of
+// N / 2 weight rows).  A pair's ranks are cut into balanced chunks, so rank
+// padding stays at a few percent.  The a (Delta_j, U) and b (Delta_i, V)
+// products are independent GEMMs: the ring holds half-stages of one side each,
+// 64 basis functions deep (2 x 16 KB Delta tile + 2 weight half-tiles), three
+// of them, consumed a, b, a, b, ...  TMEM lane = walker row, column = rank: the
+// epilogue sums over ranks along its own columns, with one lane-pair shuffle
+// for the complex product.
 constexpr int kLBK = kTileK;                                 // basis functions per k-step
-constexpr uint32_t kLTileA = kTileBytes;                     // 16 KB: 128 weight rows
+constexpr uint32_t kLTileA = kTileBytes;                     // 16 KB: up to 128 weight rows
 constexpr uint32_t kLTileBh = kTileBytes;                    // 16 KB: 128 Delta rows
 constexpr uint32_t kLSlotBytes = 2 * kLTileA + 2 * kLTileBh;  // 64 KB
 constexpr int kLSlots = 3;
@@ -750,7 +761,8 @@ struct LoShared {
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
-    float red[4][kBN];
+    float red[4][kBM];         // per column group: sum over its ranks, per walker row
+    float4 cst[kBN];           // per rank of the chunk: {p inv_sv, q inv_su, inv_su inv_sv, 0}
 };
 
 // Roles per CTA: warp 0 lane 0 TMA producer; warp 1 lane 0 the MMA issuer on
@@ -762,8 +774,8 @@ lo_exchange_tc_kernel(LoParams P) {
     extern __shared__ uint8_t dyn_smem[];
     __shared__ LoShared sh;
     uint8_t* base = align1024(dyn_smem);
-    // slot: W hi, W lo (8 KB each), D hi, D lo (8 KB each); W = U, D = Delta_j on
-    // the a side, W = V, D = Delta_i on the b side
+    // slot: W hi, W lo (the chunk's H weight rows, up to 16 KB each), D hi, D lo
+    // (16 KB each); W = U, D = Delta_j on the a side, W = V, D = Delta_i on the b side
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = tc::cluster_ctarank();
     const bool even = rank == 0;
@@ -799,17 +811,18 @@ lo_exchange_tc_kernel(LoParams P) {
         for (int u = cid; u < n_units && !*abort; u += n_cl) {
             const int4 t = P.pt[2 * (u / P.n_wt) + rank];
             const int rb = 2 * (u % P.n_wt) + (int)rank;  // this CTA's 128 Delta rows
+            const uint32_t wbytes = (uint32_t)(t.y >> 16) * 128u;  // H weight rows of 128 bytes
             for (int h = 0; h < 2 * P.nk; ++h) {
                 if (!tc::mbar_wait_cluster(&sh.empty[s], ph ^ 1, abort)) break;
                 uint8_t* st = base + s * kLSlotBytes;
-                tc::mbar_arrive_expect_tx(&sh.full[s], kLSlotBytes);
+                tc::mbar_arrive_expect_tx(&sh.full[s], 2 * wbytes + 2 * kLTileBh);
                 const int kb = h >> 1;
                 const bool side_b = h & 1;
-                const size_t ao = ((size_t)t.w * P.nk + kb) * kTileElems;
+                const size_t ao = (size_t)(unsigned)t.w + (size_t)kb * (t.y >> 16) * kTileK;
                 const int orb = side_b ? (t.z >> 16) : (t.z & 0xffff);
                 const size_t bo = (((size_t)orb * P.nrb + rb) * P.nk + kb) * kTileElems;
-                tc::bulk_load(st, (side_b ? P.v_hi : P.u_hi) + ao, kLTileA, &sh.full[s]);
-                tc::bulk_load(st + kLTileA, (side_b ? P.v_lo : P.u_lo) + ao, kLTileA, &sh.full[s]);
+                tc::bulk_load(st, (side_b ? P.v_hi : P.u_hi) + ao, wbytes, &sh.full[s]);
+                tc::bulk_load(st + kLTileA, (side_b ? P.v_lo : P.u_lo) + ao, wbytes, &sh.full[s]);
                 tc::bulk_load(st + 2 * kLTileA, P.d_hi + bo, kLTileBh, &sh.full[s]);
                 tc::bulk_load(st + 2 * kLTileA + kLTileBh, P.d_lo + bo, kLTileBh, &sh.full[s]);
                 filled |= 1u << s;
@@ -852,6 +865,9 @@ lo_exchange_tc_kernel(LoParams P) {
         uint32_t ph = 0, tph = 0;
         const uint32_t tA = tmem, tB = tmem + kBN;  // accumulators a (U side), b (V side)
         for (int u = cid; u < n_units && !*abort; u += n_cl) {
+            // N = the chunk's ranks = twice the half-tile height
+            const int Nc = 2 * (P.pt[2 * (u / P.n_wt)].y >> 16);
+            const uint32_t idesc = (P.idesc & ~(0x3fu << 17)) | ((uint32_t)(Nc >> 3) << 17);
             if (!tc::mbar_wait_cluster(&sh.tmem_empty, tph ^ 1, abort)) break;
             tc::tc_fence_after();
             bool ok = true;
@@ -868,9 +884,10 @@ lo_exchange_tc_kernel(LoParams P) {
                     const uint64_t dhi = tc::smem_desc(st + 2 * kLTileA + off, 128);
                     const uint64_t dlo = tc::smem_desc(st + 2 * kLTileA + kLTileBh + off, 128);
                     const uint32_t acc = (h > 1 || kk > 0) ? 1u : 0u;
-                    tc::mma_f16_pair(d, whi, dhi, P.idesc, acc);
-                    tc::mma_f16_pair(d, whi, dlo, P.idesc, 1u);
-                    tc::mma_f16_pair(d, wlo, dhi, P.idesc, 1u);
+                    // A = Delta rows (walkers), B = weight rows (ranks)
+                    tc::mma_f16_pair(d, dhi, whi, idesc, acc);
+                    tc::mma_f16_pair(d, dlo, whi, idesc, 1u);
+                    tc::mma_f16_pair(d, dhi, wlo, idesc, 1u);
                 }
                 tc::mma_commit_pair(&sh.empty[s], 0x3);
                 if (++s == kLSlots) { s = 0; ph ^= 1; }
@@ -884,71 +901,87 @@ lo_exchange_tc_kernel(LoParams P) {
         tc::mbar_wait(&sh.drain, 0, &never);
     } else if (warp >= 2) {
         // ---------------- epilogue (both CTAs) ----------------
-        // lane = rank within the tile; per walker m of a 16-walker chunk:
-        //   da = inv_su * inv_t * acc_a, db = inv_sv * inv_t * acc_b
-        //   val = p db + q da + da db   (complex; p, q real)
-        // then a butterfly reduction over the 32 ranks of the warp and a sum
-        // over the 4 lane quarters in shared memory.
+        // lane = walker row z = 2 w + re/im of this CTA, column = rank n of the
+        // chunk.  Per rank and walker (complex; the other component sits in the
+        // partner lane z ^ 1):
+        //   da = inv_su it a, db = inv_sv it b,   val = p db + q da + da db
+        // summed over this warp's column group (64 ranks, in 32-column loads);
+        // the four groups add in shared memory; one FP64 value per (chunk, walker).
         const int q = warp & 3;                       // TMEM lane quarter
-        const int sub = (warp - 2) >> 2;              // which pair of chunks
+        const int grp = (warp - 2) >> 2;              // column group
         const int ep_tid = threadIdx.x - 64;          // 0..511
-        constexpr int kChunks = kBN / 32 / (kLEpiWarps / 4);
+        const int z = q * 32 + lane;                  // walker row of this CTA
+        const bool odd = (lane & 1) != 0;             // imaginary component
         const uint32_t even_tmem_empty = tc::mapa_shared(&sh.tmem_empty, 0);
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         uint32_t tph = 0;
         for (int u = cid; u < n_units; u += n_cl) {
-            const int pti = 2 * (u / P.n_wt) + (int)rank, wt = u % P.n_wt;
-            const int4 t = P.pt[pti];
-            const int rl = q * 32 + lane;
-            float4 rc = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (rl < t.y) rc = P.rowc[t.x + rl];
-            const float cb = rc.z * rc.y;   // p * inv_sv
-            const float ca = rc.w * rc.x;   // q * inv_su
-            const float cq = rc.x * rc.y;   // inv_su * inv_sv
+            const int ch = u / P.n_wt, wt = u % P.n_wt;
+            const int4 t0 = P.pt[2 * ch], t1 = P.pt[2 * ch + 1];
+            const int Nc = 2 * (t0.y >> 16);
+            const int nvalid = (t0.y & 0xffff) + (t1.y & 0xffff);
+            const int w = wt * kBNW + (int)rank * (kBNW / 2) + (z >> 1);
+            const float it = w < P.W ? __ldg(P.inv_t + w) : 0.f;
+            // the chunk's per-rank constants (zero beyond its valid ranks); the
+            // previous unit's readers are past its closing barrier
+            if (ep_tid < kBN) {
+                float4 k4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ep_tid < nvalid) {
+                    const float4 rc = __ldg(P.rowc + t0.x + ep_tid);
+                    k4 = make_float4(rc.z * rc.y, rc.w * rc.x, rc.x * rc.y, 0.f);
+                }
+                sh.cst[ep_tid] = k4;
+            }
+            asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
             const bool got = tc::mbar_wait_cluster(&sh.tmem_full, tph, abort);
             // leave together: the named barriers below expect every epilogue warp
             if (tc::bar_or(!got, 1, 32 * kLEpiWarps)) break;
             tc::tc_fence_after();
+            const int c_begin = grp * 64;
+            const int nld = c_begin >= Nc ? 0 : (min(Nc - c_begin, 64) + 31) / 32;
+            if (nld == 0) {
+                // no columns for this warp: release at once
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive_remote(even_tmem_empty);
+            }
+            float acc = 0.f;
 #pragma unroll 1
-            for (int c2 = 0; c2 < kChunks; ++c2) {
-                const int ch = sub * kChunks + c2;
+            for (int c2 = 0; c2 < nld; ++c2) {
+                const int col0 = c_begin + 32 * c2;
                 float va[32], vb[32];
-                const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-                tc::tmem_ld32(tmem + lane_off + ch * 32, va);
-                tc::tmem_ld32(tmem + lane_off + kBN + ch * 32, vb);
+                tc::tmem_ld32(tmem + lane_off + col0, va);
+                tc::tmem_ld32(tmem + lane_off + kBN + col0, vb);
                 tc::tmem_wait_ld();
-                if (c2 == kChunks - 1) {
+                if (c2 == nld - 1) {
                     // the last TMEM read of this warp is complete: release
                     tc::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive_remote(even_tmem_empty);
                 }
-                // per rank and walker: p db + q da + it da db with da, db in units of
-                // the walker's power-of-two Delta scale it; the overall factor it
-                // is applied once after the sum over ranks (exact)
-                float v[32];
 #pragma unroll
-                for (int m = 0; m < 16; ++m) {
-                    const int w = wt * kBNW + ch * 16 + m;
-                    const float itq = cq * (w < P.W ? __ldg(P.inv_t + w) : 0.f);
-                    const float ar = va[2 * m], ai = va[2 * m + 1];
-                    const float br = vb[2 * m], bi = vb[2 * m + 1];
-                    const float lr = fmaf(cb, br, ca * ar), li = fmaf(cb, bi, ca * ai);
-                    v[2 * m] = fmaf(itq, fmaf(ar, br, -ai * bi), lr);
-                    v[2 * m + 1] = fmaf(itq, fmaf(ar, bi, ai * br), li);
+                for (int m = 0; m < 32; ++m) {
+                    const float a = va[m], b = vb[m];
+                    const float pa = __shfl_xor_sync(0xffffffffu, a, 1);
+                    const float pb = __shfl_xor_sync(0xffffffffu, b, 1);
+                    const float4 k4 = sh.cst[col0 + m];        // broadcast
+                    const float lin = fmaf(k4.x, b, k4.y * a);  // p inv_sv db' + q inv_su da'
+                    const float quad = odd ? fmaf(pa, b, a * pb) : fmaf(a, b, -pa * pb);
+                    const float v = fmaf(k4.z * it, quad, lin);
+                    // columns past the chunk were not written by this unit's MMAs
+                    acc += col0 + m < Nc ? v : 0.f;
                 }
-                const float r = tc::warp_transpose_sum(v, lane);
-                const int wl = wt * kBNW + ch * 16 + (lane >> 1);  // this lane's sum: walker wl
-                sh.red[q][ch * 32 + lane] = r * (wl < P.W ? __ldg(P.inv_t + wl) : 0.f);
             }
             tph ^= 1;
+            sh.red[grp][z] = acc * it;
             asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
-            if (ep_tid < kBNW) {
-                const int w = wt * kBNW + ep_tid;
+            if (ep_tid < kBNW / 2) {
+                const int wl = wt * kBNW + (int)rank * (kBNW / 2) + ep_tid;
                 const double re = f2d_bits(sh.red[0][2 * ep_tid]) + f2d_bits(sh.red[1][2 * ep_tid]) +
                                   f2d_bits(sh.red[2][2 * ep_tid]) + f2d_bits(sh.red[3][2 * ep_tid]);
                 const double im = f2d_bits(sh.red[0][2 * ep_tid + 1]) + f2d_bits(sh.red[1][2 * ep_tid + 1]) +
                                   f2d_bits(sh.red[2][2 * ep_tid + 1]) + f2d_bits(sh.red[3][2 * ep_tid + 1]);
-                if (w < P.W) P.part[(size_t)pti * P.ldp + w] = make_double2(re, im);
+                if (wl < P.W) P.part[(size_t)ch * P.ldp + wl] = make_double2(re, im);
             }
             asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
         }
@@ -1049,7 +1082,8 @@ __global__ void lo_tc_reduce_kernel(int n_pairs, int W, int ldp, const int* __re
     if (w < W) {
         for (int n = n0 + gg; n < n1; n += 8) {
             double2 d = make_double2(0.0, 0.0);
-            for (int k = 0; k < npt[n]; ++k) d = cadd(d, part[(size_t)(pt0[n] + k) * ldp + w]);
+            // a pair's half-tiles come in pairs, one partial row per pair of them
+            for (int k = 0; k < (npt[n] >> 1); ++k) d = cadd(d, part[(size_t)((pt0[n] >> 1) + k) * ldp + w]);
             if (e_pairs) e_pairs[(size_t)n * W + w] = make_double2(e0[n] + d.x, d.y);
             acc = cadd(acc, cscale(d, pw[n]));
         }
@@ -1162,6 +1196,8 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     std::vector<double> pw;
     std::vector<int4> tiles;
     std::vector<int> pt0(npairs), npt(npairs);
+    const int nkb = ceil_div(M, kTileK);
+    long woff = 0;  // weight half-tile elements so far
     long row_base = 0;
     int pair_base = 0;
     for (int s = 0; s < c->nspin; ++s) {
@@ -1236,16 +1272,23 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
             pt0[gpair] = (int)tiles.size();
             int cnt = 0;
             const int cij = ((sd.col0 + pt.i[n]) << 16) | (sd.col0 + pt.j[n]);
-            for (int k0 = 0; k0 < pt.K[n]; k0 += kBM) {
-                tiles.push_back(make_int4((int)(row_base + pt.off[n] + k0), std::min(kBM, pt.K[n] - k0),
-                                          cij, (int)tiles.size()));
-                ++cnt;
-            }
-            // the CTA-pair kernel takes a pair's tiles two at a time: an odd
-            // count gets an empty tile (no valid rows: zero operand, zero partials)
-            if (cnt & 1) {
-                tiles.push_back(make_int4((int)(row_base + pt.off[n]), 0, cij, (int)tiles.size()));
-                ++cnt;
+            // the pair's ranks in balanced chunks of at most 256 (the MMA's N, a
+            // multiple of 16); each chunk is two half-tiles of H = N / 2 rows, one
+            // per CTA of the pair, stored at element offset woff
+            const int K = pt.K[n];
+            if (K > 0) {
+                const int nch = (K + 255) / 256;
+                const int Nc = ((K + nch - 1) / nch + 15) / 16 * 16;
+                const int H = Nc / 2;
+                for (int ch = 0; ch < nch; ++ch)
+                    for (int hf = 0; hf < 2; ++hf) {
+                        const int r0 = ch * Nc + hf * H;
+                        const int nv = std::max(0, std::min(H, K - r0));
+                        tiles.push_back(make_int4((int)(row_base + pt.off[n] + (nv > 0 ? r0 : 0)),
+                                                  nv | (H << 16), cij, (int)woff));
+                        woff += (long)H * kTileK * nkb;
+                        ++cnt;
+                    }
             }
             npt[gpair] = cnt;
         }
@@ -1316,9 +1359,10 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     mx.h_e0 = e0;
     mx.screen_built = -1;
     // operand tiles [tile][kb]; the row-major staging planes are then dropped
-    mx.nkb = ceil_div(M, kTileK);
+    mx.nkb = nkb;
+    LOAF_REQUIRE(woff < (1L << 31), LOAF_ERR_SHAPE, "LO weight tiles beyond 2^31 elements");
     if (mx.n_pt > 0) {
-        const size_t tb = (size_t)mx.n_pt * mx.nkb * kTileBytes;
+        const size_t tb = (size_t)woff * sizeof(uint16_t);
         const dim3 tg(mx.n_pt, mx.nkb);
         DevBuf* dst[4] = {&mx.Ub_hi, &mx.Ub_lo, &mx.Vb_hi, &mx.Vb_lo};
         DevBuf* src[4] = {&mx.U_hi, &mx.U_lo, &mx.V_hi, &mx.V_lo};
