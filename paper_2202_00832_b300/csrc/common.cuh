@@ -209,14 +209,14 @@ struct MixedOps {
     long R = 0;
     DevBuf U_hi, U_lo, V_hi, V_lo;  // R x r_pad 16-bit
     DevBuf row_c;              // R float4 {inv_su, inv_sv, p, q}
-    DevBuf pt;                 // pair tiles int4 {row0, nvalid, ci << 16 | cj, tile block}
+    DevBuf pt;                 // weight half-tiles, two per rank chunk: int4 {row0, nvalid | H << 16, ci << 16 | cj, element offset}
     int n_pt = 0;
     int n_pairs = 0;           // pairs over both spins
-    DevBuf pair_pt0, pair_npt; // first pair tile and count per pair (int)
+    DevBuf pair_pt0, pair_npt; // first half-tile and half-tile count per pair (int, both even)
     DevBuf pair_w;             // per pair: 0.5 * mult * (1 or 2) (double)
     DevBuf e0;                 // per pair: trial value p . q (double)
     double EK0 = 0.0;          // 1/2 sum_sigma mult sum_n wgt_n e0_n
-    DevBuf Ub_hi, Ub_lo, Vb_hi, Vb_lo;  // LO operand tiles [tile][kb]
+    DevBuf Ub_hi, Ub_lo, Vb_hi, Vb_lo;  // LO weight half-tiles (H rows x 64 per basis block)
     // host copies of the unscreened tile list, and the screened list
     std::vector<int4> h_tiles;
     std::vector<int> h_pt0, h_npt, h_order;

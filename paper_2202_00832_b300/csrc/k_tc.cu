@@ -9,17 +9,20 @@
 //   A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi   (tcgen05.mma kind::f16, FP32 accumulate)
 // with power-of-two scales per operand row (weights) and per walker (Delta).
 //
-// Kernels (sm_103a, one CTA per SM, warp-specialised, 192 threads):
-//   coulomb_tc_kernel  dJ[g][w] = sum_(c,r) Lbar'[g][c][r] Delta[w][c][r]
-//                      (rows g < X: Cholesky vectors, row X: hbar -> dE1):
-//                      128-term TMEM chains folded into double-float
-//                      registers, FP64 partials per split of the contraction
-//                      (576 threads: 16 epilogue warps).
-//   lo_exchange_tc_kernel  per pair tile (<= 128 ranks of one pair [ij]) and
-//                      128 walkers: a = Ubar^T Delta_j, b = Vbar Delta_i in two
-//                      TMEM accumulators, then the epilogue forms
-//                      p.db + q.da + da.db and reduces over the ranks.
-// Warp 0 issues TMA loads, warp 1 issues tcgen05.mma, warps 2-5 drain TMEM.
+// Kernels (sm_103a, persistent, warp-specialised: one thread of warp 0 issues
+// the bulk copies, one of warp 1 the tcgen05.mma, 16 epilogue warps drain TMEM):
+//   coulomb_tc_pair_kernel  dJ[g][w] = sum_(c,r) Lbar'[g][c][r] Delta[w][c][r]
+//                      (rows g < X: Cholesky vectors, row X: hbar -> dE1) on CTA
+//                      pairs (cta_group::2, M = 256 rows g, N = 64 walkers x
+//                      re/im): 128-term TMEM chains folded into double-float,
+//                      FP64 partials per split of the contraction.
+//   coulomb_tc_kernel  the same contraction on single CTAs with a direct
+//                      walker-major output (the propagator operator).
+//   lo_exchange_tc_kernel  per rank chunk of a pair [ij] (at most 256 ranks) and
+//                      128 walkers, on CTA pairs (M = 256 Delta rows, N = the
+//                      chunk's ranks): a = Delta_j^T Ubar, b = Delta_i^T Vbar in
+//                      two TMEM accumulators, then the epilogue forms
+//                      p.db + q.da + da.db and sums over the ranks.
 // All mbarrier waits are bounded (tc_ptx.cuh); a timeout raises an error flag
 // the host turns into LOAF_ERR_TIMEOUT.
 #include "common.cuh"
@@ -35,8 +38,9 @@ namespace loaf {
 namespace {
 
 constexpr int kBM = 128;             // MMA rows per CTA
-constexpr int kBNW = 128;            // walkers per LO tile
-constexpr int kBN = 2 * kBNW;        // LO MMA columns: (walker, re/im) interleaved
+constexpr int kBNW = 128;            // walkers per LO unit (64 per CTA of the pair)
+constexpr int kBN = 2 * kBNW;        // LO: Delta rows per unit (walker, re/im) = the largest
+                                     // rank chunk = TMEM columns per accumulator
 
 
 __device__ inline double block_sum(double v, double* red) {
@@ -1637,7 +1641,8 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
                 c->nspin, s0, s1, theta, scale, c->w_dhi.as<uint16_t>(), c->w_dlo.as<uint16_t>());
         LOAF_LAUNCH_CHECK();
     }
-    const uint32_t idesc = tc::idesc_f16(2 * kBM, kBN, bf16);  // pair MMA: M = 256
+    // pair MMA: M = 256; N is set per unit from the chunk's rank count
+    const uint32_t idesc = tc::idesc_f16(2 * kBM, kBN, bf16);
 
     if (e_out) coulomb_mixed(c, mx, W, bf16, inv_t, err, e_out, nullptr);
     if (mode != LOAF_MODE_FULL) {
