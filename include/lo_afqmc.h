@@ -52,17 +52,24 @@ typedef enum {
 enum { LOAF_MODE_FULL = 0, LOAF_MODE_LO = 1, LOAF_MODE_LO_JK = 2 };
 
 /*
- * Arithmetic of the contractions (overlap, LU, log-det and Theta are FP64
- * in every mode; so is the final per-walker accumulation):
+ * Arithmetic of the contractions (the final per-walker accumulation is FP64
+ * in every mode):
  *   LOAF_PREC_FP64   every step in FP64 (CUDA cores).
  *   LOAF_PREC_FP16X3 Coulomb and LO-exchange contractions on the tcgen05
  *                    tensor cores: operands split into FP16 hi + lo parts
  *                    (power-of-two scaled), three products hi*hi + hi*lo +
  *                    lo*hi accumulated in FP32, applied to Theta - Phi_T
- *                    (the walker-independent trial part stays FP64).
+ *                    (the walker-independent trial part stays FP64).  In the
+ *                    LO modes the overlap S and Theta = phi S^-1 are exact
+ *                    products of 7-bit digit slices on the tensor cores, and
+ *                    S^-1 and log det S come from a double-float (2 x FP32,
+ *                    about 48 significant bits) Gauss-Jordan elimination.
  *   LOAF_PREC_BF16X3 the same with BF16 hi + lo parts.
+ *   LOAF_PREC_FP16X3_F64INV  LOAF_PREC_FP16X3 with S^-1 and log det S from a
+ *                    Gauss-Jordan elimination in FP64 (the overlap inversion
+ *                    and log-determinant kept in FP64 end to end).
  */
-enum { LOAF_PREC_FP64 = 0, LOAF_PREC_FP16X3 = 1, LOAF_PREC_BF16X3 = 2 };
+enum { LOAF_PREC_FP64 = 0, LOAF_PREC_FP16X3 = 1, LOAF_PREC_BF16X3 = 2, LOAF_PREC_FP16X3_F64INV = 3 };
 
 /* Per-walker status codes written to walker_status[] */
 enum { LOAF_WALKER_OK = 0, LOAF_WALKER_SINGULAR = 1, LOAF_WALKER_NAN = 2 };
@@ -346,6 +353,19 @@ loaf_status mlp_loss_grad(int device, int n, const float *x, const float *t, con
  */
 loaf_status walkers_theta_noalloc(loaf_ctx *ctx, int W, const void *phi, void *theta_out,
                                   void *logdet_out, int *walker_status);
+
+/*
+ * loaf_test_withhold_stage -- failure-path test hook (the paper has no
+ * counterpart).  The next n launches of the tensor-core LO exchange kernel on
+ * this context leave the first pipeline stage of one CTA pair unfilled: no
+ * copy is issued and no arrival is made, so that pair's bounded mbarrier waits
+ * run out after their limit (1 s of %globaltimer), every role of both CTAs
+ * leaves its loop, copies already issued are waited for (bounded), TMEM is
+ * freed, and the call that launched it returns LOAF_ERR_TIMEOUT.  Nothing
+ * faults or hangs; the context stays usable.  n = 0 (the default) turns it
+ * off.  Errors: LOAF_ERR_ARG for a NULL context or n < 0.
+ */
+loaf_status loaf_test_withhold_stage(loaf_ctx *ctx, int n);
 
 /*
  * Stage timers.  loaf_profile(ctx, 1) resets and enables CUDA-event timers

@@ -156,6 +156,43 @@ def pair_exchange(fac: PairFactors, th: np.ndarray) -> np.ndarray:
     return out
 
 
+def pair_exchange_streamed(Lbar: np.ndarray, keep: np.ndarray, ths: np.ndarray,
+                           workers: int = 1) -> np.ndarray:
+    """e_ij(w) of every pair i <= j and every walker, one pair at a time.
+
+    The same steps as pair_svds, truncate and pair_exchange: for pair n = [ij]
+    (the order of pair_svds) form Y^[ij] (eq. 2e_HRERI_RCAS), take its SVD,
+    keep its keep[n] largest singular values (Sec. 3.1.1) and return
+    e_ij(w) = (Ubar^T Theta_j(w)) . (Vbar Theta_i(w)) for every Theta(w) in
+    ths (W x M x N).  Only the pair values are kept, not every pair's factors
+    (about 8 GB at M = 440, N = 73).  workers > 1 maps the pairs over threads
+    (NumPy's LAPACK and BLAS calls release the GIL); the values do not depend
+    on it.  Returns an (n_pairs, W) complex array.
+    """
+    N = Lbar.shape[1]
+    pairs = [(i, j) for i in range(N) for j in range(i, N)]
+    if len(keep) != len(pairs):
+        raise ValueError("one kept rank per pair i <= j")
+    cols = np.ascontiguousarray(np.transpose(ths, (2, 1, 0)))  # [orbital][r][w]
+
+    def one(n):
+        i, j = pairs[n]
+        U, s, Vt = np.linalg.svd(pair_block(Lbar, i, j))
+        k = int(keep[n])
+        r = np.sqrt(s[:k])
+        a = (U[:, :k] * r[None, :]).T @ cols[j]
+        b = (r[:, None] * Vt[:k]) @ cols[i]
+        return np.sum(a * b, axis=0)
+
+    if workers <= 1:
+        rows = [one(n) for n in range(len(pairs))]
+    else:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(workers) as ex:
+            rows = list(ex.map(one, range(len(pairs))))
+    return np.array(rows, dtype=np.complex128).reshape(len(pairs), ths.shape[0])
+
+
 def exchange_lo(fac: PairFactors, th: np.ndarray, mask: Optional[np.ndarray] = None) -> complex:
     """sum_ij e_ij = sum_i e_ii + 2 sum_{i<j} e_ij (Y^[ji] = Y^[ij]T), one spin.
 

@@ -121,7 +121,7 @@ void check_ready(loaf_ctx* c, int W, const void* phi, int mode, int precision) {
     LOAF_REQUIRE(mode != LOAF_MODE_LO_JK || c->closed, LOAF_ERR_UNSUPPORTED,
                  "the compressed Coulomb (LO_JK) is defined for closed shells");
     LOAF_REQUIRE(precision == LOAF_PREC_FP64 || precision == LOAF_PREC_FP16X3 ||
-                     precision == LOAF_PREC_BF16X3,
+                     precision == LOAF_PREC_BF16X3 || precision == LOAF_PREC_FP16X3_F64INV,
                  LOAF_ERR_ARG, "unknown precision");
     LOAF_REQUIRE(mode == LOAF_MODE_FULL || c->compressed, LOAF_ERR_NOT_READY,
                  "LO mode needs lo_localize_compress");
@@ -197,6 +197,12 @@ loaf_status loaf_profile(loaf_ctx* c, int enable) {
 }
 
 int loaf_profile_count(const loaf_ctx* c) { return c ? (int)c->prof.size() : 0; }
+
+loaf_status loaf_test_withhold_stage(loaf_ctx* c, int n) {
+    if (!c || n < 0) return LOAF_ERR_ARG;
+    c->test_withhold = n;
+    return LOAF_OK;
+}
 
 loaf_status loaf_profile_get(const loaf_ctx* c, int idx, const char** name, double* total_ms,
                              long* calls, long* launches) {
@@ -520,6 +526,9 @@ struct MultiPlan {
     std::vector<void*> e, ld;
     std::vector<int*> st;
     int mode = 0, precision = 0;
+    // device allocations and frees seen when the graph was recorded: any later
+    // one may have moved a buffer the graph holds, and the graph is re-recorded
+    unsigned long long alloc_gen = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -636,7 +645,9 @@ loaf_status walkers_energy_multi(loaf_ctx* const* ctxs, int n, const int* W, con
     int flags[2] = {0, 0};
     loaf_status st = guarded(c0, [&] {
         LOAF_REQUIRE(mode == LOAF_MODE_LO, LOAF_ERR_UNSUPPORTED, "the multi-system launch runs the LO mode");
-        LOAF_REQUIRE(precision == LOAF_PREC_FP16X3 || precision == LOAF_PREC_BF16X3, LOAF_ERR_UNSUPPORTED,
+        LOAF_REQUIRE(precision == LOAF_PREC_FP16X3 || precision == LOAF_PREC_BF16X3 ||
+                         precision == LOAF_PREC_FP16X3_F64INV,
+                     LOAF_ERR_UNSUPPORTED,
                      "the multi-system launch runs the split-precision path");
         for (int k = 0; k < n; ++k) {
             loaf_ctx* c = ctxs[k];
@@ -664,9 +675,9 @@ loaf_status walkers_energy_multi(loaf_ctx* const* ctxs, int n, const int* W, con
                        q->screen_v[k] == ctxs[k]->screen_version && q->trial_v[k] == ctxs[k]->trial_version;
             if (same) { P = q; break; }
         }
-        if (!P) {
-            // first call of this signature: an eager pass on each context sets up
-            // its operands and workspace, then the graph is recorded
+        // an eager pass on each context sets up its operands and workspace, so
+        // that recording a graph allocates nothing and waits on nothing
+        auto eager_pass = [&] {
             for (int k = 0; k < n; ++k) {
                 loaf_ctx* c = ctxs[k];
                 check_ready(c, W[k], phi[k], mode, precision);
@@ -688,6 +699,23 @@ loaf_status walkers_energy_multi(loaf_ctx* const* ctxs, int n, const int* W, con
                 LOAF_CUDA(cudaStreamSynchronize(c->stream));
                 c->prof_on = prof;
             }
+        };
+        if (P && P->alloc_gen != devbuf_generation().load()) {
+            // a buffer of some context may have moved since the graph was
+            // recorded (another call grew a workspace, a setup call rebuilt the
+            // operands): record it again with the SM budgets already chosen
+            eager_pass();
+            std::vector<bool> prof(n);
+            for (int k = 0; k < n; ++k) { prof[k] = ctxs[k]->prof_on; ctxs[k]->prof_on = false; }
+            cudaGraphExec_t ex = capture_multi(*P, P->caps);
+            for (int k = 0; k < n; ++k) ctxs[k]->prof_on = prof[k];
+            cudaGraphExecDestroy(P->exec);
+            P->exec = ex;
+            P->alloc_gen = devbuf_generation().load();
+        }
+        if (!P) {
+            // first call of this signature: eager pass, then the graph is recorded
+            eager_pass();
             P = new MultiPlan;
             g_plans.push_back(P);
             P->ctxs.assign(ctxs, ctxs + n);
@@ -741,6 +769,7 @@ loaf_status walkers_energy_multi(loaf_ctx* const* ctxs, int n, const int* W, con
                 }
             }
             for (int k = 0; k < n; ++k) ctxs[k]->prof_on = prof[k];
+            P->alloc_gen = devbuf_generation().load();
         }
         LOAF_CUDA(cudaGraphLaunch(P->exec, P->stream));
         LOAF_CUDA(cudaStreamSynchronize(P->stream));
@@ -820,7 +849,7 @@ loaf_status walkers_propagator(loaf_ctx* c, int W, const void* x, int precision,
         LOAF_REQUIRE(W >= 1, LOAF_ERR_ARG, "W must be >= 1");
         LOAF_REQUIRE(x != nullptr && v_out != nullptr, LOAF_ERR_ARG, "x or v_out is NULL");
         LOAF_REQUIRE(precision == LOAF_PREC_FP64 || precision == LOAF_PREC_FP16X3 ||
-                         precision == LOAF_PREC_BF16X3,
+                         precision == LOAF_PREC_BF16X3 || precision == LOAF_PREC_FP16X3_F64INV,
                      LOAF_ERR_ARG, "unknown precision");
         const size_t xb = (size_t)W * c->X * sizeof(double2);
         const size_t vb = (size_t)W * c->M * c->M * sizeof(double2);

@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -69,11 +70,22 @@ struct Error {
 // device buffers owned by the context
 // ---------------------------------------------------------------------------
 
+// Number of device allocations and frees made through DevBuf in this process.
+// A recorded CUDA graph holds buffer addresses, so a graph is replayed only
+// while this count is the one it was recorded at.
+inline std::atomic<unsigned long long>& devbuf_generation() {
+    static std::atomic<unsigned long long> g{0};
+    return g;
+}
+
 struct DevBuf {
     void* ptr = nullptr;
     size_t bytes = 0;
     void release() {
-        if (ptr) cudaFree(ptr);
+        if (ptr) {
+            cudaFree(ptr);
+            devbuf_generation().fetch_add(1);
+        }
         ptr = nullptr;
         bytes = 0;
     }
@@ -82,6 +94,7 @@ struct DevBuf {
         if (nbytes <= bytes) return;
         release();
         LOAF_CUDA(cudaMalloc(&ptr, nbytes));
+        devbuf_generation().fetch_add(1);
         bytes = nbytes;
     }
     // as ensure, and zero-filled whenever it had to (re)allocate
@@ -304,6 +317,7 @@ struct loaf_ctx {
         w_part2, w_dhi, w_dlo, w_dscale, w_host_stage, w_cpart, w_lopart, w_red, w_flag, w_oz_at, w_oz_bs,
         w_oz_bt, w_oz_S, w_oz_int, w_oz_key, w_prop_x, w_prop_part;
     int trial_version = 0;  // bumped whenever a trial (canonical or localized) is loaded
+    int test_withhold = 0;  // LO kernel launches left that withhold a stage (failure-path tests)
 
     // per-stage CUDA-event timers (loaf_profile); stage kernels are bracketed
     // by events on the context stream while enabled

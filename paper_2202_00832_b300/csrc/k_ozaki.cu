@@ -635,64 +635,122 @@ __device__ inline float4 cdf_mul(float4 x, float4 y) {
 
 constexpr int kGJMaxCols = (LOAF_MAX_NOCC + 15) / 16;  // columns per thread of the 16 x 16 grid
 
+// Element arithmetic of the Gauss-Jordan kernel.  Both forms hold a complex
+// value in 16 bytes, so the shared-memory layout is the same.
+//   DFArith:  double-float float4 {re.hi, re.lo, im.hi, im.lo} on the FP32
+//             pipe (about 48 significant bits); pivot moduli from the leading parts
+//   F64Arith: double2 on the FP64 pipe (B300: about 1/64 of the FP32 rate)
+struct DFArith {
+    using T = float4;
+    using R = float;
+    __device__ static T from(double2 z) {
+        const dfl r = df_split_bits(z.x), i = df_split_bits(z.y);
+        return make_float4(r.hi, r.lo, i.hi, i.lo);
+    }
+    __device__ static R mag2(T a) { return fmaf(a.x, a.x, a.z * a.z); }
+    __device__ static double mag2d(T a) { return (double)a.x * a.x + (double)a.z * a.z; }
+    __device__ static bool finite(T a) { return isfinite(a.x) && isfinite(a.z); }
+    __device__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ static T sub_mul(T v, T f, T u) { return cdf_sub_mul(v, f, u); }
+    __device__ static T mul(T x, T y) { return cdf_mul(x, y); }
+    __device__ static T recip(T z) { return cdf_recip(z); }
+    __device__ static double2 to_d(T z) { return cdf_to(z); }
+    __device__ static R absmax(T z) { return fmaxf(fabsf(z.x), fabsf(z.z)); }
+    // round(z 2^sh) of both parts, from hi + lo (one more unit of rounding)
+    __device__ static void scaled(T z, int sh, long long& xr, long long& xi) {
+        xr = round_scaled_f(z.x, sh) + round_scaled_f(z.y, sh);
+        xi = round_scaled_f(z.z, sh) + round_scaled_f(z.w, sh);
+    }
+};
+struct F64Arith {
+    using T = double2;
+    using R = double;
+    __device__ static T from(double2 z) { return z; }
+    __device__ static R mag2(T a) { return fma(a.x, a.x, a.y * a.y); }
+    __device__ static double mag2d(T a) { return a.x * a.x + a.y * a.y; }
+    __device__ static bool finite(T a) { return isfinite(a.x) && isfinite(a.y); }
+    __device__ static T zero() { return make_double2(0.0, 0.0); }
+    __device__ static T sub_mul(T v, T f, T u) {  // v - f u
+        return make_double2(fma(f.y, u.y, fma(-f.x, u.x, v.x)), fma(-f.y, u.x, fma(-f.x, u.y, v.y)));
+    }
+    __device__ static T mul(T x, T y) { return cmul(x, y); }
+    __device__ static T recip(T z) { return cdiv(make_double2(1.0, 0.0), z); }
+    __device__ static double2 to_d(T z) { return z; }
+    __device__ static R absmax(T z) { return fmax(fabs(z.x), fabs(z.y)); }
+    __device__ static void scaled(T z, int sh, long long& xr, long long& xi) {
+        xr = round_scaled(z.x, sh);
+        xi = round_scaled(z.y, sh);
+    }
+};
+
 // Z = S^-1 of one walker and spin by Gauss-Jordan elimination with partial
-// pivoting in double-float arithmetic (pivot search on |.|^2 of the leading
-// parts, each pivot's reciprocal and the log-det in FP64).  Writes the log-det
+// pivoting in the arithmetic Ar (double-float: pivot search on |.|^2 of the
+// leading parts; the singularity test and the log-det in FP64 either way).  Writes the log-det
 // part, the status, the per-column exponents g_k and the digits of the real
 // block form of Z:
 //   Bt[s][w][2k + ro][2j + ri] = {Zr, -Zi, Zi, Zr}[ri][ro] (j, k) / 2^g_k,
 // the B operand of the Theta GEMM (Theta = [phi_re phi_im] B, column pairs).
 constexpr int kGJThreads = 256;  // update grid: 16 row groups x 16 column groups
 
-template <int MAXC>  // column slots per thread: ceil(N / 16)
+template <int MAXC, class Ar>  // column slots per thread: ceil(N / 16); element arithmetic
 __global__ void __launch_bounds__(kGJThreads)
-gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint16_t* __restrict__ Bt,
+gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S,
+                    const unsigned long long* __restrict__ phi_key, uint16_t* __restrict__ Bt,
                     int* __restrict__ col_exp, int* __restrict__ gmax, double2* __restrict__ ld_part,
                     int* __restrict__ st_part) {
     extern __shared__ __align__(16) unsigned char sm[];
-    float4* A = reinterpret_cast<float4*>(sm);    // N x N complex double-float
-    float4* colk = A + N * N;                     // N
-    float4* pivv = colk + N;                      // N pivots (double-float)
+    using T = typename Ar::T;
+    using R = typename Ar::R;
+    T* A = reinterpret_cast<T*>(sm);              // N x N complex
+    T* colk = A + N * N;                          // N
+    T* pivv = colk + N;                           // N pivots
     int* piv = reinterpret_cast<int*>(pivv + N);  // N
     int* gk = piv + N;                            // N
     __shared__ double red_v[32];
     __shared__ double2 red_c[32];
     __shared__ int s_p, s_flag, s_swaps;
     __shared__ double s_tol;
-    __shared__ float4 s_inv;
+    __shared__ T s_inv;
     const int w = blockIdx.x, tid = threadIdx.x;
     const int ti = tid >> 4, tj = tid & 15;  // 16 x 16 grid over the matrix
     double m = 0.0;
-    float mf = 0.f;
-    bool finite = true;
+    R mf = 0;
+    // a NaN or infinity anywhere in the walker's spin block (its largest |phi|
+    // key is that of a non-finite double) marks the walker; its digit slices,
+    // and so S, would otherwise be finite and meaningless
+    bool finite = phi_key[w] < 0x7ff0000000000000ull;
     for (int e = tid; e < N * N; e += blockDim.x) {
         const double2 z = S[(size_t)w * N * N + e];
-        const dfl zr = df_split_bits(z.x), zi = df_split_bits(z.y);
-        A[e] = make_float4(zr.hi, zr.lo, zi.hi, zi.lo);
-        mf = fmaxf(mf, fmaf(zr.hi, zr.hi, zi.hi * zi.hi));
-        finite = finite && isfinite(zr.hi) && isfinite(zi.hi);
+        const T a = Ar::from(z);
+        A[e] = a;
+        mf = max(mf, Ar::mag2(a));
+        finite = finite && Ar::finite(a);
     }
     m = block_max_d(finite ? (double)mf : (double)INFINITY, red_v);
     if (tid == 0) {
-        const double tol = (double)N * 2.220446049250313e-16 * sqrt(m);
+        // S comes from 42-bit digit slices of phi and Phi_T, and the digit
+        // products left out (s + t >= 8) add up to about M 2^-44 of the operand
+        // scale per entry (1.4e-11 measured on a 60-orbital case): a pivot below
+        // N 2^-36 max|S| is not distinguishable from zero and marks the walker
+        // singular
+        const double tol = (double)N * 1.4551915228366852e-11 * sqrt(m);
         s_tol = tol * tol;
         s_flag = (m == m && !isinf(m)) ? 0 : 2;
         s_swaps = 0;
     }
     __syncthreads();
-    __shared__ float4 s_akk;
+    __shared__ T s_akk;
     for (int k = 0; k < N && s_flag == 0; ++k) {
         // phase A (one warp): pivot row p of column k, 1/pivot, the old A[k][k]
         if (tid < 32) {
-            float best = -1.f;
+            R best = -1;
             int bi = k;
             for (int i = k + tid; i < N; i += 32) {
-                const float4 a = A[i * N + k];
-                const float v = a.x * a.x + a.z * a.z;
+                const R v = Ar::mag2(A[i * N + k]);
                 if (v > best) { best = v; bi = i; }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const R ov = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
             }
@@ -701,27 +759,27 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
                 piv[k] = bi;
                 if (bi != k) s_swaps += 1;
                 s_akk = A[k * N + k];
-                const float4 pv = A[bi * N + k];
-                // |pivot|^2 of the leading parts against the tolerance (FP64: no underflow)
-                if (!((double)pv.x * pv.x + (double)pv.z * pv.z > s_tol)) {
+                const T pv = A[bi * N + k];
+                // |pivot|^2 against the tolerance, in FP64 (no underflow)
+                if (!(Ar::mag2d(pv) > s_tol)) {
                     s_flag = 1;
                 } else {
                     pivv[k] = pv;
-                    s_inv = cdf_recip(pv);
+                    s_inv = Ar::recip(pv);
                 }
             }
         }
         __syncthreads();
         if (s_flag) break;
         const int p = s_p;
-        const float4 inv = s_inv;
+        const T inv = s_inv;
         // phase B: exchange rows k and p, scale the new row k (A[k][k] = 1/pivot),
         // and take column k of the other rows (row p's entry is the old A[k][k])
         for (int j = tid; j < N; j += blockDim.x) {
-            const float4 rk = A[k * N + j];
-            const float4 rp = p != k ? A[p * N + j] : rk;
+            const T rk = A[k * N + j];
+            const T rp = p != k ? A[p * N + j] : rk;
             if (p != k) A[p * N + j] = rk;
-            A[k * N + j] = j == k ? inv : cdf_mul(rp, inv);
+            A[k * N + j] = j == k ? inv : Ar::mul(rp, inv);
         }
         for (int i = tid; i < N; i += blockDim.x)
             if (i != k) colk[i] = i == p ? s_akk : A[i * N + k];
@@ -729,23 +787,23 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
         // phase C: other rows, A[i][j] -= A[i][k] (old) * A[k][j] (new); A[i][k]
         // starts from 0.  Each thread's columns are loaded, updated and stored
         // as a group so that their independent error-free chains interleave.
-        float4 u[MAXC];
+        T u[MAXC];
 #pragma unroll
         for (int q = 0; q < MAXC; ++q) {
             const int j = tj + 16 * q;
-            u[q] = j < N ? A[k * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            u[q] = j < N ? A[k * N + j] : Ar::zero();
         }
         for (int i = ti; i < N; i += kGJThreads / 16) {
             if (i == k) continue;
-            const float4 f = colk[i];
-            float4 v[MAXC];
+            const T f = colk[i];
+            T v[MAXC];
 #pragma unroll
             for (int q = 0; q < MAXC; ++q) {
                 const int j = tj + 16 * q;
-                v[q] = (j < N && j != k) ? A[i * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                v[q] = (j < N && j != k) ? A[i * N + j] : Ar::zero();
             }
 #pragma unroll
-            for (int q = 0; q < MAXC; ++q) v[q] = cdf_sub_mul(v[q], f, u[q]);
+            for (int q = 0; q < MAXC; ++q) v[q] = Ar::sub_mul(v[q], f, u[q]);
 #pragma unroll
             for (int q = 0; q < MAXC; ++q) {
                 const int j = tj + 16 * q;
@@ -762,7 +820,7 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
             const int p = piv[k];
             if (p != k)
                 for (int i = tid; i < N; i += blockDim.x) {
-                    const float4 t = A[i * N + k];
+                    const T t = A[i * N + k];
                     A[i * N + k] = A[i * N + p];
                     A[i * N + p] = t;
                 }
@@ -773,7 +831,7 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
     double2 lp = make_double2(0.0, 0.0);
     if (flag == 0)
         for (int k = tid; k < N; k += blockDim.x) {
-            const double2 d = cdf_to(pivv[k]);
+            const double2 d = Ar::to_d(pivv[k]);
             lp.x += log(hypot(d.x, d.y));
             lp.y += atan2(d.y, d.x);
         }
@@ -798,13 +856,10 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
     // per-column exponents of Z (one warp per column)
     const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     for (int k = wid; k < N; k += nw) {
-        float mm = 0.f;  // leading parts: |z| <= |hi| (1 + 2^-23), within the 2-bit headroom
+        R mm = 0;  // double-float: leading parts, |z| <= |hi| (1 + 2^-23), within the 2-bit headroom
         if (flag == 0)
-            for (int j = lane; j < N; j += 32) {
-                const float4 z = A[j * N + k];
-                mm = fmaxf(mm, fmaxf(fabsf(z.x), fabsf(z.z)));
-            }
-        for (int o = 16; o > 0; o >>= 1) mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+            for (int j = lane; j < N; j += 32) mm = max(mm, Ar::absmax(A[j * N + k]));
+        for (int o = 16; o > 0; o >>= 1) mm = max(mm, __shfl_xor_sync(0xffffffffu, mm, o));
         if (lane == 0) {
             const int g = slice_exponent((double)mm);
             gk[k] = g;
@@ -825,11 +880,8 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S, uint1
         const int k = cc >> 1, ro = cc & 1;
         long long X0 = 0, X1 = 0;
         if (flag == 0) {
-            // digits of hi + lo from the two parts (one more unit of rounding)
-            const float4 z = A[j * N + k];
-            const int sh = 42 - gk[k];
-            const long long xr = round_scaled_f(z.x, sh) + round_scaled_f(z.y, sh);
-            const long long xi = round_scaled_f(z.z, sh) + round_scaled_f(z.w, sh);
+            long long xr, xi;
+            Ar::scaled(A[j * N + k], 42 - gk[k], xr, xi);
             X0 = ro ? xi : xr;   // ri = 0: Zr (ro = 0) or Zi (ro = 1)
             X1 = ro ? xr : -xi;  // ri = 1: -Zi (ro = 0) or Zr (ro = 1)
         }
@@ -959,7 +1011,8 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
             LOAF_LAUNCH_CHECK();
         }
         {
-            StageScope sc(c, "inverse_df", 1);
+            const bool f64 = precision == LOAF_PREC_FP16X3_F64INV;
+            StageScope sc(c, f64 ? "inverse_f64" : "inverse_df", 1);
             const size_t smem = (size_t)N * N * sizeof(double2) + (size_t)2 * N * sizeof(double2) +
                                 2 * N * sizeof(int) + 16;
             // as many column slots per thread as N needs: empty slots would still
@@ -967,16 +1020,28 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
             auto launch = [&](auto kern) {
                 LOAF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 kern<<<W, kGJThreads, smem, c->stream>>>(
-                    N, kpad, W, c->w_oz_S.as<double2>(), Bt + bt_spin * s, cexp(s), gmx(s),
+                    N, kpad, W, c->w_oz_S.as<double2>(), c->w_oz_key.as<unsigned long long>(),
+                    Bt + bt_spin * s, cexp(s), gmx(s),
                     c->w_logdet.as<double2>() + (size_t)s * W, c->w_status.as<int>() + (size_t)s * W);
             };
-            switch (ceil_div(N, 16)) {
-                case 1: launch(gauss_jordan_kernel<1>); break;
-                case 2: launch(gauss_jordan_kernel<2>); break;
-                case 3: launch(gauss_jordan_kernel<3>); break;
-                case 4: launch(gauss_jordan_kernel<4>); break;
-                case 5: launch(gauss_jordan_kernel<5>); break;
-                default: launch(gauss_jordan_kernel<kGJMaxCols>); break;
+            if (f64) {
+                switch (ceil_div(N, 16)) {
+                    case 1: launch(gauss_jordan_kernel<1, F64Arith>); break;
+                    case 2: launch(gauss_jordan_kernel<2, F64Arith>); break;
+                    case 3: launch(gauss_jordan_kernel<3, F64Arith>); break;
+                    case 4: launch(gauss_jordan_kernel<4, F64Arith>); break;
+                    case 5: launch(gauss_jordan_kernel<5, F64Arith>); break;
+                    default: launch(gauss_jordan_kernel<kGJMaxCols, F64Arith>); break;
+                }
+            } else {
+                switch (ceil_div(N, 16)) {
+                    case 1: launch(gauss_jordan_kernel<1, DFArith>); break;
+                    case 2: launch(gauss_jordan_kernel<2, DFArith>); break;
+                    case 3: launch(gauss_jordan_kernel<3, DFArith>); break;
+                    case 4: launch(gauss_jordan_kernel<4, DFArith>); break;
+                    case 5: launch(gauss_jordan_kernel<5, DFArith>); break;
+                    default: launch(gauss_jordan_kernel<kGJMaxCols, DFArith>); break;
+                }
             }
             LOAF_LAUNCH_CHECK();
         }

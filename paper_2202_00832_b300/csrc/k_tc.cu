@@ -736,6 +736,9 @@ struct LoParams {
     int n_pt, n_wt, W, ldp, nk;
     uint32_t idesc;
     int* err;
+    // failure-path test hook: the even CTA of the first CTA pair leaves the
+    // first stage of its first unit unfilled, so that its waits run out
+    int withhold;
 };
 
 // ---- LO exchange kernel: one CTA pair per (rank chunk of a pair, 128 walkers) ----
@@ -818,6 +821,12 @@ lo_exchange_tc_kernel(LoParams P) {
             const uint32_t wbytes = (uint32_t)(t.y >> 16) * 128u;  // H weight rows of 128 bytes
             for (int h = 0; h < 2 * P.nk; ++h) {
                 if (!tc::mbar_wait_cluster(&sh.empty[s], ph ^ 1, abort)) break;
+                if (P.withhold && cid == 0 && even && u == cid && h == 0) {
+                    // no arrival and no copy: the MMA issuer's wait on this stage
+                    // (and every wait behind it) runs out after the wait limit
+                    if (++s == kLSlots) { s = 0; ph ^= 1; }
+                    continue;
+                }
                 uint8_t* st = base + s * kLSlotBytes;
                 tc::mbar_arrive_expect_tx(&sh.full[s], 2 * wbytes + 2 * kLTileBh);
                 const int kb = h >> 1;
@@ -1678,6 +1687,11 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             P.nk = dg.nkb;
             P.idesc = idesc;
             P.err = err;
+            P.withhold = 0;
+            if (c->test_withhold > 0) {
+                P.withhold = 1;
+                --c->test_withhold;
+            }
             c->w_lopart.ensure((size_t)ntiles * Wpad * sizeof(double2));
             P.part = c->w_lopart.as<double2>();
             const int units = (ntiles / 2) * n_wt;

@@ -84,6 +84,7 @@ theta_fp64_kernel(int M, int N, int ntot, const double* __restrict__ trial,
     }
     __syncthreads();
     double local_max = 0.0;
+    bool local_finite = true;
 #pragma unroll
     for (int a = 0; a < NI; ++a)
 #pragma unroll
@@ -92,20 +93,22 @@ theta_fp64_kernel(int M, int N, int ntot, const double* __restrict__ trial,
             if (i < N && j < N) {
                 A[i * N + j] = acc[a][b];
                 local_max = fmax(local_max, mag2(acc[a][b]));
+                local_finite = local_finite && isfinite(acc[a][b].x) && isfinite(acc[a][b].y);
             }
         }
-    // block max of |S|^2 (singularity tolerance)
+    // block max of |S|^2 (singularity tolerance); fmax passes over a NaN, so
+    // finiteness is reduced on its own
     for (int o = 16; o > 0; o >>= 1) local_max = fmax(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
     if ((tid & 31) == 0) red_v[tid >> 5] = local_max;
     if (tid == 0) { s_flag = 0; s_swaps = 0; }
-    __syncthreads();
+    const int all_finite = __syncthreads_and(local_finite);
     if (tid == 0) {
         double m = 0.0;
         for (int k = 0; k < kThreads / 32; ++k) m = fmax(m, red_v[k]);
         // pivots below N * 2^-52 * max|S| count as zero
         const double tol = (double)N * 2.220446049250313e-16 * sqrt(m);
         s_tol = tol * tol;
-        if (!(m == m) || isinf(m)) s_flag = 2;  // non-finite input
+        if (!all_finite || !(m == m) || isinf(m)) s_flag = 2;  // non-finite input
     }
     for (int k = tid; k < N; k += kThreads) perm[k] = k;
     __syncthreads();

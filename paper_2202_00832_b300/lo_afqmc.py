@@ -19,8 +19,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblo_afqmc.so")
 
 MODE_FULL, MODE_LO, MODE_LO_JK = 0, 1, 2
-PREC_FP64, PREC_FP16X3, PREC_BF16X3 = 0, 1, 2
-PRECISIONS = {"fp64": PREC_FP64, "fp16x3": PREC_FP16X3, "bf16x3": PREC_BF16X3}
+PREC_FP64, PREC_FP16X3, PREC_BF16X3, PREC_FP16X3_F64INV = 0, 1, 2, 3
+PRECISIONS = {"fp64": PREC_FP64, "fp16x3": PREC_FP16X3, "bf16x3": PREC_BF16X3,
+              "fp16x3_f64inv": PREC_FP16X3_F64INV}
 MODES = {"full": MODE_FULL, "lo": MODE_LO, "lo_jk": MODE_LO_JK}
 
 STATUS = {0: "LOAF_OK", 1: "LOAF_ERR_ARG", 2: "LOAF_ERR_SHAPE", 3: "LOAF_ERR_CUDA",
@@ -53,6 +54,7 @@ SIGNATURES = [
     ("pair_screen_set", _I, [_P, _D, _P]),
     ("pair_screen_query", _I, [_P, _P, _P, _P, _P, _P]),
     ("mlp_loss_grad", _I, [_I, _I, _P, _P, _P, _P, _P]),
+    ("loaf_test_withhold_stage", _I, [_P, _I]),
     ("loaf_profile", _I, [_P, _I]),
     ("loaf_profile_count", _I, [_P]),
     ("loaf_profile_get", _I, [_P, _I, ctypes.POINTER(ctypes.c_char_p),
@@ -203,6 +205,11 @@ class Context:
     @property
     def ntot(self) -> int:
         return self.n_alpha if self.closed else self.n_alpha + self.n_beta
+
+    def test_withhold_stage(self, n: int = 1):
+        """Failure-path test hook: the next n LO tensor-core launches leave one
+        pipeline stage unfilled, so their bounded waits run out (LOAF_ERR_TIMEOUT)."""
+        self._check(self._lib.loaf_test_withhold_stage(self._h, int(n)), "loaf_test_withhold_stage")
 
     # -- stage timers ---------------------------------------------------------
     def profile(self, enable: bool = True):

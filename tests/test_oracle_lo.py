@@ -163,3 +163,26 @@ def test_open_shell_lo_threshold_zero():
         full = E.walker_energy(mol, walk[w])
         got = lo.energy_lo(mol, spins, walk[w])
         assert rel(got["E"], full["E"]) < 1e-10
+
+
+@pytest.mark.parametrize("threshold", [0.0, 1e-2])
+def test_streamed_pair_values(chain_lo, threshold):
+    """The pair-at-a-time form (used where every pair's factors would not fit in
+    host memory) gives the stored-factor pair values; at full rank its weighted
+    sum is the exchange of the Cholesky form (eq. 2e_HRchol_RCAS), which uses no
+    SVD at all."""
+    mol, walk, spins0 = chain_lo
+    sp = spins0[0]
+    fac = lo.truncate(sp.svds, threshold)
+    ths = np.array([E.theta(sp.trial_loc, walk[w]) for w in range(3)])
+    for workers in (1, 3):
+        got = lo.pair_exchange_streamed(sp.Lbar, fac.m_svd, ths, workers=workers)
+        for w in range(3):
+            ref = lo.pair_exchange(fac, ths[w])
+            assert np.abs(got[:, w] - ref).max() < 1e-11 * np.abs(ref).max()
+    if threshold == 0.0:
+        wts = np.array([1.0 if i == j else 2.0 for i, j in fac.pairs])
+        for w in range(3):
+            ek = 2.0 * 0.5 * np.sum(wts * got[:, w])  # both spins of the closed shell
+            ref = E.walker_energy(mol, walk[w])["EK"]
+            assert rel(ek, ref) < 1e-11
