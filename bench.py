@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--workload", default="pentacene", choices=sorted(WORKLOADS),
                     help="pentacene (the benchmark) or a smaller system for profiling")
     ap.add_argument("--threshold", type=float, default=1e-4)
-    ap.add_argument("--precision", default="fp16x3", choices=["fp16x3", "bf16x3", "fp64"])
+    ap.add_argument("--precision", default="fp16x3",
+                    choices=["fp16x3", "fp16x3_f64inv", "bf16x3", "fp64"])
     ap.add_argument("--cpu-sample", type=int, default=3, help="walkers timed on the oracle")
     ap.add_argument("--full-sample", type=int, default=64, help="walkers of the FP64 full GPU leg")
     ap.add_argument("--no-extras", action="store_true", help="skip accuracy / FP64 / CPU legs")
@@ -347,12 +348,16 @@ def run_ours(args, rank, world, local):
     fp64_peak_tflops = 1.25  # nominal B300 FP64 (2 DFMA / clk / SM class figure)
 
     def tc_roof(name, flops):
+        # the kernel runs for a few ms of each step at the maximum SM clock, so the
+        # measured burst rate is its peak (the sustained figure was taken at a
+        # power-capped clock)
         t = per_launch_ms[name] / 1e3
         ach = flops / t / 1e12
-        pk = peaks["bf16_tflops_sustained"]
+        pk = peaks["bf16_tflops"]
         return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                 "frac": ach / pk, "traffic": None,
-                "peak_source": f"{peaks['source']} bf16 sustained (fp16 same rate)"}
+                "peak_source": f"{peaks['source']} bf16 burst (fp16 same rate); of measured",
+                "frac_of_sustained": ach / peaks["bf16_tflops_sustained"]}
 
     rooflines = {}
     if "lo_exchange_tc" in per_launch_ms:
@@ -375,6 +380,15 @@ def run_ours(args, rank, world, local):
                                    "achieved": ach, "peak": pk, "unit": "T FP32 lane-ops/s",
                                    "frac": ach / pk, "traffic": None,
                                    "peak_source": "148 SMs x 128 FP32 lanes x 2.032 GHz"}
+    if "inverse_f64" in per_launch_ms:
+        # FP64 Gauss-Jordan: N^3 complex multiply-adds (8 flops) per walker and spin
+        t = per_launch_ms["inverse_f64"] / 1e3
+        n3 = N ** 3 if mol.closed_shell else mol.n_alpha ** 3 + mol.n_beta ** 3
+        ach = 8.0 * n3 * W / t / 1e12
+        rooflines["inverse_f64"] = {"kernel": "gauss_jordan (FP64)", "bound": "alu", "achieved": ach,
+                                    "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                                    "frac": ach / fp64_peak_tflops, "traffic": None,
+                                    "peak_source": "nominal FP64 ALU peak of B300"}
     if "theta_fp64" in per_launch_ms:
         t = per_launch_ms["theta_fp64"] / 1e3
         ach = theta_flops / t / 1e12
@@ -387,21 +401,59 @@ def run_ours(args, rank, world, local):
     extras = {}
     cpu = None
     if not args.no_extras:
-        # accuracy against the FP64 oracle and against the FP64 GPU LO path
+        # accuracy of every walker of the batch against the FP64 LO path on the GPU
+        # (same factors), and of a few walkers against the FP64 oracle's full energy
+        e_mixed = e_d.cpu().numpy()
+        e64_d = torch.zeros_like(e_d)
+        ctx.walkers_energy(phi_d, mode="lo", precision="fp64", e_out=e64_d)
+        torch.cuda.synchronize()
+        e_lo64 = e64_d.cpu().numpy()
+        dev = np.abs(e_mixed - e_lo64)
         n_acc = max(1, args.cpu_sample)
-        e_mixed = e_d[:n_acc].cpu().numpy()
-        sub = walk[:n_acc]
-        e_lo64, _, _ = ctx.walkers_energy(sub, mode="lo", precision="fp64")
-        ref, dt = time_oracle(mol, sub)
+        ref, dt = time_oracle(mol, walk[:n_acc])
         extras["accuracy_mha"] = {
-            "walkers": n_acc,
-            "mixed_vs_fp64_lo_max": float(np.abs(e_mixed - e_lo64).max() * 1e3),
-            "mixed_vs_oracle_full_max": float(np.abs(e_mixed - ref).max() * 1e3),
-            "lo_truncation_vs_oracle_full_max": float(np.abs(e_lo64 - ref).max() * 1e3),
+            "walkers": W,
+            "mixed_vs_fp64_lo_max": float(dev.max() * 1e3),
+            "mixed_vs_fp64_lo_mean": float(dev.mean() * 1e3),
+            "oracle_walkers": n_acc,
+            "mixed_vs_oracle_full_max": float(np.abs(e_mixed[:n_acc] - ref).max() * 1e3),
+            "lo_truncation_vs_oracle_full_max": float(np.abs(e_lo64[:n_acc] - ref).max() * 1e3),
         }
         cpu = {"value": n_acc / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                "sample": f"{n_acc} walkers of the workload through the FP64 oracle "
                          f"(exact Cholesky form, {dt:.1f} s)"}
+        # precision variants of the same step: the overlap inverse and log-det on
+        # the FP64 pipe (FP16X3_F64INV), and BF16 hi + lo operands (BF16X3)
+        if args.precision == "fp16x3":
+            variants = {}
+            for prec in ("fp16x3_f64inv", "bf16x3"):
+                ev = torch.zeros_like(e_d)
+                ldv = torch.zeros_like(e_d)
+                for _ in range(2):
+                    ctx.walkers_energy(phi_d, mode="lo", precision=prec, e_out=ev, logdet_out=ldv)
+                ctx.profile(True)
+                torch.cuda.synchronize()
+                v0 = torch.cuda.Event(enable_timing=True)
+                v1 = torch.cuda.Event(enable_timing=True)
+                v0.record(stream)
+                for _ in range(args.steps):
+                    ctx.walkers_energy(phi_d, mode="lo", precision=prec, e_out=ev, logdet_out=ldv)
+                v1.record(stream)
+                torch.cuda.synchronize()
+                vprof = ctx.profile_read()
+                ctx.profile(False)
+                vms = v0.elapsed_time(v1) / args.steps
+                dv = np.abs(ev.cpu().numpy() - e_lo64)
+                dld = np.abs(ldv.cpu().numpy().real - ld_d.cpu().numpy().real)
+                variants[prec] = {
+                    "value": W / (vms / 1e3), "unit": UNIT, "ms_per_step": vms,
+                    "vs_fp64_lo_max_mha": float(dv.max() * 1e3),
+                    "vs_fp64_lo_mean_mha": float(dv.mean() * 1e3),
+                    "logdet_vs_fp16x3_max": float(dld.max()),
+                    "stage_ms_per_step": {k: v[0] / args.steps for k, v in vprof.items()
+                                          if k.startswith("inverse")},
+                }
+            extras["precision_variants"] = variants
         # the plain full-exchange FP64 path on the same GPU (subset of walkers)
         nf = min(args.full_sample, W)
         phi_f = phi_d[:nf].contiguous()
@@ -420,8 +472,9 @@ def run_ours(args, rank, world, local):
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": f"{args.precision}: 16-bit hi+lo x3 tcgen05 contractions (fp32 acc); overlap and "
-                 f"Theta as exact 7-bit slice products on tcgen05; double-float (2 x f32) inverse and "
-                 f"log-det; f64 reductions"
+                 f"Theta as exact 7-bit slice products on tcgen05; "
+                 + ("f64" if args.precision == "fp16x3_f64inv" else "double-float (2 x f32)")
+                 + " inverse and log-det; f64 reductions"
                  if args.precision != "fp64" else "f64",
         "data": "synthetic",
         "config": {"workload": wl.name + (" (pentacene-scale acene ribbon)" if wl is synth.PENTACENE_440

@@ -261,7 +261,8 @@ loaf_status loaf_destroy(loaf_ctx* c) {
                             &c->w_status, &c->w_out, &c->w_part, &c->w_part2, &c->w_dhi,
                             &c->w_dlo, &c->w_dscale, &c->w_host_stage, &c->w_cpart,
                             &c->w_lopart, &c->w_red, &c->w_flag, &c->d_keep, &c->w_oz_at, &c->w_oz_bs,
-                            &c->w_oz_bt, &c->w_oz_S, &c->w_oz_int, &c->w_oz_key, &c->w_prop_x, &c->w_prop_part})
+                            &c->w_oz_bt, &c->w_oz_S, &c->w_oz_int, &c->w_oz_key, &c->w_prop_x, &c->w_prop_part,
+                            &c->w_dfull})
         b->release();
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     for (cudaEvent_t e : {c->ev_start, c->ev_copied[0], c->ev_copied[1], c->ev_free[0], c->ev_free[1]})
@@ -372,7 +373,8 @@ void energy_batch(loaf_ctx* c, int W, const double2* dphi, int mode, int precisi
     // path and the full mode use the FP64 Theta kernel
     const bool tc_theta = precision != LOAF_PREC_FP64 && mode != LOAF_MODE_FULL;
     if (tc_theta) {
-        run_theta_tc(c, W, dphi, precision);
+        // the LO operands first: the dense blocks need an FP32 copy of Delta
+        run_theta_tc(c, W, dphi, precision, prepare_lo_operands(c, mode, precision));
     } else {
         StageScope sc(c, "theta_fp64", c->nspin);
         stage_theta(c, W, dphi);
@@ -936,7 +938,7 @@ loaf_status walkers_pair_exchange(loaf_ctx* c, int W, const void* phi, int preci
             stage_theta(c, W, dphi);
             run_energy_fp64_lo(c, W, c->w_theta.as<double2>(), nullptr, c->w_part.as<double2>());
         } else {
-            run_theta_tc(c, W, dphi, precision);
+            run_theta_tc(c, W, dphi, precision, prepare_lo_operands(c, LOAF_MODE_LO, precision));
             run_energy_mixed(c, W, LOAF_MODE_LO, precision, nullptr, nullptr,
                              c->w_part.as<double2>());
         }

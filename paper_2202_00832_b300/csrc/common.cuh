@@ -237,6 +237,19 @@ struct MixedOps {
     DevBuf s_pt, s_pt0, s_npt, s_pw;
     int s_n_pt = 0, screen_built = -1;
     double s_EK0 = 0.0;
+    // rank-adaptive plan (mode LO): pairs whose dense truncated block Ytil =
+    // Ubar Vbar costs fewer MMA columns than the two factor sides are contracted
+    // densely; their half-tiles (B rows: Ytil rows s, then g = Vbar^T p) come
+    // first in pair_pt0.  lo_dense_ok records which plan the LO operands hold.
+    bool lo_dense_ok = false;
+    int n_dpt = 0;             // dense half-tiles
+    int Sd = 0;                // s-extent of the FP32 Delta copy the dense kernel reads
+    DevBuf dpt, Yb_hi, Yb_lo;  // dense half-tile list {row0, nvalid | H << 16, ci << 24 | cj << 16 | s0, offset}, B tiles
+    DevBuf rowc_d;             // per dense row {1 / row scale, h = (Ubar q)[s]} (float2)
+    std::vector<int4> h_dtiles;
+    std::vector<unsigned char> h_dense;  // per pair: contracted densely
+    DevBuf s_dpt;
+    int s_n_dpt = 0;
     // compressed Coulomb (closed shell): the same tiles with the pair's
     // orbitals swapped, row constants {inv_su, inv_sv, U.Phi_i, V.Phi_j},
     // per-pair trial parts, weights 2 (1 or 2) and their trial sum
@@ -250,12 +263,14 @@ struct MixedOps {
         for (DevBuf* b : {&L_hi, &L_lo, &L_inv, &J0, &U_hi, &U_lo, &V_hi, &V_lo, &row_c, &pt,
                           &pair_pt0, &pair_npt, &pair_w, &e0, &s_pt, &s_pt0, &s_npt, &s_pw,
                           &Lb_hi, &Lb_lo, &Ub_hi, &Ub_lo, &Vb_hi, &Vb_lo, &pt_J, &row_cJ, &e0_J, &pw_J,
-                          &Lt_hi, &Lt_lo, &Lt_inv})
+                          &Lt_hi, &Lt_lo, &Lt_inv, &dpt, &Yb_hi, &Yb_lo, &rowc_d, &s_dpt})
             b->release();
         coul_ready = lo_ready = prop_ready = false;
         screen_built = -1;
         h_tiles.clear(); h_pt0.clear(); h_npt.clear(); h_order.clear(); h_pw.clear(); h_e0.clear();
-        n_pt = n_pairs = 0;
+        h_dtiles.clear(); h_dense.clear();
+        n_pt = n_dpt = n_pairs = s_n_pt = s_n_dpt = 0;
+        Sd = 0;
         R = 0;
     }
 };
@@ -316,6 +331,10 @@ struct loaf_ctx {
     loaf::DevBuf w_phi, w_theta, w_z, w_lu, w_perm, w_logdet, w_status, w_out, w_part,
         w_part2, w_dhi, w_dlo, w_dscale, w_host_stage, w_cpart, w_lopart, w_red, w_flag, w_oz_at, w_oz_bs,
         w_oz_bt, w_oz_S, w_oz_int, w_oz_key, w_prop_x, w_prop_part;
+    // FP32 copy of the scaled Delta for the dense LO epilogue, [c][rb][128][Sd];
+    // zeroed whenever its geometry changes (the columns past M stay zero)
+    loaf::DevBuf w_dfull;
+    long dfull_key = -1;
     int trial_version = 0;  // bumped whenever a trial (canonical or localized) is loaded
     int test_withhold = 0;  // LO kernel launches left that withhold a stage (failure-path tests)
 
@@ -397,7 +416,12 @@ void run_energy_cas(loaf_ctx* c, int W, int N, const double2* phi, int n_det, co
 void run_force_bias_mixed(loaf_ctx* c, int W, int precision, double2* e_scratch, double2* j_out);
 void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2* theta,
                       double2* e_out, double2* e_pairs);
-void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision);
+// Sd > 0: also write the FP32 copy of the scaled Delta (s-extent Sd) for the
+// dense LO kernel
+void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision, int Sd = 0);
+// LO operands of the mode (LO: rank-adaptive, LO_JK: factored); returns the
+// s-extent of the FP32 Delta copy the dense kernel reads (0: no dense pair)
+int prepare_lo_operands(loaf_ctx* c, int mode, int precision);
 void setup_load(loaf_ctx* c, int M, int X, const double* h, const double* L, int na, int nb,
                 const double* ta, const double* tb, double e0, int on_device);
 void setup_compress(loaf_ctx* c, double t_svd, const double* r_ops, int n_ops, int localize,

@@ -340,6 +340,8 @@ struct OzParams {
     uint16_t* dhi;
     uint16_t* dlo;
     int bf16;
+    float* dfull;         // mode 1, optional: FP32 Delta t as [c][rb][128 rows z][Sd] (dense LO epilogue)
+    int Sd;
 };
 
 struct OzShared {
@@ -379,6 +381,10 @@ __device__ inline void store_delta(const OzParams& P, int w, int r, int cc, long
     const size_t o = delta_elem(2 * w + ro, P.col0 + k, r, P.nrb, P.nkb);
     P.dhi[o] = h;
     P.dlo[o] = l;
+    if (P.dfull) {
+        const int z = 2 * w + ro;
+        P.dfull[(((size_t)(P.col0 + k) * P.nrb + (z >> 7)) * 128 + (z & 127)) * P.Sd + r] = f;
+    }
 }
 
 constexpr int kOEpiWarps = 16;  // four per TMEM lane quarter, 8-column chunks h, h + 4, h + 8
@@ -914,7 +920,7 @@ __global__ void delta_scale_kernel(int W, int nspin, const int* __restrict__ wex
 
 }  // namespace
 
-void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
+void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision, int Sd) {
     const int M = c->M;
     const int p_pad = (M + 15) / 16 * 16;  // 32-byte rows: whole L2 sectors
     const int r_pad = p_pad;
@@ -933,6 +939,17 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
     const DeltaGeom dg = delta_geom(M, c->ntot, W);
     c->w_dhi.ensure_zeroed(dg.plane * 2, c->stream);
     c->w_dlo.ensure_zeroed(dg.plane * 2, c->stream);
+    if (Sd > 0) {
+        // the FP32 copy for the dense LO epilogue: zero wherever the Theta stage
+        // does not write (basis columns past M, walker rows past W)
+        const size_t n = (size_t)c->ntot * dg.nrb * 128 * Sd;
+        const long key = (((long)Sd * 2048 + c->M) * 65536 + dg.nrb) * 256 + c->ntot;
+        if (c->w_dfull.bytes < n * sizeof(float) || c->dfull_key != key) {
+            c->w_dfull.ensure(n * sizeof(float));
+            LOAF_CUDA(cudaMemsetAsync(c->w_dfull.ptr, 0, n * sizeof(float), c->stream));
+            c->dfull_key = key;
+        }
+    }
     c->w_dscale.ensure((size_t)W * (sizeof(float) + sizeof(double)) + 64);
     float* inv_t = c->w_dscale.as<float>();
     double* tscale =
@@ -1078,6 +1095,8 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision) {
         P.dhi = c->w_dhi.as<uint16_t>();
         P.dlo = c->w_dlo.as<uint16_t>();
         P.bf16 = bf16 ? 1 : 0;
+        P.dfull = Sd > 0 ? c->w_dfull.as<float>() : nullptr;
+        P.Sd = Sd;
         const int units = P.n_rt * P.n_ct * P.n_b;
         ozaki_gemm_kernel<<<std::min(units, c->persistent_grid()), kOThreads, kOSmem, c->stream>>>(mA, mB, P);
         LOAF_LAUNCH_CHECK();

@@ -1009,6 +1009,281 @@ lo_exchange_tc_kernel(LoParams P) {
     if (threadIdx.x == 0 && sh.abort) atomicExch(P.err, 1);
 }
 
+// ---- LO exchange through dense truncated blocks ----
+// For a pair [ij] whose kept rank K is above about M / 2, the truncated block
+// Ytil = Ubar Vbar (M x M) costs M^2 multiply-adds per walker against 2 M K
+// through its factors, and gives the same pair value (eq. 2e_HR_RCAS_LO read
+// right to left):  e_ij = Theta_j^T Ytil Theta_i.  With Theta = Phi_T + Delta,
+//   e_ij = e0 + g . Delta_i + Delta_j . (Ytil Delta_i + h),
+//   g = Ytil^T Phi_j = Vbar^T p,  h = Ytil Phi_i = Ubar q,  e0 = p . q,
+// all walker-independent parts in FP64 at setup.  B operand: the rows s of
+// Ytil followed by g (M + 1 rows, in balanced chunks of at most 256, two
+// half-tiles per chunk as in the factored kernel); A operand: the Delta_i rows
+// of 128 walkers (M = 256 over the CTA pair); K = the basis.  The accumulator
+// Z[z][s] = (Ytil Delta_i)[s] (row g: g . Delta_i) sits in one of two TMEM
+// buffers of 256 columns, so the epilogue of one unit runs under the MMAs of
+// the next.  The epilogue reads Delta_j[w][s] in FP32 from the walker-row-major
+// copy the Theta stage writes and sums the complex products along its columns.
+struct LoDenseParams {
+    const uint16_t* y_hi;  // B half-tiles [tile][kb]
+    const uint16_t* y_lo;
+    const uint16_t* d_hi;  // Delta tiles [c][rb][kb]
+    const uint16_t* d_lo;
+    const float* dfull;    // Delta t: [c][rb][128 rows z][Sd] FP32
+    int nrb, Sd;
+    const int4* pt;        // half-tiles {row0, nvalid | H << 16, ci << 24 | cj << 16 | s0, element offset}
+    const float2* rowc;    // per dense row {1 / row scale, h}
+    const float* inv_t;    // per walker 1 / t
+    double2* part;         // [chunk][ldp]
+    int n_pt, n_wt, W, ldp, nk, M;
+    uint32_t idesc;
+    int* err;
+    int withhold;          // failure-path test hook, as in the factored kernel
+};
+
+struct LoDenseShared {
+    uint64_t full[kLSlots];     // even CTA: own bytes + the odd CTA's forward
+    uint64_t empty[kLSlots];    // both: the pair MMA's commit (multicast)
+    uint64_t tmem_full[2];      // both: the pair MMA's commit (multicast)
+    uint64_t tmem_empty[2];     // even CTA: 16 local + 16 remote epilogue warps
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+    float red[4][kBM];          // per column group: sum over its columns, per walker row
+    float2 cst[kBN];            // per column of the chunk: {1 / row scale, h}
+};
+
+__global__ void __launch_bounds__(kLThreads, 1)
+lo_dense_tc_kernel(LoDenseParams P) {
+    extern __shared__ uint8_t dyn_smem[];
+    __shared__ LoDenseShared sh;
+    uint8_t* base = align1024(dyn_smem);
+    // slot: Y hi, Y lo (the chunk's H rows, up to 16 KB each), D hi, D lo (16 KB each)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = tc::cluster_ctarank();
+    const bool even = rank == 0;
+    const int cid = blockIdx.x >> 1, n_cl = gridDim.x >> 1;
+    const int n_units = (P.n_pt >> 1) * P.n_wt;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kLSlots; ++s) {
+            tc::mbar_init(&sh.full[s], even ? 2 : 1);
+            tc::mbar_init(&sh.empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&sh.tmem_full[b], 1);
+            tc::mbar_init(&sh.tmem_empty[b], 2 * kLEpiWarps);
+        }
+        tc::mbar_init(&sh.drain, 1);
+        sh.abort = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc_pair(&sh.tmem_base, 2 * kBN);
+        tc::tmem_relinquish_pair();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::cluster_sync();  // both CTAs' barriers initialised before any remote arrive
+    tc::tc_fence_after();
+    const uint32_t tmem = sh.tmem_base;
+    volatile int* abort = &sh.abort;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- bulk-copy producer (both CTAs) ----------------
+        int s = 0;
+        uint32_t ph = 0, filled = 0, last_par = 0;
+        for (int u = cid; u < n_units && !*abort; u += n_cl) {
+            const int4 t = P.pt[2 * (u / P.n_wt) + rank];
+            const int rb = 2 * (u % P.n_wt) + (int)rank;  // this CTA's 128 Delta rows
+            const uint32_t H = (uint32_t)(t.y >> 16);
+            const uint32_t wbytes = H * 128u;  // H rows of 128 bytes
+            const int orb = (int)((unsigned)t.z >> 24);
+            for (int kb = 0; kb < P.nk; ++kb) {
+                if (!tc::mbar_wait_cluster(&sh.empty[s], ph ^ 1, abort)) break;
+                if (P.withhold && cid == 0 && even && u == cid && kb == 0) {
+                    // no arrival and no copy: the waits behind this stage run out
+                    if (++s == kLSlots) { s = 0; ph ^= 1; }
+                    continue;
+                }
+                uint8_t* st = base + s * kLSlotBytes;
+                tc::mbar_arrive_expect_tx(&sh.full[s], 2 * wbytes + 2 * kLTileBh);
+                const size_t ao = (size_t)(unsigned)t.w + (size_t)kb * H * kTileK;
+                const size_t bo = (((size_t)orb * P.nrb + rb) * P.nk + kb) * kTileElems;
+                tc::bulk_load(st, P.y_hi + ao, wbytes, &sh.full[s]);
+                tc::bulk_load(st + kLTileA, P.y_lo + ao, wbytes, &sh.full[s]);
+                tc::bulk_load(st + 2 * kLTileA, P.d_hi + bo, kLTileBh, &sh.full[s]);
+                tc::bulk_load(st + 2 * kLTileA + kLTileBh, P.d_lo + bo, kLTileBh, &sh.full[s]);
+                filled |= 1u << s;
+                last_par = (last_par & ~(1u << s)) | (ph << s);
+                if (++s == kLSlots) { s = 0; ph ^= 1; }
+            }
+        }
+        if (*abort) {
+            // every load issued has landed once its phase completes; bounded waits
+            for (int q = 0; q < kLSlots; ++q)
+                if (filled & (1u << q)) {
+                    volatile int never = 0;
+                    if (even)
+                        tc::mbar_wait_cluster(&sh.full[q], (last_par >> q) & 1, &never);
+                    else
+                        tc::mbar_wait(&sh.full[q], (last_par >> q) & 1, &never);
+                }
+        }
+    } else if (warp == 1 && lane == 0 && !even) {
+        // ---------------- forwarder (odd CTA) ----------------
+        const uint32_t peer_full0 = tc::mapa_shared(&sh.full[0], 0);
+        int s = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        for (int u = cid; u < n_units && ok && !*abort; u += n_cl) {
+            for (int kb = 0; kb < P.nk; ++kb) {
+                if (!tc::mbar_wait(&sh.full[s], ph, abort)) { ok = false; break; }
+                tc::mbar_arrive_remote(peer_full0 + s * (uint32_t)sizeof(uint64_t));
+                if (++s == kLSlots) { s = 0; ph ^= 1; }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- pair MMA issuer (even CTA) ----------------
+        int s = 0, k = 0;
+        uint32_t ph = 0;
+        for (int u = cid; u < n_units && !*abort; u += n_cl, ++k) {
+            const int Nc = 2 * (P.pt[2 * (u / P.n_wt)].y >> 16);
+            const uint32_t idesc = (P.idesc & ~(0x3fu << 17)) | ((uint32_t)(Nc >> 3) << 17);
+            const uint32_t buf = (uint32_t)k & 1u, use = (uint32_t)k >> 1;
+            if (!tc::mbar_wait_cluster(&sh.tmem_empty[buf], (use & 1u) ^ 1u, abort)) break;
+            tc::tc_fence_after();
+            const uint32_t d = tmem + buf * kBN;
+            bool ok = true;
+            for (int kb = 0; kb < P.nk; ++kb) {
+                if (!tc::mbar_wait_cluster(&sh.full[s], ph, abort)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint32_t st = tc::smem_u32(base + s * kLSlotBytes);
+#pragma unroll
+                for (int kk = 0; kk < kLBK / 16; ++kk) {
+                    const uint32_t off = kk * 32;
+                    const uint64_t whi = tc::smem_desc(st + off, 128);
+                    const uint64_t wlo = tc::smem_desc(st + kLTileA + off, 128);
+                    const uint64_t dhi = tc::smem_desc(st + 2 * kLTileA + off, 128);
+                    const uint64_t dlo = tc::smem_desc(st + 2 * kLTileA + kLTileBh + off, 128);
+                    const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                    // A = Delta_i rows (walkers), B = rows of Ytil and g
+                    tc::mma_f16_pair(d, dhi, whi, idesc, acc);
+                    tc::mma_f16_pair(d, dlo, whi, idesc, 1u);
+                    tc::mma_f16_pair(d, dhi, wlo, idesc, 1u);
+                }
+                tc::mma_commit_pair(&sh.empty[s], 0x3);
+                if (++s == kLSlots) { s = 0; ph ^= 1; }
+            }
+            if (!ok) break;
+            tc::mma_commit_pair(&sh.tmem_full[buf], 0x3);
+        }
+        tc::mma_commit_pair(&sh.drain, 0x1);
+        volatile int never = 0;
+        tc::mbar_wait(&sh.drain, 0, &never);
+    } else if (warp >= 2) {
+        // ---------------- epilogue (both CTAs) ----------------
+        // lane = walker row z = 2 w + re/im of this CTA, column = row s of the
+        // chunk.  With Y = Z / (row scale) / t + h (the Delta_i part scaled back,
+        // h on the real row only) and D = t Delta_j from the FP32 copy:
+        //   real row: D_re Y_re - D_im Y_im,   imaginary row: D_re Y_im + D_im Y_re
+        // (the other component from the partner lane z ^ 1); the g row adds
+        // Z / (row scale) instead.  The lane sum times 1/t is this walker's part.
+        const int q = warp & 3;                       // TMEM lane quarter
+        const int grp = (warp - 2) >> 2;              // column group of 64
+        const int ep_tid = threadIdx.x - 64;          // 0..511
+        const int z = q * 32 + lane;                  // walker row of this CTA
+        const bool odd = (lane & 1) != 0;             // imaginary component
+        const uint32_t even_tmem_empty0 = tc::mapa_shared(&sh.tmem_empty[0], 0);
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        int k = 0;
+        for (int u = cid; u < n_units; u += n_cl, ++k) {
+            const uint32_t buf = (uint32_t)k & 1u, use = (uint32_t)k >> 1;
+            const int ch = u / P.n_wt, wt = u % P.n_wt;
+            const int4 t0 = P.pt[2 * ch], t1 = P.pt[2 * ch + 1];
+            const int Nc = 2 * (t0.y >> 16);
+            const int nvalid = (t0.y & 0xffff) + (t1.y & 0xffff);
+            const int cj = (int)(((unsigned)t0.z >> 16) & 0xffu);
+            const int s0 = t0.z & 0xffff;
+            const int gcol = P.M - s0;  // local column of the g row (only if inside this chunk)
+            const int rb = 2 * wt + (int)rank;
+            const int w = wt * kBNW + (int)rank * (kBNW / 2) + (z >> 1);
+            const float it = w < P.W ? __ldg(P.inv_t + w) : 0.f;
+            // the chunk's per-row constants (zero beyond its valid rows); the
+            // previous unit's readers are past its closing barrier
+            if (ep_tid < kBN) {
+                float2 k2 = make_float2(0.f, 0.f);
+                if (ep_tid < nvalid) k2 = __ldg(P.rowc + t0.x + ep_tid);
+                sh.cst[ep_tid] = k2;
+            }
+            asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
+            const bool got = tc::mbar_wait_cluster(&sh.tmem_full[buf], use & 1u, abort);
+            // leave together: the named barriers below expect every epilogue warp
+            if (tc::bar_or(!got, 1, 32 * kLEpiWarps)) break;
+            tc::tc_fence_after();
+            const int c_begin = grp * 64;
+            const int nld = c_begin >= Nc ? 0 : (min(Nc - c_begin, 64) + 31) / 32;
+            if (nld == 0) {
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive_remote(even_tmem_empty0 + buf * (uint32_t)sizeof(uint64_t));
+            }
+            const float* drow = P.dfull + (((size_t)cj * P.nrb + rb) * kBM + z) * P.Sd + s0;
+            float acc = 0.f;
+#pragma unroll 1
+            for (int c2 = 0; c2 < 2 * nld; ++c2) {
+                // 16 columns at a time (registers: the TMEM values and Delta_j)
+                const int col0 = c_begin + 16 * c2;
+                float4 dv4[4];
+#pragma unroll
+                for (int m4 = 0; m4 < 4; ++m4) dv4[m4] = __ldg(reinterpret_cast<const float4*>(drow + col0) + m4);
+                float zv[16];
+                tc::tmem_ld16(tmem + lane_off + buf * kBN + col0, zv);
+                tc::tmem_wait_ld();
+                if (c2 == 2 * nld - 1) {
+                    // the last TMEM read of this warp is complete: release the buffer
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive_remote(even_tmem_empty0 + buf * (uint32_t)sizeof(uint64_t));
+                }
+                const float* dv = reinterpret_cast<const float*>(dv4);
+#pragma unroll
+                for (int m = 0; m < 16; ++m) {
+                    const int col = col0 + m;
+                    const float2 k2 = sh.cst[col];  // broadcast
+                    const float y = fmaf(zv[m], k2.x * it, odd ? 0.f : k2.y);
+                    const float yp = __shfl_xor_sync(0xffffffffu, y, 1);
+                    const float d = dv[m];
+                    const float dp = __shfl_xor_sync(0xffffffffu, d, 1);
+                    float v = odd ? fmaf(dp, y, d * yp) : fmaf(d, y, -dp * yp);
+                    v = col == gcol ? zv[m] * k2.x : v;
+                    // columns past the chunk were not written by this unit's MMAs
+                    acc += col < Nc ? v : 0.f;
+                }
+            }
+            sh.red[grp][z] = acc * it;
+            asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
+            if (ep_tid < kBNW / 2) {
+                const int wl = wt * kBNW + (int)rank * (kBNW / 2) + ep_tid;
+                const double re = f2d_bits(sh.red[0][2 * ep_tid]) + f2d_bits(sh.red[1][2 * ep_tid]) +
+                                  f2d_bits(sh.red[2][2 * ep_tid]) + f2d_bits(sh.red[3][2 * ep_tid]);
+                const double im = f2d_bits(sh.red[0][2 * ep_tid + 1]) + f2d_bits(sh.red[1][2 * ep_tid + 1]) +
+                                  f2d_bits(sh.red[2][2 * ep_tid + 1]) + f2d_bits(sh.red[3][2 * ep_tid + 1]);
+                if (wl < P.W) P.part[(size_t)ch * P.ldp + wl] = make_double2(re, im);
+            }
+            asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    // the even CTA's MMAs read the odd CTA's shared memory and write its TMEM,
+    // and both CTAs arrive on each other's barriers: neither leaves early
+    tc::cluster_sync();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc_pair(tmem, 2 * kBN);
+    if (threadIdx.x == 0 && sh.abort) atomicExch(P.err, 1);
+}
+
 // ---------------------------------------------------------------------------
 // FP64 reductions of the tensor-core partials
 // ---------------------------------------------------------------------------
@@ -1176,9 +1451,66 @@ void ensure_coulomb_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     mx.coul_ready = true;
 }
 
-void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
-    if (mx.lo_ready) return;
+// rank chunks of a list of K rows: ceil(K / 256) balanced chunks of Nc rows
+// (a multiple of 16, the MMA's N), two half-tiles of Nc / 2 rows each
+struct ChunkGeom {
+    int nch = 0, Nc = 0;
+    int cols() const { return nch * Nc; }
+};
+inline ChunkGeom chunk_geom(int K) {
+    ChunkGeom g;
+    if (K <= 0) return g;
+    g.nch = (K + 255) / 256;
+    g.Nc = ((K + g.nch - 1) / g.nch + 15) / 16 * 16;
+    return g;
+}
+
+// FP64 rows of the dense blocks -> 16-bit planes, per-row inverse scale and h
+template <bool BF16>
+__global__ void dense_rows_kernel(int M, int r_pad, const double* __restrict__ rows,
+                                  const double* __restrict__ hrow, uint16_t* __restrict__ hi,
+                                  uint16_t* __restrict__ lo, float2* __restrict__ rowc) {
+    __shared__ double red[32];
+    const long row = blockIdx.x;
+    const double* s = rows + row * M;
+    double m = 0.0;
+    for (int r = threadIdx.x; r < M; r += blockDim.x) m = fmax(m, fabs(s[r]));
+    const double sc = pow2_scale(block_max(m, red));
+    for (int r = threadIdx.x; r < r_pad; r += blockDim.x) {
+        uint16_t h, l;
+        split16<BF16>(r < M ? s[r] * sc : 0.0, h, l);
+        hi[row * r_pad + r] = h;
+        lo[row * r_pad + r] = l;
+    }
+    if (threadIdx.x == 0) rowc[row] = make_float2((float)(1.0 / sc), (float)hrow[row]);
+}
+
+void release_lo(MixedOps& mx) {
+    for (DevBuf* b : {&mx.U_hi, &mx.U_lo, &mx.V_hi, &mx.V_lo, &mx.row_c, &mx.pt, &mx.pair_pt0,
+                      &mx.pair_npt, &mx.pair_w, &mx.e0, &mx.s_pt, &mx.s_pt0, &mx.s_npt, &mx.s_pw,
+                      &mx.Ub_hi, &mx.Ub_lo, &mx.Vb_hi, &mx.Vb_lo, &mx.pt_J, &mx.row_cJ, &mx.e0_J,
+                      &mx.pw_J, &mx.dpt, &mx.Yb_hi, &mx.Yb_lo, &mx.rowc_d, &mx.s_dpt})
+        b->release();
+    mx.lo_ready = false;
+    mx.screen_built = -1;
+    mx.h_tiles.clear(); mx.h_dtiles.clear(); mx.h_pt0.clear(); mx.h_npt.clear(); mx.h_order.clear();
+    mx.h_pw.clear(); mx.h_e0.clear(); mx.h_dense.clear();
+    mx.n_pt = mx.n_dpt = mx.n_pairs = mx.s_n_pt = mx.s_n_dpt = 0;
+    mx.Sd = 0;
+    mx.R = 0;
+}
+
+// LO operands.  dense_ok (mode LO): every pair whose dense truncated block
+// (M + 1 rows in chunks) costs fewer MMA columns than its two factor sides is
+// contracted densely (lo_dense_tc_kernel), the rest through its factors
+// (lo_exchange_tc_kernel); the dense half-tiles come first in the pair lists.
+// Without dense_ok (mode LO_JK) every pair goes through its factors, and the
+// swapped lists of the compressed Coulomb are built too (closed shells).
+void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool dense_ok) {
+    if (mx.lo_ready && mx.lo_dense_ok == dense_ok) return;
+    if (mx.lo_ready) release_lo(mx);
     mx.bf16 = bf16;
+    mx.lo_dense_ok = dense_ok;
     mx.r_pad = (c->M + 7) / 8 * 8;
     const int M = c->M;
     long R = 0;
@@ -1197,7 +1529,8 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     inv_v.ensure(Rb * sizeof(float));
     pbuf.ensure(Rb * sizeof(double));
     qbuf.ensure(Rb * sizeof(double));
-    const bool jk = c->nspin == 1;  // the compressed Coulomb is built for closed shells
+    // the compressed Coulomb is built for closed shells, with the factored plan
+    const bool jk = c->nspin == 1 && !dense_ok;
     if (jk) {
         pJ.ensure(Rb * sizeof(double));
         qJ.ensure(Rb * sizeof(double));
@@ -1206,11 +1539,14 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     mx.e0.ensure(std::max(npairs, 1) * sizeof(double));
     mx.pair_w.ensure(std::max(npairs, 1) * sizeof(double));
 
-    std::vector<double> pw;
-    std::vector<int4> tiles;
-    std::vector<int> pt0(npairs), npt(npairs);
     const int nkb = ceil_div(M, kTileK);
-    long woff = 0;  // weight half-tile elements so far
+    const ChunkGeom dg = chunk_geom(M + 1);  // dense: the rows s of Ytil and g
+    std::vector<double> pw;
+    std::vector<int4> tiles, dtiles;
+    std::vector<int> pt0(npairs), npt(npairs);
+    std::vector<unsigned char> is_dense(npairs, 0);
+    std::vector<long> prow(npairs);  // first packed factor row of each pair (both spins)
+    std::vector<int> pspin(npairs), plocal(npairs);
     long row_base = 0;
     int pair_base = 0;
     for (int s = 0; s < c->nspin; ++s) {
@@ -1272,43 +1608,75 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
             }
             LOAF_CUDA(cudaStreamSynchronize(c->stream));
         }
-        // pair tiles in 8 x 8 orbital blocks (pairs sharing orbitals run together)
+        for (int n = 0; n < pt.npairs; ++n) {
+            const int g = pair_base + n;
+            prow[g] = row_base + pt.off[n];
+            pspin[g] = s;
+            plocal[g] = n;
+            const ChunkGeom fg = chunk_geom(pt.K[n]);
+            is_dense[g] = dense_ok && fg.nch > 0 && dg.cols() < 2 * fg.cols();
+            pw.push_back(0.5 * sd.mult * (pt.i[n] == pt.j[n] ? 1.0 : 2.0));
+        }
+        // pair order: 8 x 8 orbital blocks (pairs sharing orbitals run together)
         std::vector<int> order(pt.npairs);
         for (int n = 0; n < pt.npairs; ++n) order[n] = n;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
             const int ba = (pt.i[a] / 8) * 1024 + pt.j[a] / 8, bb = (pt.i[b] / 8) * 1024 + pt.j[b] / 8;
             return ba < bb;
         });
-        for (int n : order) {
-            const int gpair = pair_base + n;
-            mx.h_order.push_back(gpair);
-            pt0[gpair] = (int)tiles.size();
-            int cnt = 0;
-            const int cij = ((sd.col0 + pt.i[n]) << 16) | (sd.col0 + pt.j[n]);
-            // the pair's ranks in balanced chunks of at most 256 (the MMA's N, a
-            // multiple of 16); each chunk is two half-tiles of H = N / 2 rows, one
-            // per CTA of the pair, stored at element offset woff
-            const int K = pt.K[n];
-            if (K > 0) {
-                const int nch = (K + 255) / 256;
-                const int Nc = ((K + nch - 1) / nch + 15) / 16 * 16;
-                const int H = Nc / 2;
-                for (int ch = 0; ch < nch; ++ch)
-                    for (int hf = 0; hf < 2; ++hf) {
-                        const int r0 = ch * Nc + hf * H;
-                        const int nv = std::max(0, std::min(H, K - r0));
-                        tiles.push_back(make_int4((int)(row_base + pt.off[n] + (nv > 0 ? r0 : 0)),
-                                                  nv | (H << 16), cij, (int)woff));
-                        woff += (long)H * kTileK * nkb;
-                        ++cnt;
-                    }
-            }
-            npt[gpair] = cnt;
-        }
-        for (int n = 0; n < pt.npairs; ++n)
-            pw.push_back(0.5 * sd.mult * (pt.i[n] == pt.j[n] ? 1.0 : 2.0));
+        for (int n : order) mx.h_order.push_back(pair_base + n);
         row_base += pt.rows;
         pair_base += pt.npairs;
+    }
+    // half-tile lists in pair order: dense chunks of the dense pairs, then the
+    // factor chunks of the others; pair_pt0 indexes the two lists as one
+    long woff = 0, doff = 0;  // tile elements so far (factored, dense)
+    std::vector<int> dense_rank(npairs, -1);  // index among the dense pairs
+    int n_dense_pairs = 0;
+    for (int g : mx.h_order) {
+        if (!is_dense[g]) continue;
+        dense_rank[g] = n_dense_pairs++;
+        const SpinData& sd = c->sp[pspin[g]];
+        const PairTable& pt = sd.pairs;
+        const int n = plocal[g];
+        const unsigned ci = (unsigned)(sd.col0 + pt.i[n]), cj = (unsigned)(sd.col0 + pt.j[n]);
+        pt0[g] = (int)dtiles.size();
+        const int H = dg.Nc / 2, Kd = M + 1;
+        for (int ch = 0; ch < dg.nch; ++ch)
+            for (int hf = 0; hf < 2; ++hf) {
+                const int r0 = ch * dg.Nc + hf * H;
+                const int nv = std::max(0, std::min(H, Kd - r0));
+                const long row0 = (long)dense_rank[g] * Kd + (nv > 0 ? r0 : 0);
+                dtiles.push_back(make_int4((int)row0, nv | (H << 16),
+                                           (int)((ci << 24) | (cj << 16) | (unsigned)(ch * dg.Nc)), (int)doff));
+                doff += (long)H * kTileK * nkb;
+            }
+        npt[g] = 2 * dg.nch;
+    }
+    const int n_dpt = (int)dtiles.size();
+    for (int g : mx.h_order) {
+        if (is_dense[g]) continue;
+        const SpinData& sd = c->sp[pspin[g]];
+        const PairTable& pt = sd.pairs;
+        const int n = plocal[g];
+        pt0[g] = n_dpt + (int)tiles.size();
+        int cnt = 0;
+        const int cij = ((sd.col0 + pt.i[n]) << 16) | (sd.col0 + pt.j[n]);
+        // the pair's ranks in balanced chunks of at most 256 (the MMA's N, a
+        // multiple of 16); each chunk is two half-tiles of H = N / 2 rows, one
+        // per CTA of the pair, stored at element offset woff
+        const int K = pt.K[n];
+        const ChunkGeom fg = chunk_geom(K);
+        const int H = fg.Nc / 2;
+        for (int ch = 0; ch < fg.nch; ++ch)
+            for (int hf = 0; hf < 2; ++hf) {
+                const int r0 = ch * fg.Nc + hf * H;
+                const int nv = std::max(0, std::min(H, K - r0));
+                tiles.push_back(make_int4((int)(prow[g] + (nv > 0 ? r0 : 0)), nv | (H << 16), cij, (int)woff));
+                woff += (long)H * kTileK * nkb;
+                ++cnt;
+            }
+        npt[g] = cnt;
     }
     if (R > 0) {
         row_consts_kernel<<<ceil_div(R, 256), 256, 0, c->stream>>>(R, inv_u.as<float>(), inv_v.as<float>(),
@@ -1324,11 +1692,16 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
         LOAF_LAUNCH_CHECK();
     }
     mx.n_pt = (int)tiles.size();
+    mx.n_dpt = n_dpt;
     mx.pt.ensure(std::max<size_t>(tiles.size(), 1) * sizeof(int4));
+    mx.dpt.ensure(std::max<size_t>(dtiles.size(), 1) * sizeof(int4));
     mx.pair_pt0.ensure(std::max(npairs, 1) * sizeof(int));
     mx.pair_npt.ensure(std::max(npairs, 1) * sizeof(int));
     if (!tiles.empty())
         LOAF_CUDA(cudaMemcpyAsync(mx.pt.ptr, tiles.data(), tiles.size() * sizeof(int4),
+                                  cudaMemcpyHostToDevice, c->stream));
+    if (!dtiles.empty())
+        LOAF_CUDA(cudaMemcpyAsync(mx.dpt.ptr, dtiles.data(), dtiles.size() * sizeof(int4),
                                   cudaMemcpyHostToDevice, c->stream));
     LOAF_CUDA(cudaMemcpyAsync(mx.pair_pt0.ptr, pt0.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     LOAF_CUDA(cudaMemcpyAsync(mx.pair_npt.ptr, npt.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, c->stream));
@@ -1366,14 +1739,16 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
         mx.EJ0 = ej0;
     }
     mx.h_tiles = tiles;
+    mx.h_dtiles = dtiles;
     mx.h_pt0 = pt0;
     mx.h_npt = npt;
     mx.h_pw = pw;
     mx.h_e0 = e0;
+    mx.h_dense = is_dense;
     mx.screen_built = -1;
-    // operand tiles [tile][kb]; the row-major staging planes are then dropped
     mx.nkb = nkb;
-    LOAF_REQUIRE(woff < (1L << 31), LOAF_ERR_SHAPE, "LO weight tiles beyond 2^31 elements");
+    LOAF_REQUIRE(woff < (1L << 31) && doff < (1L << 31), LOAF_ERR_SHAPE, "LO weight tiles beyond 2^31 elements");
+    // factor tiles [tile][kb]
     if (mx.n_pt > 0) {
         const size_t tb = (size_t)woff * sizeof(uint16_t);
         const dim3 tg(mx.n_pt, mx.nkb);
@@ -1388,34 +1763,114 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
         LOAF_CUDA(cudaStreamSynchronize(c->stream));
     }
     for (DevBuf* b : {&mx.U_hi, &mx.U_lo, &mx.V_hi, &mx.V_lo}) b->release();
+    // dense blocks: Ytil = Ubar Vbar (rows s), g = Vbar^T p, h = Ubar q in FP64
+    // (cuBLAS), split into 16-bit rows with per-row scales, then tiled
+    if (n_dense_pairs > 0) {
+        const int Kd = M + 1;
+        mx.Sd = dg.cols() + 32;  // columns a chunk's epilogue may read, padded
+        mx.Yb_hi.ensure((size_t)doff * sizeof(uint16_t));
+        mx.Yb_lo.ensure((size_t)doff * sizeof(uint16_t));
+        mx.rowc_d.ensure((size_t)n_dense_pairs * Kd * sizeof(float2));
+        const int batch = std::max(1, std::min(n_dense_pairs, (int)((256L << 20) / ((long)Kd * M * 8))));
+        DevBuf ytmp, htmp, plane_hi, plane_lo, btiles;
+        ytmp.ensure((size_t)batch * Kd * M * sizeof(double));
+        htmp.ensure((size_t)batch * Kd * sizeof(double));
+        plane_hi.ensure((size_t)batch * Kd * mx.r_pad * 2);
+        plane_lo.ensure((size_t)batch * Kd * mx.r_pad * 2);
+        btiles.ensure((size_t)batch * 2 * dg.nch * sizeof(int4));
+        std::vector<int> dense_pairs(n_dense_pairs);
+        for (int g = 0; g < npairs; ++g)
+            if (dense_rank[g] >= 0) dense_pairs[dense_rank[g]] = g;
+        const double one = 1.0, zero = 0.0;
+        LOAF_CUBLAS(cublasSetStream(c->cublas, c->stream));
+        for (int b0 = 0; b0 < n_dense_pairs; b0 += batch) {
+            const int nb = std::min(batch, n_dense_pairs - b0);
+            LOAF_CUDA(cudaMemsetAsync(htmp.ptr, 0, (size_t)nb * Kd * sizeof(double), c->stream));
+            std::vector<int4> bt;
+            for (int b = 0; b < nb; ++b) {
+                const int g = dense_pairs[b0 + b];
+                const PairTable& pt = c->sp[pspin[g]].pairs;
+                const int n = plocal[g], K = pt.K[n];
+                const double* U = pt.d_U.as<double>() + (size_t)pt.off[n] * M;  // K rows of Ubar^T
+                const double* V = pt.d_V.as<double>() + (size_t)pt.off[n] * M;  // K rows of Vbar
+                double* Y = ytmp.as<double>() + (size_t)b * Kd * M;
+                // Ytil[s][r] = sum_k U[k][s] V[k][r]: column-major V U^T
+                LOAF_CUBLAS(cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_T, M, M, K, &one, V, M, U, M,
+                                        &zero, Y, M));
+                // row M: g[r] = sum_k V[k][r] p[k];  h[s] = sum_k U[k][s] q[k]
+                LOAF_CUBLAS(cublasDgemv(c->cublas, CUBLAS_OP_N, M, K, &one, V, M,
+                                        pbuf.as<double>() + prow[g], 1, &zero, Y + (size_t)M * M, 1));
+                LOAF_CUBLAS(cublasDgemv(c->cublas, CUBLAS_OP_N, M, K, &one, U, M,
+                                        qbuf.as<double>() + prow[g], 1, &zero,
+                                        htmp.as<double>() + (size_t)b * Kd, 1));
+                for (int q = 0; q < 2 * dg.nch; ++q) {
+                    int4 t = dtiles[mx.h_pt0[g] + q];
+                    t.x -= b0 * Kd;  // row of the batch's plane
+                    bt.push_back(t);
+                }
+            }
+            const long rows = (long)nb * Kd;
+            const size_t roff = (size_t)b0 * Kd;
+            if (bf16)
+                dense_rows_kernel<true><<<rows, 128, 0, c->stream>>>(M, mx.r_pad, ytmp.as<double>(), htmp.as<double>(),
+                    plane_hi.as<uint16_t>(), plane_lo.as<uint16_t>(), mx.rowc_d.as<float2>() + roff);
+            else
+                dense_rows_kernel<false><<<rows, 128, 0, c->stream>>>(M, mx.r_pad, ytmp.as<double>(), htmp.as<double>(),
+                    plane_hi.as<uint16_t>(), plane_lo.as<uint16_t>(), mx.rowc_d.as<float2>() + roff);
+            LOAF_LAUNCH_CHECK();
+            LOAF_CUDA(cudaMemcpyAsync(btiles.ptr, bt.data(), bt.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                      c->stream));
+            const dim3 tg((unsigned)bt.size(), mx.nkb);
+            lo_tiles_kernel<<<tg, 256, 0, c->stream>>>(plane_hi.as<uint16_t>(), mx.r_pad, mx.nkb,
+                                                      btiles.as<int4>(), mx.Yb_hi.as<uint16_t>());
+            lo_tiles_kernel<<<tg, 256, 0, c->stream>>>(plane_lo.as<uint16_t>(), mx.r_pad, mx.nkb,
+                                                      btiles.as<int4>(), mx.Yb_lo.as<uint16_t>());
+            LOAF_LAUNCH_CHECK();
+            LOAF_CUDA(cudaStreamSynchronize(c->stream));  // bt and the batch buffers are reused
+        }
+    }
     mx.lo_ready = true;
 }
 
-// Tile list restricted to the pairs the screen keeps (same order as the full
-// list); a dropped pair loses both its walker part and its trial part e0.
+// Tile lists restricted to the pairs the screen keeps (same order as the full
+// lists, dense half-tiles first); a dropped pair loses both its walker part
+// and its trial part e0.
 void ensure_screened_tiles(loaf_ctx* c, MixedOps& mx) {
     if (mx.screen_built == c->screen_version) return;
     const int npairs = mx.n_pairs;
-    std::vector<int4> tiles;
+    std::vector<int4> tiles, dtiles;
     std::vector<int> pt0(npairs, 0), npt(npairs, 0);
     std::vector<double> pw(npairs, 0.0);
     double ek0 = 0.0;
+    auto kept = [&](int g) { return c->keep.empty() || c->keep[g]; };
     for (int g : mx.h_order) {
-        const bool k = c->keep.empty() || c->keep[g];
-        pt0[g] = (int)tiles.size();
-        if (!k) continue;
-        for (int t = 0; t < mx.h_npt[g]; ++t) tiles.push_back(mx.h_tiles[mx.h_pt0[g] + t]);
+        if (!mx.h_dense[g] || !kept(g)) continue;
+        pt0[g] = (int)dtiles.size();
+        for (int t = 0; t < mx.h_npt[g]; ++t) dtiles.push_back(mx.h_dtiles[mx.h_pt0[g] + t]);
+        npt[g] = mx.h_npt[g];
+        pw[g] = mx.h_pw[g];
+    }
+    const int nd = (int)dtiles.size();
+    for (int g : mx.h_order) {
+        if (mx.h_dense[g] || !kept(g)) continue;
+        pt0[g] = nd + (int)tiles.size();
+        for (int t = 0; t < mx.h_npt[g]; ++t) tiles.push_back(mx.h_tiles[mx.h_pt0[g] - mx.n_dpt + t]);
         npt[g] = mx.h_npt[g];
         pw[g] = mx.h_pw[g];
     }
     for (int g = 0; g < npairs; ++g) ek0 += pw[g] * mx.h_e0[g];  // same order as the full list
     mx.s_n_pt = (int)tiles.size();
+    mx.s_n_dpt = nd;
     mx.s_pt.ensure(std::max<size_t>(tiles.size(), 1) * sizeof(int4));
+    mx.s_dpt.ensure(std::max<size_t>(dtiles.size(), 1) * sizeof(int4));
     mx.s_pt0.ensure(std::max(npairs, 1) * sizeof(int));
     mx.s_npt.ensure(std::max(npairs, 1) * sizeof(int));
     mx.s_pw.ensure(std::max(npairs, 1) * sizeof(double));
     if (!tiles.empty())
         LOAF_CUDA(cudaMemcpyAsync(mx.s_pt.ptr, tiles.data(), tiles.size() * sizeof(int4),
+                                  cudaMemcpyHostToDevice, c->stream));
+    if (!dtiles.empty())
+        LOAF_CUDA(cudaMemcpyAsync(mx.s_dpt.ptr, dtiles.data(), dtiles.size() * sizeof(int4),
                                   cudaMemcpyHostToDevice, c->stream));
     LOAF_CUDA(cudaMemcpyAsync(mx.s_pt0.ptr, pt0.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     LOAF_CUDA(cudaMemcpyAsync(mx.s_npt.ptr, npt.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, c->stream));
@@ -1501,6 +1956,17 @@ int lo_max_clusters(loaf_ctx* c) {
     int n = 0;
     LOAF_CUDA(cudaOccupancyMaxActiveClusters(&n, lo_exchange_tc_kernel, &cfg));
     LOAF_REQUIRE(n > 0, LOAF_ERR_CUDA, "the LO exchange kernel's CTA pair does not fit on an SM pair");
+    if (dev < 64) cached[dev] = n;
+    return n;
+}
+
+int lo_dense_max_clusters(loaf_ctx* c) {
+    static int cached[64] = {0};
+    int dev = 0;
+    LOAF_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && cached[dev] > 0) return cached[dev];
+    const int n = max_pair_clusters((const void*)lo_dense_tc_kernel, kLThreads, kLoSmem, c->sm_count);
+    LOAF_REQUIRE(n > 0, LOAF_ERR_CUDA, "the dense LO kernel's CTA pair does not fit on an SM pair");
     if (dev < 64) cached[dev] = n;
     return n;
 }
@@ -1612,7 +2078,15 @@ void run_force_bias_mixed(loaf_ctx* c, int W, int precision, double2* e_scratch,
 void setup_mixed_operands(loaf_ctx* c, int mode, bool bf16) {
     MixedOps& mx = c->mix[bf16 ? 1 : 0];
     ensure_coulomb_ops(c, mx, bf16);
-    if (mode != LOAF_MODE_FULL) ensure_lo_ops(c, mx, bf16);
+    if (mode != LOAF_MODE_FULL) ensure_lo_ops(c, mx, bf16, mode == LOAF_MODE_LO);
+}
+
+int prepare_lo_operands(loaf_ctx* c, int mode, int precision) {
+    if (mode == LOAF_MODE_FULL || precision == LOAF_PREC_FP64) return 0;
+    const bool bf16 = precision == LOAF_PREC_BF16X3;
+    MixedOps& mx = c->mix[bf16 ? 1 : 0];
+    ensure_lo_ops(c, mx, bf16, mode == LOAF_MODE_LO);
+    return mx.n_dpt > 0 ? mx.Sd : 0;
 }
 
 void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2* theta,
@@ -1620,7 +2094,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
     const bool bf16 = precision == LOAF_PREC_BF16X3;
     MixedOps& mx = c->mix[bf16 ? 1 : 0];
     if (e_out) ensure_coulomb_ops(c, mx, bf16);
-    if (mode != LOAF_MODE_FULL) ensure_lo_ops(c, mx, bf16);
+    if (mode != LOAF_MODE_FULL) ensure_lo_ops(c, mx, bf16, mode == LOAF_MODE_LO);
     mx.r_pad = (c->M + 7) / 8 * 8;
     mx.kflat = (long)c->ntot * mx.r_pad;
 
@@ -1661,13 +2135,69 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         const bool screened = !c->keep.empty() && e_pairs == nullptr;
         if (screened) ensure_screened_tiles(c, mx);
         const int n_pt = screened ? mx.s_n_pt : mx.n_pt;
+        const int n_dpt = screened ? mx.s_n_dpt : mx.n_dpt;
         const int4* tile_list = screened ? mx.s_pt.as<int4>() : mx.pt.as<int4>();
+        const int4* dense_list = screened ? mx.s_dpt.as<int4>() : mx.dpt.as<int4>();
         const int* list_pt0 = screened ? mx.s_pt0.as<int>() : mx.pair_pt0.as<int>();
         const int* list_npt = screened ? mx.s_npt.as<int>() : mx.pair_npt.as<int>();
         const double* list_pw = screened ? mx.s_pw.as<double>() : mx.pair_w.as<double>();
         const double list_ek0 = screened ? mx.s_EK0 : mx.EK0;
-        // one launch of the CTA-pair kernel over a tile list with its row constants
-        auto launch_lo = [&](const int4* tiles, int ntiles, const float4* rowc, const char* stage) {
+        // partial sums per chunk and walker: the dense chunks first, then the factored
+        c->w_lopart.ensure((size_t)std::max(n_pt + n_dpt, 2) / 2 * Wpad * sizeof(double2));
+        auto take_withhold = [&] {
+            if (c->test_withhold <= 0) return 0;
+            --c->test_withhold;
+            return 1;
+        };
+        auto cluster_cfg = [&](int n_cl) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(2 * n_cl);
+            cfg.blockDim = dim3(kLThreads);
+            cfg.dynamicSmemBytes = kLoSmem;
+            cfg.stream = c->stream;
+            return cfg;
+        };
+        cudaLaunchAttribute cl_attr[1];
+        cl_attr[0].id = cudaLaunchAttributeClusterDimension;
+        cl_attr[0].val.clusterDim.x = 2;
+        cl_attr[0].val.clusterDim.y = 1;
+        cl_attr[0].val.clusterDim.z = 1;
+        // the dense kernel over its half-tile list (partial rows 0 .. n_dpt / 2)
+        if (n_dpt > 0) {
+            LoDenseParams P;
+            P.y_hi = mx.Yb_hi.as<uint16_t>();
+            P.y_lo = mx.Yb_lo.as<uint16_t>();
+            P.d_hi = c->w_dhi.as<uint16_t>();
+            P.d_lo = c->w_dlo.as<uint16_t>();
+            P.dfull = c->w_dfull.as<float>();
+            P.nrb = dg.nrb;
+            P.Sd = mx.Sd;
+            P.pt = dense_list;
+            P.rowc = mx.rowc_d.as<float2>();
+            P.inv_t = inv_t;
+            P.part = c->w_lopart.as<double2>();
+            P.n_pt = n_dpt;
+            P.n_wt = n_wt;
+            P.W = W;
+            P.ldp = Wpad;
+            P.nk = dg.nkb;
+            P.M = c->M;
+            P.idesc = idesc;
+            P.err = err;
+            P.withhold = take_withhold();
+            const int units = (n_dpt / 2) * n_wt;
+            const int n_cl = std::max(1, std::min({units, lo_dense_max_clusters(c), c->persistent_grid() / 2}));
+            cudaLaunchConfig_t cfg = cluster_cfg(n_cl);
+            cfg.attrs = cl_attr;
+            cfg.numAttrs = 1;
+            StageScope dsc(c, "lo_dense_tc", 1);
+            LOAF_CUDA(cudaLaunchKernelEx(&cfg, lo_dense_tc_kernel, P));
+            LOAF_LAUNCH_CHECK();
+        }
+        // one launch of the factored CTA-pair kernel over a tile list with its
+        // row constants, writing partial rows from part_row0
+        auto launch_lo = [&](const int4* tiles, int ntiles, const float4* rowc, const char* stage,
+                             int part_row0) {
             if (ntiles <= 0) return;
             LoParams P;
             P.u_hi = mx.Ub_hi.as<uint16_t>();
@@ -1687,33 +2217,18 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             P.nk = dg.nkb;
             P.idesc = idesc;
             P.err = err;
-            P.withhold = 0;
-            if (c->test_withhold > 0) {
-                P.withhold = 1;
-                --c->test_withhold;
-            }
-            c->w_lopart.ensure((size_t)ntiles * Wpad * sizeof(double2));
-            P.part = c->w_lopart.as<double2>();
+            P.withhold = take_withhold();
+            P.part = c->w_lopart.as<double2>() + (size_t)part_row0 * Wpad;
             const int units = (ntiles / 2) * n_wt;
             const int n_cl = std::max(1, std::min({units, lo_max_clusters(c), c->persistent_grid() / 2}));
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = 2;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.gridDim = dim3(2 * n_cl);
-            cfg.blockDim = dim3(kLThreads);
-            cfg.dynamicSmemBytes = kLoSmem;
-            cfg.stream = c->stream;
-            cfg.attrs = attr;
+            cudaLaunchConfig_t cfg = cluster_cfg(n_cl);
+            cfg.attrs = cl_attr;
             cfg.numAttrs = 1;
             StageScope lsc(c, stage, 1);
             LOAF_CUDA(cudaLaunchKernelEx(&cfg, lo_exchange_tc_kernel, P));
             LOAF_LAUNCH_CHECK();
         };
-        launch_lo(tile_list, n_pt, mx.row_c.as<float4>(), "lo_exchange_tc");
-        c->w_lopart.ensure(16);
+        launch_lo(tile_list, n_pt, mx.row_c.as<float4>(), "lo_exchange_tc", n_dpt / 2);
         StageScope lrs(c, "lo_reduce", ek ? 2 : 1);
         const int nsl = std::max(1, std::min(kRedSlices, mx.n_pairs));
         c->w_red.ensure((size_t)kRedSlices * W * sizeof(double2));
@@ -1730,7 +2245,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         if (mode == LOAF_MODE_LO_JK && e_out) {
             // E_J from the compressed factors replaces the exact Coulomb term:
             // the pair's orbitals exchanged, every pair (the screen is for exchange)
-            launch_lo(mx.pt_J.as<int4>(), mx.n_pt, mx.row_cJ.as<float4>(), "lo_coulomb_tc");
+            launch_lo(mx.pt_J.as<int4>(), mx.n_pt, mx.row_cJ.as<float4>(), "lo_coulomb_tc", 0);
             StageScope jrs(c, "lo_coulomb_reduce", 2);
             lo_tc_reduce_kernel<<<dim3(ceil_div(W, 32), nsl), 256, 0, c->stream>>>(
                 mx.n_pairs, W, Wpad, mx.pair_pt0.as<int>(), mx.pair_npt.as<int>(), mx.pw_J.as<double>(),
