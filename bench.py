@@ -287,11 +287,14 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
+        # the timed region is also the profiler's range (ncu --profile-from-start off)
+        torch.cuda.profiler.start()
         ev0.record(stream)
         for _ in range(args.steps):
             step()
         ev1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         barrier()
     ms = ev0.elapsed_time(ev1)
     prof = ctx.profile_read()

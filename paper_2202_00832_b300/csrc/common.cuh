@@ -137,6 +137,12 @@ inline DeltaGeom delta_geom(int M, int ntot, int W) {
     g.plane = (size_t)ntot * g.nrb * g.nkb * kTileElems;
     return g;
 }
+// FP32 copy of the scaled Delta for the dense LO epilogue: element (walker row
+// z, basis function s) of orbital c at [c][z / 128][s / 4][z % 128][s % 4], so that
+// the 32 rows of a warp read four consecutive s as 512 contiguous bytes
+__host__ __device__ inline size_t dfull_elem(int c, int nrb, int Sd, int z, int s) {
+    return ((((size_t)c * nrb + (z >> 7)) * (size_t)(Sd >> 2) + (s >> 2)) * 128 + (z & 127)) * 4 + (s & 3);
+}
 __device__ inline size_t delta_elem(int z, int c, int r, int nrb, int nkb) {
     return ((size_t)((size_t)c * nrb + (z >> 7)) * nkb + (r >> 6)) * kTileElems +
            sw128_elem(z & 127, r & 63);
@@ -331,7 +337,7 @@ struct loaf_ctx {
     loaf::DevBuf w_phi, w_theta, w_z, w_lu, w_perm, w_logdet, w_status, w_out, w_part,
         w_part2, w_dhi, w_dlo, w_dscale, w_host_stage, w_cpart, w_lopart, w_red, w_flag, w_oz_at, w_oz_bs,
         w_oz_bt, w_oz_S, w_oz_int, w_oz_key, w_prop_x, w_prop_part;
-    // FP32 copy of the scaled Delta for the dense LO epilogue, [c][rb][128][Sd];
+    // FP32 copy of the scaled Delta for the dense LO epilogue (dfull_elem layout);
     // zeroed whenever its geometry changes (the columns past M stay zero)
     loaf::DevBuf w_dfull;
     long dfull_key = -1;

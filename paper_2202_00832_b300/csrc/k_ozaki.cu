@@ -340,7 +340,7 @@ struct OzParams {
     uint16_t* dhi;
     uint16_t* dlo;
     int bf16;
-    float* dfull;         // mode 1, optional: FP32 Delta t as [c][rb][128 rows z][Sd] (dense LO epilogue)
+    float* dfull;         // mode 1, optional: FP32 Delta t in the dfull_elem layout (dense LO epilogue)
     int Sd;
 };
 
@@ -381,10 +381,7 @@ __device__ inline void store_delta(const OzParams& P, int w, int r, int cc, long
     const size_t o = delta_elem(2 * w + ro, P.col0 + k, r, P.nrb, P.nkb);
     P.dhi[o] = h;
     P.dlo[o] = l;
-    if (P.dfull) {
-        const int z = 2 * w + ro;
-        P.dfull[(((size_t)(P.col0 + k) * P.nrb + (z >> 7)) * 128 + (z & 127)) * P.Sd + r] = f;
-    }
+    if (P.dfull) P.dfull[dfull_elem(P.col0 + k, P.nrb, P.Sd, 2 * w + ro, r)] = f;
 }
 
 constexpr int kOEpiWarps = 16;  // four per TMEM lane quarter, 8-column chunks h, h + 4, h + 8
@@ -918,6 +915,17 @@ __global__ void delta_scale_kernel(int W, int nspin, const int* __restrict__ wex
     texp[w] = 12 - b;
 }
 
+// The g row of the dense LO blocks reads its "Delta_j" from column s = M of the
+// FP32 copy: t (the walker's Delta scale) in the real row, 0 in the imaginary
+// row, so that it adds g . Delta_i to the pair value unchanged
+__global__ void dfull_gcol_kernel(int W, int ntot, int nrb, int Sd, int M, const int* __restrict__ texp,
+                                  float* __restrict__ dfull) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (orbital, walker)
+    if (e >= ntot * W) return;
+    const int c = e / W, w = e - c * W;
+    dfull[dfull_elem(c, nrb, Sd, 2 * w, M)] = ldexpf(1.f, texp[w]);
+}
+
 }  // namespace
 
 void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision, int Sd) {
@@ -1067,6 +1075,11 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision, int Sd)
     delta_scale_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(
         W, c->nspin, wexp(0), gmx(0), wexp(c->nspin - 1), gmx(c->nspin - 1), inv_t, tscale, texp);
     LOAF_LAUNCH_CHECK();
+    if (Sd > 0) {
+        dfull_gcol_kernel<<<ceil_div((long)c->ntot * W, 256), 256, 0, c->stream>>>(
+            W, c->ntot, dg.nrb, Sd, M, texp, c->w_dfull.as<float>());
+        LOAF_LAUNCH_CHECK();
+    }
     // phase 3, per spin: Theta = phi Z on the tensor cores -> Delta planes
     for (int s = 0; s < c->nspin; ++s) {
         SpinData& sd = c->sp[s];

@@ -1029,7 +1029,7 @@ struct LoDenseParams {
     const uint16_t* y_lo;
     const uint16_t* d_hi;  // Delta tiles [c][rb][kb]
     const uint16_t* d_lo;
-    const float* dfull;    // Delta t: [c][rb][128 rows z][Sd] FP32
+    const float* dfull;    // Delta t, FP32, dfull_elem layout
     int nrb, Sd;
     const int4* pt;        // half-tiles {row0, nvalid | H << 16, ci << 24 | cj << 16 | s0, element offset}
     const float2* rowc;    // per dense row {1 / row scale, h}
@@ -1050,7 +1050,7 @@ struct LoDenseShared {
     uint32_t tmem_base;
     int abort;
     float red[4][kBM];          // per column group: sum over its columns, per walker row
-    float2 cst[kBN];            // per column of the chunk: {1 / row scale, h}
+    __align__(16) float2 cst[2][kBN];  // per column of a chunk: {1 / row scale, h}; two units
 };
 
 __global__ void __launch_bounds__(kLThreads, 1)
@@ -1184,84 +1184,114 @@ lo_dense_tc_kernel(LoDenseParams P) {
     } else if (warp >= 2) {
         // ---------------- epilogue (both CTAs) ----------------
         // lane = walker row z = 2 w + re/im of this CTA, column = row s of the
-        // chunk.  With Y = Z / (row scale) / t + h (the Delta_i part scaled back,
-        // h on the real row only) and D = t Delta_j from the FP32 copy:
-        //   real row: D_re Y_re - D_im Y_im,   imaginary row: D_re Y_im + D_im Y_re
-        // (the other component from the partner lane z ^ 1); the g row adds
-        // Z / (row scale) instead.  The lane sum times 1/t is this walker's part.
+        // chunk.  Y = Z / (row scale) / t + h is this lane's component of
+        // Ytil Theta_i (h on the real row only); D = t Delta_j from the FP32
+        // copy (the partner row's value by a shuffle).  Each lane sums
+        //   a1 = sum_s D_own Y,  a2 = sum_s D_other Y
+        // and the walker's part is (a1(re) - a1(im), a2(re) + a2(im)) / t.  The g
+        // row (g . Delta_i) needs no case of its own: the copy holds t in the
+        // real row and 0 in the imaginary row at s = M.
         const int q = warp & 3;                       // TMEM lane quarter
         const int grp = (warp - 2) >> 2;              // column group of 64
         const int ep_tid = threadIdx.x - 64;          // 0..511
         const int z = q * 32 + lane;                  // walker row of this CTA
-        const bool odd = (lane & 1) != 0;             // imaginary component
+        const float hsel = (lane & 1) ? 0.f : 1.f;    // h enters the real row
         const uint32_t even_tmem_empty0 = tc::mapa_shared(&sh.tmem_empty[0], 0);
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        // per-row constants of a unit's chunk into cst[b] (zero past its rows)
+        auto fetch_cst = [&](int u) {
+            float2 k2 = make_float2(0.f, 0.f);
+            if (u < n_units && ep_tid < kBN) {
+                const int ch = u / P.n_wt;
+                const int4 t0 = P.pt[2 * ch], t1 = P.pt[2 * ch + 1];
+                if (ep_tid < (t0.y & 0xffff) + (t1.y & 0xffff)) k2 = __ldg(P.rowc + t0.x + ep_tid);
+            }
+            return k2;
+        };
+        {
+            const float2 k2 = fetch_cst(cid);
+            if (ep_tid < kBN) sh.cst[0][ep_tid] = k2;
+        }
+        asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
         int k = 0;
         for (int u = cid; u < n_units; u += n_cl, ++k) {
             const uint32_t buf = (uint32_t)k & 1u, use = (uint32_t)k >> 1;
             const int ch = u / P.n_wt, wt = u % P.n_wt;
-            const int4 t0 = P.pt[2 * ch], t1 = P.pt[2 * ch + 1];
+            const int4 t0 = P.pt[2 * ch];
             const int Nc = 2 * (t0.y >> 16);
-            const int nvalid = (t0.y & 0xffff) + (t1.y & 0xffff);
             const int cj = (int)(((unsigned)t0.z >> 16) & 0xffu);
             const int s0 = t0.z & 0xffff;
-            const int gcol = P.M - s0;  // local column of the g row (only if inside this chunk)
             const int rb = 2 * wt + (int)rank;
             const int w = wt * kBNW + (int)rank * (kBNW / 2) + (z >> 1);
             const float it = w < P.W ? __ldg(P.inv_t + w) : 0.f;
-            // the chunk's per-row constants (zero beyond its valid rows); the
-            // previous unit's readers are past its closing barrier
-            if (ep_tid < kBN) {
-                float2 k2 = make_float2(0.f, 0.f);
-                if (ep_tid < nvalid) k2 = __ldg(P.rowc + t0.x + ep_tid);
-                sh.cst[ep_tid] = k2;
-            }
-            asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
+            const float2* cst = sh.cst[k & 1];
+            // the next unit's constants, stored after this unit's columns
+            const float2 next_cst = fetch_cst(u + n_cl);
+            const int c_begin = grp * 64;
+            const int nb = c_begin >= Nc ? 0 : min(Nc - c_begin, 64) / 16;  // 16-column batches
+            // this lane's row in the dfull_elem layout: float4 q of the chunk's
+            // columns (s = s0 + c_begin + 4 q ..) at d_own[128 q]
+            const float4* d_own = reinterpret_cast<const float4*>(P.dfull) +
+                                  ((size_t)cj * P.nrb + rb) * (size_t)(P.Sd >> 2) * 128 +
+                                  (size_t)((s0 + c_begin) >> 2) * 128 + z;
+            // the first three batches of Delta_j are requested before the wait for
+            // the MMAs, the fourth once the first is summed: the loads' latency
+            // (microseconds from L2 under the operand copies) runs under the MMAs
+            // instead of between batches (registers allow three in flight)
+            float4 da[3][4];
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int m4 = 0; m4 < 4; ++m4)
+                    da[b][m4] = b < nb ? __ldg(d_own + 128 * (4 * b + m4)) : make_float4(0.f, 0.f, 0.f, 0.f);
             const bool got = tc::mbar_wait_cluster(&sh.tmem_full[buf], use & 1u, abort);
             // leave together: the named barriers below expect every epilogue warp
             if (tc::bar_or(!got, 1, 32 * kLEpiWarps)) break;
             tc::tc_fence_after();
-            const int c_begin = grp * 64;
-            const int nld = c_begin >= Nc ? 0 : (min(Nc - c_begin, 64) + 31) / 32;
-            if (nld == 0) {
+            if (nb == 0) {
                 tc::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive_remote(even_tmem_empty0 + buf * (uint32_t)sizeof(uint64_t));
             }
-            const float* drow = P.dfull + (((size_t)cj * P.nrb + rb) * kBM + z) * P.Sd + s0;
-            float acc = 0.f;
-#pragma unroll 1
-            for (int c2 = 0; c2 < 2 * nld; ++c2) {
-                // 16 columns at a time (registers: the TMEM values and Delta_j)
-                const int col0 = c_begin + 16 * c2;
-                float4 dv4[4];
+            float a1 = 0.f, a2 = 0.f;
 #pragma unroll
-                for (int m4 = 0; m4 < 4; ++m4) dv4[m4] = __ldg(reinterpret_cast<const float4*>(drow + col0) + m4);
+            for (int bi = 0; bi < 4; ++bi) {
+                if (bi >= nb) break;
+                const int col0 = c_begin + 16 * bi;
                 float zv[16];
                 tc::tmem_ld16(tmem + lane_off + buf * kBN + col0, zv);
                 tc::tmem_wait_ld();
-                if (c2 == 2 * nld - 1) {
+                if (bi == nb - 1) {
                     // the last TMEM read of this warp is complete: release the buffer
                     tc::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive_remote(even_tmem_empty0 + buf * (uint32_t)sizeof(uint64_t));
                 }
-                const float* dv = reinterpret_cast<const float*>(dv4);
+                const float* dov = reinterpret_cast<const float*>(da[bi == 3 ? 0 : bi]);
+                const float4* c4 = reinterpret_cast<const float4*>(cst + col0);
 #pragma unroll
-                for (int m = 0; m < 16; ++m) {
-                    const int col = col0 + m;
-                    const float2 k2 = sh.cst[col];  // broadcast
-                    const float y = fmaf(zv[m], k2.x * it, odd ? 0.f : k2.y);
-                    const float yp = __shfl_xor_sync(0xffffffffu, y, 1);
-                    const float d = dv[m];
-                    const float dp = __shfl_xor_sync(0xffffffffu, d, 1);
-                    float v = odd ? fmaf(dp, y, d * yp) : fmaf(d, y, -dp * yp);
-                    v = col == gcol ? zv[m] * k2.x : v;
-                    // columns past the chunk were not written by this unit's MMAs
-                    acc += col < Nc ? v : 0.f;
+                for (int m2 = 0; m2 < 8; ++m2) {
+                    const float4 kk = c4[m2];  // two columns: {1/scale, h, 1/scale, h}
+                    const float y0 = fmaf(zv[2 * m2], kk.x * it, kk.y * hsel);
+                    const float y1 = fmaf(zv[2 * m2 + 1], kk.z * it, kk.w * hsel);
+                    // the partner row's Delta_j (the other component of the walker)
+                    const float o0 = __shfl_xor_sync(0xffffffffu, dov[2 * m2], 1);
+                    const float o1 = __shfl_xor_sync(0xffffffffu, dov[2 * m2 + 1], 1);
+                    a1 = fmaf(dov[2 * m2], y0, a1);
+                    a2 = fmaf(o0, y0, a2);
+                    a1 = fmaf(dov[2 * m2 + 1], y1, a1);
+                    a2 = fmaf(o1, y1, a2);
+                }
+                if (bi == 0 && nb == 4) {
+#pragma unroll
+                    for (int m4 = 0; m4 < 4; ++m4) da[0][m4] = __ldg(d_own + 128 * (12 + m4));
                 }
             }
-            sh.red[grp][z] = acc * it;
+            // this walker's real part from the real row's a1 and the imaginary row's
+            // a1; its imaginary part from both rows' a2
+            const float p1 = __shfl_xor_sync(0xffffffffu, a1, 1);
+            const float p2 = __shfl_xor_sync(0xffffffffu, a2, 1);
+            sh.red[grp][z] = ((lane & 1) ? a2 + p2 : a1 - p1) * it;
             asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
             if (ep_tid < kBNW / 2) {
                 const int wl = wt * kBNW + (int)rank * (kBNW / 2) + ep_tid;
@@ -1271,6 +1301,7 @@ lo_dense_tc_kernel(LoDenseParams P) {
                                   f2d_bits(sh.red[2][2 * ep_tid + 1]) + f2d_bits(sh.red[3][2 * ep_tid + 1]);
                 if (wl < P.W) P.part[(size_t)ch * P.ldp + wl] = make_double2(re, im);
             }
+            if (ep_tid < kBN) sh.cst[(k + 1) & 1][ep_tid] = next_cst;
             asm volatile("bar.sync 1, %0;" :: "n"(32 * kLEpiWarps) : "memory");
         }
     }
