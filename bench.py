@@ -166,19 +166,69 @@ class ClockSampler:
 
 
 PROFILE_TRAFFIC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
-                               "lo_exchange_tc_pentacene_M440_W1024_dram.md")
+                               "lo_dense_tc_naphthalene_M250_W1024.md")
 
 
-def lo_traffic(wl, W, args):
-    """DRAM bytes per launch of the LO kernel from the committed one-pass ncu capture,
-    for the configuration it was taken on (else None)."""
-    if wl is not synth.PENTACENE_440 or W != 1024 or args.threshold != 1e-4 \
-            or args.precision != "fp16x3" or not os.path.exists(PROFILE_TRAFFIC):
+def chunk_geom(k: int):
+    """Balanced chunks of at most 256 rows, a multiple of 16 (the library's rule)."""
+    if k <= 0:
+        return 0, 0
+    nch = (k + 255) // 256
+    return nch, ((k + nch - 1) // nch + 15) // 16 * 16
+
+
+def lo_work(M: int, N: int, msvd, W: int, ntot=None):
+    """Work of the LO exchange split as the library splits it: a pair whose dense
+    block (M + 1 rows) takes fewer MMA columns than its two factor sides runs in
+    the dense kernel.  Flops are real flops per launch over W walkers."""
+    nkb = (M + 63) // 64
+    n_wt = (W + 127) // 128
+    dn, dnc = chunk_geom(M + 1)
+    dense_cols = dn * dnc
+    out = {p: {"method_flops": 0.0, "performed_flops": 0.0, "issued_flops": 0.0, "pairs": 0,
+               "alg_bytes": 0.0} for p in ("dense", "factored")}
+    for k in msvd:
+        k = int(k)
+        fn, fnc = chunk_geom(k)
+        if fn > 0 and dense_cols < 2 * fn * fnc:
+            d = out["dense"]
+            d["performed_flops"] += 4.0 * M * (M + 1) * W
+            d["issued_flops"] += dense_cols * 3 * 2 * 64 * nkb * 256 * n_wt
+            d["alg_bytes"] += dense_cols * 64 * nkb * 2 * 2 + dn * W * 16  # B tiles hi/lo once, partials
+        else:
+            d = out["factored"]
+            d["performed_flops"] += 8.0 * M * k * W
+            d["issued_flops"] += 2 * fn * fnc * 3 * 2 * 64 * nkb * 256 * n_wt
+        d["method_flops"] += 8.0 * M * k * W
+        d["pairs"] += 1
+    if out["dense"]["pairs"]:
+        nt = N if ntot is None else ntot
+        nrb = 2 * n_wt
+        sd = dense_cols + 32
+        # Delta tiles (A operand, hi/lo) and the FP32 Delta copy, each read once
+        out["dense"]["alg_bytes"] += nt * nrb * nkb * 16384 * 2 + nt * nrb * 128 * sd * 4
+    return out
+
+
+def lo_traffic(wl, alg_bytes):
+    """DRAM bytes per launch of the dense LO kernel, scaled from the committed
+    naphthalene-scale ncu capture by the ratio of algorithmic bytes (None if the
+    summary is missing)."""
+    if not os.path.exists(PROFILE_TRAFFIC):
         return None, None
+    vals = {}
     for line in open(PROFILE_TRAFFIC):
-        if line.startswith("traffic_bytes_per_launch"):
-            return float(line.split("=")[1]) / 1e9, "GB per launch, ncu one-pass capture (profiles/)"
-    return None, None
+        if "=" in line and line.split("=")[0].strip() in ("traffic_bytes_per_launch",
+                                                         "algorithmic_bytes_per_launch"):
+            k, v = line.split("=", 1)
+            vals[k.strip()] = float(v)
+    if len(vals) < 2:
+        return None, None
+    if wl is synth.NAPHTHALENE_250:
+        return vals["traffic_bytes_per_launch"] / 1e9, "GB per launch, ncu capture of this case (profiles/)"
+    scaled = vals["traffic_bytes_per_launch"] / vals["algorithmic_bytes_per_launch"] * alg_bytes
+    return scaled / 1e9, ("GB per launch, scaled from the naphthalene-scale ncu capture (profiles/) "
+                          "by algorithmic bytes")
 
 
 def load_peaks():
@@ -329,23 +379,10 @@ def run_ours(args, rank, world, local):
     # ---- roofline of the dominant kernel (live stage timers) ----
     peaks = load_peaks()
     M, N, X = mol.M, mol.n_alpha, mol.X
-    sum_k = int(msvd.sum())
     kernels = {k: v for k, v in prof.items() if k not in ("h2d_walkers", "finalize_d2h")}
     dominant = max(kernels, key=lambda k: kernels[k][0])
     per_launch_ms = {k: v[0] / max(v[1], 1) for k, v in kernels.items()}
-    # algorithmic work per launch (one launch covers the W-walker batch)
-    lo_flops = 8.0 * M * sum_k * W                      # a = Ubar^T Theta_j, b = Vbar Theta_i
-    # issued MMA flops: each pair's ranks in balanced chunks of at most 256
-    # rounded up to 16 (the MMA's N), 64-deep basis blocks, 256 walker rows
-    # (re/im) per 128 walkers, a and b sides, three hi/lo products
-    def chunk_cols(k):
-        if k <= 0:
-            return 0
-        nch = (k + 255) // 256
-        return nch * (((k + nch - 1) // nch + 15) // 16 * 16)
-    rank_cols = sum(chunk_cols(int(k)) for k in msvd)
-    lo_issued = (rank_cols * 2 * 3 * 2 * (64 * ((M + 63) // 64))
-                 * (256 * ((W + 127) // 128)))
+    lo = lo_work(M, N, msvd, W, ntot=N if mol.closed_shell else mol.n_alpha + mol.n_beta)
     coul_flops = 4.0 * (X + 1) * N * M * W            # dJ_g = sum_ir Lbar_gir Delta_ri (complex)
     theta_flops = (4.0 * N * N * M + 8.0 / 3.0 * N ** 3 + 8.0 * M * N * N) * W
     fp64_peak_tflops = 1.25  # nominal B300 FP64 (2 DFMA / clk / SM class figure)
@@ -363,12 +400,26 @@ def run_ours(args, rank, world, local):
                 "frac_of_sustained": ach / peaks["bf16_tflops_sustained"]}
 
     rooflines = {}
-    if "lo_exchange_tc" in per_launch_ms:
-        r = tc_roof("lo_exchange_tc", lo_flops)
-        r["issued_tflops"] = lo_issued / (per_launch_ms["lo_exchange_tc"] / 1e3) / 1e12
+    for name, part in (("lo_dense_tc", "dense"), ("lo_exchange_tc", "factored")):
+        if name not in per_launch_ms:
+            continue
+        w = lo[part]
+        t = per_launch_ms[name] / 1e3
+        # achieved: the method's algorithmic work of these pairs, 8 M K per pair and
+        # walker (a = Ubar^T Theta_j, b = Vbar Theta_i); performed: the flops of the
+        # contraction the kernel runs (dense blocks: 4 M (M + 1)); issued: MMA flops
+        # with three hi/lo products and the padding of chunks and basis blocks
+        r = tc_roof(name, w["method_flops"])
+        r["algorithmic_flops"] = "8 M K per pair and walker (the method's count)"
+        r["performed_tflops"] = w["performed_flops"] / t / 1e12
+        r["performed_frac_of_burst"] = r["performed_tflops"] / peaks["bf16_tflops"]
+        r["issued_tflops"] = w["issued_flops"] / t / 1e12
         r["issued_frac_of_burst"] = r["issued_tflops"] / peaks["bf16_tflops"]
-        r["traffic"], r["traffic_source"] = lo_traffic(wl, W, args)
-        rooflines["lo_exchange_tc"] = r
+        r["pairs"] = w["pairs"]
+        if part == "dense":
+            r["traffic"], r["traffic_source"] = lo_traffic(wl, w["alg_bytes"])
+            r["algorithmic_bytes"] = w["alg_bytes"]
+        rooflines[name] = r
     if "coulomb_tc" in per_launch_ms:
         rooflines["coulomb_tc"] = tc_roof("coulomb_tc", coul_flops)
     if "inverse_df" in per_launch_ms:
