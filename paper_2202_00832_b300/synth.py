@@ -21,7 +21,9 @@ Recipe (all lengths in units of one bond):
     l_pq = 2.0, or the metal length when p or q sits on the metal site;
   * trial per spin = the lowest n_sigma eigenvectors of h (numpy eigh);
   * walker (per spin) = Q of the QR of expm(i eps A) Phi_T with
-    A = (G + G^H)/2, G = (N(0,1) + i N(0,1))/sqrt(2), M x M.
+    A = (G + G^H)/sqrt(2M), G = (N(0,1) + i N(0,1))/sqrt(2), M x M (the
+    Wigner normalisation: A's spectrum lies near [-2, 2], so eps sets the size
+    of the perturbation); raw_gaussian=True uses A = (G + G^H)/2 instead.
 """
 from __future__ import annotations
 
