@@ -71,6 +71,11 @@ def parse():
                          "throughput line: time per 1024 walkers (split precision and FP64) and its roofline")
     ap.add_argument("--cas-report", action="store_true",
                     help="multi-determinant (CAS) trial energy through SMW updates: timing and oracle check")
+    ap.add_argument("--tsvd-workload", default="naphthalene", choices=["naphthalene", "fragments"],
+                    help="T_SVD sweep system: the naphthalene-scale honeycomb or four separate fragments")
+    ap.add_argument("--screen-workload", default="metallocene", choices=["metallocene", "fragments"],
+                    help="screen report system: the metallocene-scale cage (2048 walkers) or four "
+                         "separate fragments (1024 walkers)")
     ap.add_argument("--screen-cutoffs", default="1e-6,1e-3,1e-2,1e-1",
                     help="per-pair cutoffs (Ha) of the screen report")
     return ap.parse_args()
@@ -553,10 +558,11 @@ def run_ours(args, rank, world, local):
 
 
 def screen_report(args):
-    """Learned pair screen (a8) on the metallocene-scale cage (M 500, N 48/47, X 2000):
-    the network is trained on walkers 0-255; at each cutoff the screen's kept pairs,
-    the step time of the screened LO energy against the unscreened one (1024
-    device-resident walkers), and the energy change per walker on held-out walkers
+    """Learned pair screen (a8) on the metallocene-scale cage (M 500, N 48/47, X 2000,
+    2048 device-resident walkers timed) or on four separate fragments (M 480, N 80,
+    X 960, 1024 walkers): the network is trained on walkers 0-255; at each cutoff
+    the screen's kept pairs, the step time of the screened LO energy against the
+    unscreened one, and the energy change per walker on held-out walkers
     against unscreened LO (FP16x3) and against the full FP64 energy.  The bound
     screen keeps a pair when max_w sigma_1 |Theta_i(w)| |Theta_j(w)| over the
     training walkers reaches the cutoff (|e_ij| <= sigma_1 |Theta_i| |Theta_j|)."""
@@ -564,9 +570,9 @@ def screen_report(args):
     from paper_2202_00832_b300.lo_afqmc import Context, init_screen_params, position_operators
 
     torch.cuda.set_device(0)
-    wl = synth.METALLOCENE_500
+    wl = synth.FRAGMENTS_480 if args.screen_workload == "fragments" else synth.METALLOCENE_500
     mol = wl.molecule()
-    W = args.walkers or 1024
+    W = args.walkers or wl.W
     n_train, n_test = 256, 16
     walk = wl.walkers(mol, W=max(W, n_train + n_test), processes=min(16, os.cpu_count() or 1))
     stream = torch.cuda.current_stream()
@@ -719,19 +725,25 @@ def hetero_report(args):
 
 def tsvd_report(args):
     """T_SVD sweep on the naphthalene-scale honeycomb (M 250, N 34, X 1000; 64
-    walkers): per threshold the compression, <M_SVD> (Boys-localized and canonical
-    orbitals), the LO-vs-full error of the FP64 path, the mixed-vs-FP64 LO error,
+    walkers) or four separate fragments: per threshold the compression, <M_SVD>
+    and the M_SVD histogram (Boys-localized and canonical orbitals), the LO-vs-full error of the FP64 path, the mixed-vs-FP64 LO error,
     and the closed-form truncation bound |E_K^LO - E_K| < (mult/2) sum_sigma
     T (sum_i |Theta_i|)^2 (every dropped singular value is below T), checked per
     walker."""
     from paper_2202_00832_b300.lo_afqmc import Context, position_operators
 
-    wl = synth.NAPHTHALENE_250
+    wl = synth.FRAGMENTS_480 if args.tsvd_workload == "fragments" else synth.NAPHTHALENE_250
     mol = wl.molecule()
     walk = wl.walkers(mol, W=64, processes=min(16, os.cpu_count() or 1))
     ctx = Context(0)
     ctx.load_molecule(mol)
     e_full, _, _ = ctx.walkers_energy(walk, mode="full", precision="fp64")
+    # M_SVD histograms (the paper's compression figure, localized against canonical
+    # orbitals): ten bins of M / 10 kept ranks
+    edges = np.linspace(0, mol.M, 11)
+
+    def hist(m):
+        return np.histogram(np.asarray(m), bins=edges)[0].tolist()
     canon = Context(0)
     canon.load_molecule(mol)
     mult = 2.0 if mol.closed_shell else 1.0
@@ -752,6 +764,8 @@ def tsvd_report(args):
         rows.append({
             "t_svd": T, "compression_pct": pct, "mean_m_svd": float(msvd.mean()),
             "canonical_compression_pct": pct_c, "canonical_mean_m_svd": float(msvd_c.mean()),
+            "m_svd_histogram": {"bin_edges": edges.tolist(), "localized": hist(msvd),
+                                "canonical": hist(msvd_c)},
             "lo_vs_full_fp64_mean_mha": float(err.mean() * 1e3), "lo_vs_full_fp64_max_mha": float(err.max() * 1e3),
             "mixed_vs_fp64_lo_max_mha": float(np.abs(e16 - e64).max() * 1e3),
             "bound_max_mha": float(bound.max() * 1e3), "bound_holds_all_walkers": bool(np.all(err <= bound)),

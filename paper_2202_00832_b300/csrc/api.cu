@@ -413,12 +413,13 @@ void energy_batch(loaf_ctx* c, int W, const double2* dphi, int mode, int precisi
     }
 }
 
-// Upload chunks for a host array of W walkers (empty: one piece).  Uploading a
-// walker takes about two thirds of the time computing it takes, so the chunks
-// start small (computing starts early) and grow by about 1.5x, each uploaded
-// while the previous one computes; sizes are whole 128-walker tiles, the last
-// takes the rest.  Even and odd chunks alternate between two device buffers;
-// any two chunks add up to at most W walkers, so both fit in the workspace.
+// Upload chunks for a host array of W walkers (empty: one piece).  At
+// pentacene scale uploading a walker over the host link takes a little longer
+// than computing it (about 10.3 against 8.8 us), so the copies run back to back
+// and a call costs all the copies plus the compute of the last chunk: the
+// chunks are 128 walkers (computing starts early), then 256, and the last one
+// 128 again, each uploaded while the previous one computes.  Even and odd
+// chunks alternate between two device buffers of at most 256 walkers each.
 // Walkers per pass over the pipeline: larger batches run slower per walker at
 // pentacene scale (65.5k walker energies/s at 1024, 60k at 2048 and 4096 on
 // B300), so bigger calls are processed in slices of this size.
@@ -427,14 +428,17 @@ constexpr int kMaxBatch = 1024;
 std::vector<int> host_chunks(int W) {
     std::vector<int> v;
     if (W < 512) return v;
-    int c = std::min(kMaxBatch, ceil_div(ceil_div(W, 8), 128) * 128), rem = W;
-    while (rem > 0) {
-        int take = std::min(c, rem);
-        if (rem - take < 128) take = rem;
-        v.push_back(take);
-        rem -= take;
-        c = std::min(kMaxBatch, ceil_div(c * 3 / 2, 128) * 128);
+    v.push_back(128);
+    int rem = W - 128;
+    while (rem - 256 >= 128) {
+        v.push_back(256);
+        rem -= 256;
     }
+    if (rem > 256) {  // 257 .. 383 left: split so that the last chunk is 128
+        v.push_back(rem - 128);
+        rem = 128;
+    }
+    v.push_back(rem);
     return v;
 }
 

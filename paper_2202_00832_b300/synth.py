@@ -45,6 +45,20 @@ def chain_sites(n_sites: int) -> np.ndarray:
     return x
 
 
+def fragment_sites(n_sites: int, n_frag: int, gap: float) -> np.ndarray:
+    """n_frag chains on the x axis (unit spacing), consecutive chains ``gap``
+    bonds apart; the sites are split as evenly as possible, the first chains
+    taking the remainder."""
+    sizes = [n_sites // n_frag + (1 if f < n_sites % n_frag else 0) for f in range(n_frag)]
+    x = np.zeros((n_sites, 3))
+    k, x0 = 0, 0.0
+    for n in sizes:
+        x[k:k + n, 0] = x0 + np.arange(n, dtype=np.float64)
+        x0 += (n - 1) + gap
+        k += n
+    return x
+
+
 def acene_sites(n_sites: int) -> np.ndarray:
     """A linear acene ribbon (rings fused side by side along x), unit bonds.
 
@@ -143,12 +157,15 @@ def _orbital_sites(n_lig_orb: int, metal_orbitals: int) -> Tuple[np.ndarray, int
 def make_molecule(name: str, M: int, X: int, n_alpha: int, n_beta: int,
                   geometry: str, seed: int, decay: float = 2.0,
                   metal_orbitals: int = 0, metal_decay: float = 4.0,
-                  sphere_radius: float = 3.0, geom_seed: int = 0) -> Molecule:
+                  sphere_radius: float = 3.0, geom_seed: int = 0, n_frag: int = 2,
+                  frag_gap: float = 20.0) -> Molecule:
     """Draw h, L and the trial for one synthetic molecule.
 
-    ``geometry`` is one of "chain", "honeycomb", "acene", "cage".  For "cage"
-    the ligand sites lie on a sphere of ``sphere_radius`` and, when
-    ``metal_orbitals`` > 0, one metal site sits at the centre.
+    ``geometry`` is one of "chain", "honeycomb", "acene", "cage", "fragments".
+    For "cage" the ligand sites lie on a sphere of ``sphere_radius`` and, when
+    ``metal_orbitals`` > 0, one metal site sits at the centre.  "fragments" is
+    ``n_frag`` chains ``frag_gap`` bonds apart (separate molecules in one system:
+    with ``decay`` well below the gap, h and L couple them negligibly).
     """
     n_lig = M - metal_orbitals
     site_of, n_sites = _orbital_sites(n_lig, metal_orbitals)
@@ -160,6 +177,8 @@ def make_molecule(name: str, M: int, X: int, n_alpha: int, n_beta: int,
         pos = honeycomb_patch_sites(n_sites)
     elif geometry == "cage":
         pos = sphere_sites(n_sites, sphere_radius, geom_seed)
+    elif geometry == "fragments":
+        pos = fragment_sites(n_sites, n_frag, frag_gap)
     else:
         raise ValueError(f"unknown geometry {geometry!r}")
     if metal_orbitals:
@@ -207,13 +226,15 @@ def _expm_i_herm_times(A: np.ndarray, eps: float, B: np.ndarray) -> np.ndarray:
 
 
 def _one_walker(trials: Sequence[np.ndarray], eps: float, seed: int,
-                scale_sq: float) -> List[np.ndarray]:
+                scale_sq: float, far: Optional[np.ndarray] = None) -> List[np.ndarray]:
     rng = np.random.default_rng(seed)
     out = []
     M = trials[0].shape[0]
     for T in trials:
         G = (rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M))) / math.sqrt(2.0)
         A = (G + G.conj().T) / math.sqrt(2.0 * M * scale_sq)
+        if far is not None:
+            A[far] = 0.0  # a local perturbation: no coupling beyond the band
         q, _ = np.linalg.qr(_expm_i_herm_times(A, eps, T.astype(np.complex128)))
         out.append(np.ascontiguousarray(q))
     return out
@@ -225,18 +246,23 @@ def _walker_job(args):
 
 def make_walkers(mol: Molecule, W: int, eps: float, seed0: int,
                  first: int = 0, processes: int = 0,
-                 raw_gaussian: bool = False) -> np.ndarray:
+                 raw_gaussian: bool = False, band: Optional[float] = None) -> np.ndarray:
     """Walkers ``first`` .. ``first+W-1`` of a molecule, packed per walker.
 
     Returns a complex128 array of shape (W, M, n_alpha + n_beta) for an open
     shell and (W, M, n_alpha) for a closed shell (one restricted determinant
-    serves both spins).  Walker w uses seed ``seed0 + w``.  ``processes`` > 1
-    spreads the draws over a spawn-started process pool; the result does not
-    depend on it.
+    serves both spins).  Walker w uses seed ``seed0 + w``.  ``band`` (bonds),
+    when given, zeroes A between basis functions whose sites are farther apart
+    (the same draws, a local perturbation).  ``processes`` > 1 spreads the
+    draws over a spawn-started process pool; the result does not depend on it.
     """
     trials = [mol.trial_a] if mol.closed_shell else [mol.trial_a, mol.trial_b]
     scale_sq = 2.0 / mol.M if raw_gaussian else 1.0
-    jobs = [(trials, eps, seed0 + w, scale_sq) for w in range(first, first + W)]
+    far = None
+    if band is not None:
+        xo = mol.pos[mol.site_of]
+        far = np.linalg.norm(xo[:, None, :] - xo[None, :, :], axis=-1) > band
+    jobs = [(trials, eps, seed0 + w, scale_sq, far) for w in range(first, first + W)]
     if processes and processes > 1 and W > 8:
         import multiprocessing as mp
         import os
@@ -276,18 +302,23 @@ class Workload:
     walker_seed: int
     metal_orbitals: int = 0
     geom_seed: int = 0
+    decay: float = 2.0
+    n_frag: int = 2
+    frag_gap: float = 20.0
+    band: Optional[float] = None  # walkers: local perturbation (bonds)
 
     def molecule(self) -> Molecule:
         return make_molecule(self.name, self.M, self.X, self.n_alpha, self.n_beta,
-                             self.geometry, self.seed,
+                             self.geometry, self.seed, decay=self.decay,
                              metal_orbitals=self.metal_orbitals,
-                             geom_seed=self.geom_seed)
+                             geom_seed=self.geom_seed, n_frag=self.n_frag,
+                             frag_gap=self.frag_gap)
 
     def walkers(self, mol: Molecule, W: Optional[int] = None, first: int = 0,
                 processes: int = 0, raw_gaussian: bool = False) -> np.ndarray:
         return make_walkers(mol, self.W if W is None else W, self.eps,
                             self.walker_seed, first=first, processes=processes,
-                            raw_gaussian=raw_gaussian)
+                            raw_gaussian=raw_gaussian, band=self.band)
 
 
 # Workload sizes (M basis functions, N occupied per spin, X Cholesky vectors,
@@ -306,8 +337,15 @@ HETERO_BATCH = [
 METALLOCENE_500 = Workload("cage_M500_Na48_Nb47_X2000", 500, 48, 47, 2000, 2048, 0.1,
                            "cage", 1005, 2005, metal_orbitals=15, geom_seed=3005)
 
+# Separate fragments in one system, for the learned pair screen (Sec. 5): four
+# chains 20 bonds apart with short-range Cholesky vectors (decay 0.5) and walkers
+# perturbed within 3 bonds, so that every pair of orbitals on different
+# fragments contributes below 1e-6 Ha although its truncated block keeps its rank.
+FRAGMENTS_480 = Workload("fragments4_M480_N80_X960", 480, 80, 80, 960, 1024, 0.3, "fragments",
+                         1007, 2007, decay=0.5, n_frag=4, frag_gap=20.0, band=3.0)
+
 WORKLOADS = {w.name: w for w in [CHAIN_60, NAPHTHALENE_250, PENTACENE_440,
-                                 METALLOCENE_500, *HETERO_BATCH]}
+                                 METALLOCENE_500, FRAGMENTS_480, *HETERO_BATCH]}
 
 
 def small_case(M: int, N: int, X: int, W: int, seed: int = 7, eps: float = 0.1,

@@ -78,3 +78,55 @@ def test_training_and_screened_energies(chain_screen):
     ctx.pair_screen_set(-1.0)
     e, _, _ = ctx.walkers_energy(walk, mode="lo", precision="fp16x3")
     assert np.array_equal(e, e_full16)
+
+
+def test_screen_gain_on_separate_fragments():
+    """What the trained screen gains (Sec. 5's proposal): a system of two
+    fragments 20 bonds apart, walkers perturbed within 3 bonds.  Every pair of
+    orbitals on different fragments contributes below 1e-6 Ha, yet its truncated
+    block keeps its rank, so T_SVD cannot drop it.  At the method's 1e-6 Ha cutoff
+    the trained network drops those pairs and keeps every intra-fragment pair;
+    the screened energy equals the unscreened one minus exactly the dropped
+    pairs (FP64), and the oracle's LO energy with the same pairs masked, built
+    from the library's localized orbitals and kept ranks."""
+    from paper_2202_00832_b300 import synth
+    mol = synth.make_molecule("fragments2_M180", 180, 360, 30, 30, "fragments", 1107, decay=0.5,
+                              n_frag=2, frag_gap=20.0)
+    walk = synth.make_walkers(mol, 96, 0.3, 5107, band=3.0)
+    ctx = Context(0)
+    ctx.load_molecule(mol)
+    _, msvd = ctx.lo_localize_compress(1e-4, position_operators(mol), localize=True)
+    n = ctx.num_pairs
+    C = ctx.localized_trial(0)
+    on_first = mol.pos[mol.site_of][:, 0] < 39.0  # basis functions of the first fragment
+    frag = (np.sum(C[on_first] ** 2, axis=0) > 0.5).astype(int)  # fragment of each orbital
+    pairs = [(i, j) for i in range(mol.n_alpha) for j in range(i, mol.n_alpha)]
+    inter = np.array([frag[i] != frag[j] for i, j in pairs])
+    assert inter.sum() == 15 * 15
+    assert np.all(msvd[inter] > 0)  # the truncation keeps these blocks
+    train, test = walk[:64], walk[64:]
+    ctx.pair_screen_train(train, init_screen_params(0), epochs=800, lr=3e-3)
+    ep_train = ctx.walkers_pair_exchange(train, precision="fp64")
+    assert np.abs(ep_train[inter]).max() < 1e-6
+    kept = ctx.pair_screen_set(1e-6)
+    keep = ctx.pair_screen_query()["keep"].astype(bool)
+    assert np.all(keep[~inter]) and not np.any(keep[inter])
+    assert kept == n - inter.sum()
+    wgt = np.array([1.0 if i == j else 2.0 for i, j in pairs])
+    ep = ctx.walkers_pair_exchange(test, precision="fp64")
+    dropped = (wgt[~keep, None] * ep[~keep]).sum(axis=0)
+    assert np.abs(dropped).max() < 1e-6 * wgt[inter].sum()
+    e64_s, _, _ = ctx.walkers_energy(test, mode="lo", precision="fp64")
+    e16_s, _, _ = ctx.walkers_energy(test, mode="lo", precision="fp16x3")
+    ctx.pair_screen_set(-1.0)
+    e64_u, _, _ = ctx.walkers_energy(test, mode="lo", precision="fp64")
+    assert np.max(np.abs(e64_s - (e64_u + dropped)) / np.abs(e64_u)) < 1e-10
+    assert np.abs(e16_s - e64_u).max() < 1e-4
+    # the oracle with the same pairs masked
+    Lbar = E.half_rotate(mol.L, C)
+    ths = np.array([E.theta(C, w) for w in test[:4]])
+    pv = lo.pair_exchange_streamed(Lbar, msvd, ths, workers=4)
+    for k in range(4):
+        full = E.walker_energy(mol, test[k])
+        ref = full["E1"] + full["EJ"] - np.sum((wgt * keep)[:, None] * pv[:, k:k + 1])
+        assert abs(e64_s[k] - ref) < 1e-10 * abs(ref)
