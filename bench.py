@@ -485,7 +485,7 @@ def run_ours(args, rank, world, local):
         # the FP64 pipe (FP16X3_F64INV), and BF16 hi + lo operands (BF16X3)
         if args.precision == "fp16x3":
             variants = {}
-            for prec in ("fp16x3_f64inv", "bf16x3"):
+            for prec in ("fp16x3_f64inv", "bf16x3", "tf32"):
                 ev = torch.zeros_like(e_d)
                 ldv = torch.zeros_like(e_d)
                 for _ in range(2):
@@ -510,7 +510,7 @@ def run_ours(args, rank, world, local):
                     "vs_fp64_lo_mean_mha": float(dv.mean() * 1e3),
                     "logdet_vs_fp16x3_max": float(dld.max()),
                     "stage_ms_per_step": {k: v[0] / args.steps for k, v in vprof.items()
-                                          if k.startswith("inverse")},
+                                          if k.startswith("inverse") or k in ("lo_dense_tc", "coulomb_tc")},
                 }
             extras["precision_variants"] = variants
         # the plain full-exchange FP64 path on the same GPU (subset of walkers)
@@ -760,6 +760,7 @@ def tsvd_report(args):
             bound = mult / 2 * T * (nrm[:, :na].sum(axis=1) ** 2 + nrm[:, na:].sum(axis=1) ** 2)
         e64, _, _ = ctx.walkers_energy(walk, mode="lo", precision="fp64")
         e16, _, _ = ctx.walkers_energy(walk, mode="lo", precision=args.precision)
+        etf, _, _ = ctx.walkers_energy(walk, mode="lo", precision="tf32")
         err = np.abs(e64 - e_full)
         rows.append({
             "t_svd": T, "compression_pct": pct, "mean_m_svd": float(msvd.mean()),
@@ -768,6 +769,9 @@ def tsvd_report(args):
                                 "canonical": hist(msvd_c)},
             "lo_vs_full_fp64_mean_mha": float(err.mean() * 1e3), "lo_vs_full_fp64_max_mha": float(err.max() * 1e3),
             "mixed_vs_fp64_lo_max_mha": float(np.abs(e16 - e64).max() * 1e3),
+            "tf32_vs_fp64_lo_max_mha": float(np.abs(etf - e64).max() * 1e3),
+            "tf32_vs_fp64_lo_mean_mha": float(np.abs(etf - e64).mean() * 1e3),
+            "tf32_vs_full_fp64_max_mha": float(np.abs(etf - e_full).max() * 1e3),
             "bound_max_mha": float(bound.max() * 1e3), "bound_holds_all_walkers": bool(np.all(err <= bound)),
         })
     print(json.dumps({"tsvd_report": {"workload": wl.name, "walkers": len(walk), "precision": args.precision,

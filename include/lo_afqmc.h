@@ -68,8 +68,17 @@ enum { LOAF_MODE_FULL = 0, LOAF_MODE_LO = 1, LOAF_MODE_LO_JK = 2 };
  *   LOAF_PREC_FP16X3_F64INV  LOAF_PREC_FP16X3 with S^-1 and log det S from a
  *                    Gauss-Jordan elimination in FP64 (the overlap inversion
  *                    and log-determinant kept in FP64 end to end).
+ *   LOAF_PREC_TF32   the Coulomb and LO-exchange contractions as one TF32
+ *                    product each (kind::tf32, FP32 accumulation) on the same
+ *                    Theta - Phi_T; overlap, inverse and Theta as for FP16X3;
+ *                    every pair through its dense truncated block.  Mode LO
+ *                    only (walkers_energy, walkers_pair_exchange);
+ *                    LOAF_ERR_UNSUPPORTED elsewhere.  About 11 significant bits
+ *                    per operand: a reference point for the split products,
+ *                    not a production precision.
  */
-enum { LOAF_PREC_FP64 = 0, LOAF_PREC_FP16X3 = 1, LOAF_PREC_BF16X3 = 2, LOAF_PREC_FP16X3_F64INV = 3 };
+enum { LOAF_PREC_FP64 = 0, LOAF_PREC_FP16X3 = 1, LOAF_PREC_BF16X3 = 2, LOAF_PREC_FP16X3_F64INV = 3,
+       LOAF_PREC_TF32 = 4 };
 
 /* Per-walker status codes written to walker_status[] */
 enum { LOAF_WALKER_OK = 0, LOAF_WALKER_SINGULAR = 1, LOAF_WALKER_NAN = 2 };

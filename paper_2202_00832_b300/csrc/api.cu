@@ -121,8 +121,11 @@ void check_ready(loaf_ctx* c, int W, const void* phi, int mode, int precision) {
     LOAF_REQUIRE(mode != LOAF_MODE_LO_JK || c->closed, LOAF_ERR_UNSUPPORTED,
                  "the compressed Coulomb (LO_JK) is defined for closed shells");
     LOAF_REQUIRE(precision == LOAF_PREC_FP64 || precision == LOAF_PREC_FP16X3 ||
-                     precision == LOAF_PREC_BF16X3 || precision == LOAF_PREC_FP16X3_F64INV,
+                     precision == LOAF_PREC_BF16X3 || precision == LOAF_PREC_FP16X3_F64INV ||
+                     precision == LOAF_PREC_TF32,
                  LOAF_ERR_ARG, "unknown precision");
+    LOAF_REQUIRE(precision != LOAF_PREC_TF32 || mode == LOAF_MODE_LO, LOAF_ERR_UNSUPPORTED,
+                 "the TF32 precision is provided for the LO mode");
     LOAF_REQUIRE(mode == LOAF_MODE_FULL || c->compressed, LOAF_ERR_NOT_READY,
                  "LO mode needs lo_localize_compress");
 }
@@ -749,7 +752,7 @@ loaf_status walkers_energy_multi(loaf_ctx* const* ctxs, int n, const int* W, con
                 std::vector<double> work(n);
                 double tot = 0.0;
                 for (int k = 0; k < n; ++k) {
-                    const MixedOps& mx = ctxs[k]->mix[precision == LOAF_PREC_BF16X3 ? 1 : 0];
+                    const MixedOps& mx = ctxs[k]->mix[mix_slot(precision)];
                     work[k] = (double)W[k] * (double)std::max<long>(mx.R, 1) * ctxs[k]->M;
                     tot += work[k];
                 }
@@ -854,6 +857,8 @@ loaf_status walkers_propagator(loaf_ctx* c, int W, const void* x, int precision,
         LOAF_REQUIRE(c->loaded, LOAF_ERR_NOT_READY, "ao_load_cholesky has not been called");
         LOAF_REQUIRE(W >= 1, LOAF_ERR_ARG, "W must be >= 1");
         LOAF_REQUIRE(x != nullptr && v_out != nullptr, LOAF_ERR_ARG, "x or v_out is NULL");
+        LOAF_REQUIRE(precision != LOAF_PREC_TF32, LOAF_ERR_UNSUPPORTED,
+                     "the TF32 precision is provided for the LO energy only");
         LOAF_REQUIRE(precision == LOAF_PREC_FP64 || precision == LOAF_PREC_FP16X3 ||
                          precision == LOAF_PREC_BF16X3 || precision == LOAF_PREC_FP16X3_F64INV,
                      LOAF_ERR_ARG, "unknown precision");

@@ -214,6 +214,7 @@ struct SpinData {
 // planes are padded to r_pad (a multiple of 8) basis functions with zeros.
 struct MixedOps {
     bool coul_ready = false, lo_ready = false, bf16 = false;
+    bool tf32 = false;         // one plane of TF32-rounded FP32 values (tiles of 32-wide basis blocks)
     int r_pad = 0;
     long kflat = 0;            // ntot * r_pad
     // Coulomb operand: rows g < X are mult_sigma * Lbar^sigma_g, row X is
@@ -318,7 +319,7 @@ struct loaf_ctx {
     loaf::DevBuf d_h, d_L;
     loaf::SpinData sp[2];
     std::vector<double> canonical[2];  // trial orbitals as loaded (host)
-    loaf::MixedOps mix[2];             // split-precision operands: [0] FP16, [1] BF16
+    loaf::MixedOps mix[3];             // tensor-core operands: [0] FP16, [1] BF16, [2] TF32
 
     // learned pair screen
     std::vector<double> features;      // 8 descriptors per pair (spins concatenated)
@@ -341,6 +342,7 @@ struct loaf_ctx {
     // zeroed whenever its geometry changes (the columns past M stay zero)
     loaf::DevBuf w_dfull;
     long dfull_key = -1;
+    loaf::DevBuf w_dtf;  // TF32 precision: Delta tiles [c][rb][32-wide block] of FP32 (from w_dfull)
     int trial_version = 0;  // bumped whenever a trial (canonical or localized) is loaded
     int test_withhold = 0;  // LO kernel launches left that withhold a stage (failure-path tests)
 
@@ -393,6 +395,11 @@ __device__ inline double2 cdiv(double2 a, double2 b) {
 }
 
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+// operand set of a tensor-core precision: 0 FP16 hi/lo, 1 BF16 hi/lo, 2 TF32
+inline int mix_slot(int precision) {
+    return precision == LOAF_PREC_BF16X3 ? 1 : (precision == LOAF_PREC_TF32 ? 2 : 0);
+}
 
 // kernels and host stages (defined in the .cu files)
 void run_theta_fp64(loaf_ctx* c, int W, const double2* phi, double2* theta, double2* logdet,

@@ -98,6 +98,41 @@ __global__ void coul_split_kernel(int M, int X, int r_pad, int nspin, SpinRef s0
     if (threadIdx.x == 0) inv[g] = (float)(1.0 / sc);
 }
 
+// FP32 rounded to the nearest TF32 value (10 stored significand bits; ties away
+// from zero): the tensor cores read the upper 19 bits of each operand
+__device__ inline float tf32_round(float x) {
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+    return __uint_as_float(u);
+}
+
+// row g <= X of the Coulomb operand as TF32-rounded FP32 (same rows and scale as
+// coul_split_kernel), rows of r_pad32 values per orbital
+__global__ void coul_tf32_kernel(int M, int X, int r_pad32, int nspin, SpinRef s0, SpinRef s1,
+                                 float* __restrict__ out, float* __restrict__ inv) {
+    __shared__ double red[32];
+    const int g = blockIdx.x;
+    const long kflat = (long)(s0.N + (nspin > 1 ? s1.N : 0)) * r_pad32;
+    double m = 0.0;
+    for (int s = 0; s < nspin; ++s) {
+        const SpinRef sp = s == 0 ? s0 : s1;
+        const double* src = g < X ? sp.Lbar + (size_t)g * sp.N * M : sp.hbar;
+        for (long e = threadIdx.x; e < (long)sp.N * M; e += blockDim.x)
+            m = fmax(m, fabs(sp.mult * src[e]));
+    }
+    const double sc = pow2_scale(block_max(m, red));
+    for (int s = 0; s < nspin; ++s) {
+        const SpinRef sp = s == 0 ? s0 : s1;
+        const double* src = g < X ? sp.Lbar + (size_t)g * sp.N * M : sp.hbar;
+        for (long e = threadIdx.x; e < (long)sp.N * r_pad32; e += blockDim.x) {
+            const int i = (int)(e / r_pad32), r = (int)(e % r_pad32);
+            const double v = r < M ? sp.mult * src[(size_t)i * M + r] * sc : 0.0;
+            out[(size_t)g * kflat + (size_t)(sp.col0 + i) * r_pad32 + r] = tf32_round((float)v);
+        }
+    }
+    if (threadIdx.x == 0) inv[g] = (float)(1.0 / sc);
+}
+
 // J0[g] = sum_sigma mult sum_ir Lbar_gir Phi_ri (g < X); E1_0 at g = X (FP64)
 __global__ void trial_coulomb_kernel(int M, int X, int nspin, SpinRef s0, SpinRef s1,
                                      double* __restrict__ J0) {
@@ -538,8 +573,14 @@ struct CoulPairShared {
 
 // units (row-tile pair, walker tile, split), row-tile pairs fastest; P.n_mt is
 // the padded (even) row-tile count
+// TF32: operands are one plane of FP32 values read as TF32 (tiles of 128 rows x
+// 32 values, the same 16 KB swizzled image), one product per k-step, and a
+// chain of four 32-wide k-chunks keeps 128 terms.
+template <bool TF32>
 __global__ void __launch_bounds__(kCThreads, 1)
 coulomb_tc_pair_kernel(CoulParams P) {
+    constexpr int kGroup = TF32 ? 2 * kCGroup : kCGroup;
+    constexpr uint32_t kStageTx = TF32 ? kTileBytes + kTileBytes / 2 : kCPStageBytes;
     extern __shared__ uint8_t dyn_smem[];
     __shared__ CoulPairShared sh;
     uint8_t* base = align1024(dyn_smem);
@@ -585,14 +626,15 @@ coulomb_tc_pair_kernel(CoulParams P) {
             for (int kc = k0; kc < k1; ++kc) {
                 if (!tc::mbar_wait_cluster(&sh.empty[s], ph ^ 1, abort)) break;
                 uint8_t* st = base + s * kCPStageBytes;
-                tc::mbar_arrive_expect_tx(&sh.full[s], kCPStageBytes);
+                tc::mbar_arrive_expect_tx(&sh.full[s], kStageTx);
                 const int cc = kc / P.nkb, kb = kc - cc * P.nkb;
                 const size_t ao = ((size_t)mt * P.nk + kc) * kTileElems;
                 const size_t bo = (((size_t)cc * P.nrb + wt) * P.nkb + kb) * kTileElems + rank * (kTileElems / 2);
                 tc::bulk_load(st, P.a_hi + ao, kTileBytes, &sh.full[s]);
-                tc::bulk_load(st + kTileBytes, P.a_lo + ao, kTileBytes, &sh.full[s]);
+                if (!TF32) tc::bulk_load(st + kTileBytes, P.a_lo + ao, kTileBytes, &sh.full[s]);
                 tc::bulk_load(st + 2 * kTileBytes, P.b_hi + bo, kTileBytes / 2, &sh.full[s]);
-                tc::bulk_load(st + 2 * kTileBytes + kTileBytes / 2, P.b_lo + bo, kTileBytes / 2, &sh.full[s]);
+                if (!TF32)
+                    tc::bulk_load(st + 2 * kTileBytes + kTileBytes / 2, P.b_lo + bo, kTileBytes / 2, &sh.full[s]);
                 filled |= 1u << s;
                 last_par = (last_par & ~(1u << s)) | (ph << s);
                 if (++s == kCPStages) { s = 0; ph ^= 1; }
@@ -632,12 +674,12 @@ coulomb_tc_pair_kernel(CoulParams P) {
         for (int u = cid; u < n_units && ok && !*abort; u += n_cl) {
             const int sp = u / (n_mp * P.n_wt);
             const int k0 = (int)((long)sp * P.nk / P.n_split), k1 = (int)((long)(sp + 1) * P.nk / P.n_split);
-            for (int g0 = k0; g0 < k1 && ok; g0 += kCGroup, ++gcount) {
+            for (int g0 = k0; g0 < k1 && ok; g0 += kGroup, ++gcount) {
                 const uint32_t b = gcount % kCBufs, use = gcount / kCBufs;
                 if (!tc::mbar_wait_cluster(&sh.acc_empty[b], (use & 1) ^ 1, abort)) { ok = false; break; }
                 tc::tc_fence_after();
                 const uint32_t d = tmem + b * kCBN;
-                const int g1 = min(g0 + kCGroup, k1);
+                const int g1 = min(g0 + kGroup, k1);
                 for (int kc = g0; kc < g1; ++kc) {
                     if (!tc::mbar_wait_cluster(&sh.full[s], ph, abort)) { ok = false; break; }
                     tc::tc_fence_after();
@@ -650,9 +692,13 @@ coulomb_tc_pair_kernel(CoulParams P) {
                         const uint64_t bhi = tc::smem_desc(st + 2 * kTileBytes + off, 128);
                         const uint64_t blo = tc::smem_desc(st + 2 * kTileBytes + kTileBytes / 2 + off, 128);
                         const uint32_t acc = (kc > g0 || kk > 0) ? 1u : 0u;
-                        tc::mma_f16_pair(d, ahi, bhi, P.idesc, acc);
-                        tc::mma_f16_pair(d, ahi, blo, P.idesc, 1u);
-                        tc::mma_f16_pair(d, alo, bhi, P.idesc, 1u);
+                        if (TF32) {
+                            tc::mma_tf32_pair(d, ahi, bhi, P.idesc, acc);
+                        } else {
+                            tc::mma_f16_pair(d, ahi, bhi, P.idesc, acc);
+                            tc::mma_f16_pair(d, ahi, blo, P.idesc, 1u);
+                            tc::mma_f16_pair(d, alo, bhi, P.idesc, 1u);
+                        }
                     }
                     tc::mma_commit_pair(&sh.empty[s], 0x3);
                     if (++s == kCPStages) { s = 0; ph ^= 1; }
@@ -680,7 +726,7 @@ coulomb_tc_pair_kernel(CoulParams P) {
             float* lo = reinterpret_cast<float*>(base + kCPStages * kCPStageBytes) + (threadIdx.x - 64);
 #pragma unroll
             for (int k = 0; k < 32; ++k) { hi[k] = 0.f; lo[k * kCEpiWarps * 32] = 0.f; }
-            for (int g0 = k0; g0 < k1; g0 += kCGroup, ++gcount) {
+            for (int g0 = k0; g0 < k1; g0 += kGroup, ++gcount) {
                 const uint32_t b = gcount % kCBufs, use = gcount / kCBufs;
                 if (!tc::mbar_wait_cluster(&sh.acc_full[b], use & 1, abort)) { ok = false; break; }
                 tc::tc_fence_after();
@@ -1053,8 +1099,12 @@ struct LoDenseShared {
     __align__(16) float2 cst[2][kBN];  // per column of a chunk: {1 / row scale, h}; two units
 };
 
+// TF32: one plane of FP32 values read as TF32 (same tile images, 32-wide basis
+// blocks), one product per k-step.
+template <bool TF32>
 __global__ void __launch_bounds__(kLThreads, 1)
 lo_dense_tc_kernel(LoDenseParams P) {
+    constexpr uint32_t kPlanes = TF32 ? 1u : 2u;
     extern __shared__ uint8_t dyn_smem[];
     __shared__ LoDenseShared sh;
     uint8_t* base = align1024(dyn_smem);
@@ -1107,13 +1157,13 @@ lo_dense_tc_kernel(LoDenseParams P) {
                     continue;
                 }
                 uint8_t* st = base + s * kLSlotBytes;
-                tc::mbar_arrive_expect_tx(&sh.full[s], 2 * wbytes + 2 * kLTileBh);
+                tc::mbar_arrive_expect_tx(&sh.full[s], kPlanes * (wbytes + kLTileBh));
                 const size_t ao = (size_t)(unsigned)t.w + (size_t)kb * H * kTileK;
                 const size_t bo = (((size_t)orb * P.nrb + rb) * P.nk + kb) * kTileElems;
                 tc::bulk_load(st, P.y_hi + ao, wbytes, &sh.full[s]);
-                tc::bulk_load(st + kLTileA, P.y_lo + ao, wbytes, &sh.full[s]);
+                if (!TF32) tc::bulk_load(st + kLTileA, P.y_lo + ao, wbytes, &sh.full[s]);
                 tc::bulk_load(st + 2 * kLTileA, P.d_hi + bo, kLTileBh, &sh.full[s]);
-                tc::bulk_load(st + 2 * kLTileA + kLTileBh, P.d_lo + bo, kLTileBh, &sh.full[s]);
+                if (!TF32) tc::bulk_load(st + 2 * kLTileA + kLTileBh, P.d_lo + bo, kLTileBh, &sh.full[s]);
                 filled |= 1u << s;
                 last_par = (last_par & ~(1u << s)) | (ph << s);
                 if (++s == kLSlots) { s = 0; ph ^= 1; }
@@ -1168,9 +1218,13 @@ lo_dense_tc_kernel(LoDenseParams P) {
                     const uint64_t dlo = tc::smem_desc(st + 2 * kLTileA + kLTileBh + off, 128);
                     const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
                     // A = Delta_i rows (walkers), B = rows of Ytil and g
-                    tc::mma_f16_pair(d, dhi, whi, idesc, acc);
-                    tc::mma_f16_pair(d, dlo, whi, idesc, 1u);
-                    tc::mma_f16_pair(d, dhi, wlo, idesc, 1u);
+                    if (TF32) {
+                        tc::mma_tf32_pair(d, dhi, whi, idesc, acc);
+                    } else {
+                        tc::mma_f16_pair(d, dhi, whi, idesc, acc);
+                        tc::mma_f16_pair(d, dlo, whi, idesc, 1u);
+                        tc::mma_f16_pair(d, dhi, wlo, idesc, 1u);
+                    }
                 }
                 tc::mma_commit_pair(&sh.empty[s], 0x3);
                 if (++s == kLSlots) { s = 0; ph ^= 1; }
@@ -1434,18 +1488,26 @@ SpinRef spin_ref(const SpinData& s) {
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
-void ensure_coulomb_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
+// Row padding of the operand planes in 16-bit units: 16-bit values padded to a
+// multiple of 8, TF32 values (two units each) to a multiple of 4
+inline int plane_pad(int M, bool tf32) { return tf32 ? 2 * ((M + 3) / 4 * 4) : (M + 7) / 8 * 8; }
+
+void ensure_coulomb_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool tf32) {
     if (mx.coul_ready) return;
     mx.bf16 = bf16;
-    mx.r_pad = (c->M + 7) / 8 * 8;
+    mx.tf32 = tf32;
+    mx.r_pad = plane_pad(c->M, tf32);
     mx.kflat = (long)c->ntot * mx.r_pad;
     const int rows = c->X + 1;
     mx.L_hi.ensure((size_t)rows * mx.kflat * 2);
-    mx.L_lo.ensure((size_t)rows * mx.kflat * 2);
+    if (!tf32) mx.L_lo.ensure((size_t)rows * mx.kflat * 2);
     mx.L_inv.ensure((size_t)rows * sizeof(float));
     mx.J0.ensure((size_t)rows * sizeof(double));
     SpinRef s0 = spin_ref(c->sp[0]), s1 = c->nspin > 1 ? spin_ref(c->sp[1]) : s0;
-    if (bf16)
+    if (tf32)
+        coul_tf32_kernel<<<rows, 256, 0, c->stream>>>(c->M, c->X, mx.r_pad / 2, c->nspin, s0, s1,
+                                                     mx.L_hi.as<float>(), mx.L_inv.as<float>());
+    else if (bf16)
         coul_split_kernel<true><<<rows, 256, 0, c->stream>>>(c->M, c->X, mx.r_pad, c->nspin, s0, s1,
                                                             mx.L_hi.as<uint16_t>(), mx.L_lo.as<uint16_t>(),
                                                             mx.L_inv.as<float>());
@@ -1456,23 +1518,26 @@ void ensure_coulomb_ops(loaf_ctx* c, MixedOps& mx, bool bf16) {
     LOAF_LAUNCH_CHECK();
     trial_coulomb_kernel<<<rows, 256, 0, c->stream>>>(c->M, c->X, c->nspin, s0, s1, mx.J0.as<double>());
     LOAF_LAUNCH_CHECK();
-    // operand tiles [mt][c][kb]; the row-major staging planes are then dropped
-    mx.nkb = ceil_div(c->M, kTileK);
+    // operand tiles [mt][c][kb] (a TF32 tile holds 32 basis functions in the same
+    // 16 KB image); the row-major staging planes are then dropped
+    mx.nkb = ceil_div(c->M, tf32 ? kTileK / 2 : kTileK);
     mx.n_mt = ceil_div(rows, kTileRows);
     // an even number of row tiles for the CTA-pair kernel: the last one may be zeros
     const size_t tile_set = (size_t)c->ntot * mx.nkb * kTileBytes;  // one row tile
     const size_t tiles_bytes = (size_t)((mx.n_mt + 1) & ~1) * tile_set;
     mx.Lb_hi.ensure(tiles_bytes);
-    mx.Lb_lo.ensure(tiles_bytes);
+    if (!tf32) mx.Lb_lo.ensure(tiles_bytes);
     if (mx.n_mt & 1) {
         LOAF_CUDA(cudaMemsetAsync(mx.Lb_hi.as<uint8_t>() + mx.n_mt * tile_set, 0, tile_set, c->stream));
-        LOAF_CUDA(cudaMemsetAsync(mx.Lb_lo.as<uint8_t>() + mx.n_mt * tile_set, 0, tile_set, c->stream));
+        if (!tf32)
+            LOAF_CUDA(cudaMemsetAsync(mx.Lb_lo.as<uint8_t>() + mx.n_mt * tile_set, 0, tile_set, c->stream));
     }
     const dim3 tg(mx.n_mt * c->ntot, mx.nkb);
     coul_tiles_kernel<<<tg, 256, 0, c->stream>>>(mx.L_hi.as<uint16_t>(), rows, c->ntot, mx.r_pad, mx.nkb,
                                                 mx.Lb_hi.as<uint16_t>());
-    coul_tiles_kernel<<<tg, 256, 0, c->stream>>>(mx.L_lo.as<uint16_t>(), rows, c->ntot, mx.r_pad, mx.nkb,
-                                                mx.Lb_lo.as<uint16_t>());
+    if (!tf32)
+        coul_tiles_kernel<<<tg, 256, 0, c->stream>>>(mx.L_lo.as<uint16_t>(), rows, c->ntot, mx.r_pad, mx.nkb,
+                                                    mx.Lb_lo.as<uint16_t>());
     LOAF_LAUNCH_CHECK();
     LOAF_CUDA(cudaMemcpyAsync(&mx.E1_0, mx.J0.as<double>() + c->X, sizeof(double),
                               cudaMemcpyDeviceToHost, c->stream));
@@ -1516,6 +1581,38 @@ __global__ void dense_rows_kernel(int M, int r_pad, const double* __restrict__ r
     if (threadIdx.x == 0) rowc[row] = make_float2((float)(1.0 / sc), (float)hrow[row]);
 }
 
+// the same rows as TF32-rounded FP32 (one plane, rows of r_pad32 values)
+__global__ void dense_rows_tf32_kernel(int M, int r_pad32, const double* __restrict__ rows,
+                                       const double* __restrict__ hrow, float* __restrict__ out,
+                                       float2* __restrict__ rowc) {
+    __shared__ double red[32];
+    const long row = blockIdx.x;
+    const double* s = rows + row * M;
+    double m = 0.0;
+    for (int r = threadIdx.x; r < M; r += blockDim.x) m = fmax(m, fabs(s[r]));
+    const double sc = pow2_scale(block_max(m, red));
+    for (int r = threadIdx.x; r < r_pad32; r += blockDim.x)
+        out[row * r_pad32 + r] = tf32_round(r < M ? (float)(s[r] * sc) : 0.f);
+    if (threadIdx.x == 0) rowc[row] = make_float2((float)(1.0 / sc), (float)hrow[row]);
+}
+
+// TF32 Delta tiles [c][rb][kb] (128 walker rows x 32 basis functions, the
+// 128-byte swizzled image) from the FP32 Delta copy: the copy's float4 of four
+// consecutive s of row z is exactly the tile's 16-byte chunk of that row
+__global__ void delta_tf32_tiles_kernel(int nrb, int Sd, int nkb32, const float4* __restrict__ dfull,
+                                        float4* __restrict__ out) {
+    const int tile = blockIdx.x;  // (c * nrb + rb) * nkb32 + kb
+    const int kb = tile % nkb32, crb = tile / nkb32;
+    const float4* src = dfull + ((size_t)crb * (Sd >> 2) + (size_t)kb * 8) * 128;
+    float4* dst = out + (size_t)tile * 1024;
+    for (int q = threadIdx.x; q < 1024; q += blockDim.x) {
+        const int k4 = q >> 7, z = q & 127;
+        float4 v = src[(size_t)k4 * 128 + z];
+        v = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+        dst[z * 8 + (k4 ^ (z & 7))] = v;
+    }
+}
+
 void release_lo(MixedOps& mx) {
     for (DevBuf* b : {&mx.U_hi, &mx.U_lo, &mx.V_hi, &mx.V_lo, &mx.row_c, &mx.pt, &mx.pair_pt0,
                       &mx.pair_npt, &mx.pair_w, &mx.e0, &mx.s_pt, &mx.s_pt0, &mx.s_npt, &mx.s_pw,
@@ -1537,12 +1634,13 @@ void release_lo(MixedOps& mx) {
 // (lo_exchange_tc_kernel); the dense half-tiles come first in the pair lists.
 // Without dense_ok (mode LO_JK) every pair goes through its factors, and the
 // swapped lists of the compressed Coulomb are built too (closed shells).
-void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool dense_ok) {
+void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool tf32, bool dense_ok) {
     if (mx.lo_ready && mx.lo_dense_ok == dense_ok) return;
     if (mx.lo_ready) release_lo(mx);
     mx.bf16 = bf16;
+    mx.tf32 = tf32;
     mx.lo_dense_ok = dense_ok;
-    mx.r_pad = (c->M + 7) / 8 * 8;
+    mx.r_pad = plane_pad(c->M, tf32);
     const int M = c->M;
     long R = 0;
     int npairs = 0;
@@ -1550,11 +1648,13 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool dense_ok) {
     mx.R = R;
     mx.n_pairs = npairs;
     const long Rb = std::max<long>(R, 1);
-    mx.U_hi.ensure((size_t)Rb * mx.r_pad * 2);
-    mx.U_lo.ensure((size_t)Rb * mx.r_pad * 2);
-    mx.V_hi.ensure((size_t)Rb * mx.r_pad * 2);
-    mx.V_lo.ensure((size_t)Rb * mx.r_pad * 2);
-    mx.row_c.ensure((size_t)Rb * sizeof(float4));
+    if (!tf32) {  // the factor planes (TF32 contracts every pair densely)
+        mx.U_hi.ensure((size_t)Rb * mx.r_pad * 2);
+        mx.U_lo.ensure((size_t)Rb * mx.r_pad * 2);
+        mx.V_hi.ensure((size_t)Rb * mx.r_pad * 2);
+        mx.V_lo.ensure((size_t)Rb * mx.r_pad * 2);
+        mx.row_c.ensure((size_t)Rb * sizeof(float4));
+    }
     DevBuf inv_u, inv_v, pbuf, qbuf, pJ, qJ;
     inv_u.ensure(Rb * sizeof(float));
     inv_v.ensure(Rb * sizeof(float));
@@ -1570,7 +1670,7 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool dense_ok) {
     mx.e0.ensure(std::max(npairs, 1) * sizeof(double));
     mx.pair_w.ensure(std::max(npairs, 1) * sizeof(double));
 
-    const int nkb = ceil_div(M, kTileK);
+    const int nkb = ceil_div(M, tf32 ? kTileK / 2 : kTileK);
     const ChunkGeom dg = chunk_geom(M + 1);  // dense: the rows s of Ytil and g
     std::vector<double> pw;
     std::vector<int4> tiles, dtiles;
@@ -1585,7 +1685,9 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool dense_ok) {
         PairTable& pt = sd.pairs;
         if (pt.rows > 0) {
             const size_t o = (size_t)row_base * mx.r_pad;
-            if (bf16) {
+            if (tf32) {
+                // no factor planes: every pair is contracted through its dense block
+            } else if (bf16) {
                 row_split_kernel<true><<<pt.rows, 128, 0, c->stream>>>(M, mx.r_pad, pt.d_U.as<double>(),
                     mx.U_hi.as<uint16_t>() + o, mx.U_lo.as<uint16_t>() + o, inv_u.as<float>() + row_base);
                 row_split_kernel<true><<<pt.rows, 128, 0, c->stream>>>(M, mx.r_pad, pt.d_V.as<double>(),
@@ -1645,7 +1747,7 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool dense_ok) {
             pspin[g] = s;
             plocal[g] = n;
             const ChunkGeom fg = chunk_geom(pt.K[n]);
-            is_dense[g] = dense_ok && fg.nch > 0 && dg.cols() < 2 * fg.cols();
+            is_dense[g] = fg.nch > 0 && (tf32 || (dense_ok && dg.cols() < 2 * fg.cols()));
             pw.push_back(0.5 * sd.mult * (pt.i[n] == pt.j[n] ? 1.0 : 2.0));
         }
         // pair order: 8 x 8 orbital blocks (pairs sharing orbitals run together)
@@ -1709,7 +1811,7 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool dense_ok) {
             }
         npt[g] = cnt;
     }
-    if (R > 0) {
+    if (R > 0 && !tf32) {
         row_consts_kernel<<<ceil_div(R, 256), 256, 0, c->stream>>>(R, inv_u.as<float>(), inv_v.as<float>(),
                                                                  pbuf.as<double>(), qbuf.as<double>(),
                                                                  mx.row_c.as<float4>());
@@ -1796,11 +1898,13 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool dense_ok) {
     for (DevBuf* b : {&mx.U_hi, &mx.U_lo, &mx.V_hi, &mx.V_lo}) b->release();
     // dense blocks: Ytil = Ubar Vbar (rows s), g = Vbar^T p, h = Ubar q in FP64
     // (cuBLAS), split into 16-bit rows with per-row scales, then tiled
+    // columns a chunk's epilogue may read, padded (TF32: the Delta tiles of
+    // every call are cut from the FP32 copy as well, even without a dense pair)
+    mx.Sd = dg.cols() + 32;
     if (n_dense_pairs > 0) {
         const int Kd = M + 1;
-        mx.Sd = dg.cols() + 32;  // columns a chunk's epilogue may read, padded
         mx.Yb_hi.ensure((size_t)doff * sizeof(uint16_t));
-        mx.Yb_lo.ensure((size_t)doff * sizeof(uint16_t));
+        if (!tf32) mx.Yb_lo.ensure((size_t)doff * sizeof(uint16_t));
         mx.rowc_d.ensure((size_t)n_dense_pairs * Kd * sizeof(float2));
         const int batch = std::max(1, std::min(n_dense_pairs, (int)((256L << 20) / ((long)Kd * M * 8))));
         DevBuf ytmp, htmp, plane_hi, plane_lo, btiles;
@@ -1842,7 +1946,10 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool dense_ok) {
             }
             const long rows = (long)nb * Kd;
             const size_t roff = (size_t)b0 * Kd;
-            if (bf16)
+            if (tf32)
+                dense_rows_tf32_kernel<<<rows, 128, 0, c->stream>>>(M, mx.r_pad / 2, ytmp.as<double>(),
+                    htmp.as<double>(), plane_hi.as<float>(), mx.rowc_d.as<float2>() + roff);
+            else if (bf16)
                 dense_rows_kernel<true><<<rows, 128, 0, c->stream>>>(M, mx.r_pad, ytmp.as<double>(), htmp.as<double>(),
                     plane_hi.as<uint16_t>(), plane_lo.as<uint16_t>(), mx.rowc_d.as<float2>() + roff);
             else
@@ -1854,8 +1961,9 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool dense_ok) {
             const dim3 tg((unsigned)bt.size(), mx.nkb);
             lo_tiles_kernel<<<tg, 256, 0, c->stream>>>(plane_hi.as<uint16_t>(), mx.r_pad, mx.nkb,
                                                       btiles.as<int4>(), mx.Yb_hi.as<uint16_t>());
-            lo_tiles_kernel<<<tg, 256, 0, c->stream>>>(plane_lo.as<uint16_t>(), mx.r_pad, mx.nkb,
-                                                      btiles.as<int4>(), mx.Yb_lo.as<uint16_t>());
+            if (!tf32)
+                lo_tiles_kernel<<<tg, 256, 0, c->stream>>>(plane_lo.as<uint16_t>(), mx.r_pad, mx.nkb,
+                                                          btiles.as<int4>(), mx.Yb_lo.as<uint16_t>());
             LOAF_LAUNCH_CHECK();
             LOAF_CUDA(cudaStreamSynchronize(c->stream));  // bt and the batch buffers are reused
         }
@@ -1941,7 +2049,7 @@ int coul_max_clusters(loaf_ctx* c) {
     int dev = 0;
     LOAF_CUDA(cudaGetDevice(&dev));
     if (dev < 64 && cached[dev] > 0) return cached[dev];
-    const int n = max_pair_clusters((const void*)coulomb_tc_pair_kernel, kCThreads, kCoulPairSmem, c->sm_count);
+    const int n = max_pair_clusters((const void*)coulomb_tc_pair_kernel<false>, kCThreads, kCoulPairSmem, c->sm_count);
     LOAF_REQUIRE(n > 0, LOAF_ERR_CUDA, "the Coulomb kernel's CTA pair does not fit on an SM pair");
     if (dev < 64) cached[dev] = n;
     return n;
@@ -1996,7 +2104,7 @@ int lo_dense_max_clusters(loaf_ctx* c) {
     int dev = 0;
     LOAF_CUDA(cudaGetDevice(&dev));
     if (dev < 64 && cached[dev] > 0) return cached[dev];
-    const int n = max_pair_clusters((const void*)lo_dense_tc_kernel, kLThreads, kLoSmem, c->sm_count);
+    const int n = max_pair_clusters((const void*)lo_dense_tc_kernel<false>, kLThreads, kLoSmem, c->sm_count);
     LOAF_REQUIRE(n > 0, LOAF_ERR_CUDA, "the dense LO kernel's CTA pair does not fit on an SM pair");
     if (dev < 64) cached[dev] = n;
     return n;
@@ -2012,24 +2120,26 @@ void coulomb_mixed(loaf_ctx* c, MixedOps& mx, int W, bool bf16, const float* inv
     CoulParams P;
     P.out = nullptr;
     P.wt_fast = 0;
+    // TF32: one plane of operand tiles and the TF32 Delta tiles, 32-wide blocks
     P.a_hi = mx.Lb_hi.as<uint16_t>();
-    P.a_lo = mx.Lb_lo.as<uint16_t>();
-    P.b_hi = c->w_dhi.as<uint16_t>();
-    P.b_lo = c->w_dlo.as<uint16_t>();
-    P.nkb = dg.nkb;
+    P.a_lo = mx.tf32 ? nullptr : mx.Lb_lo.as<uint16_t>();
+    P.b_hi = mx.tf32 ? c->w_dtf.as<uint16_t>() : c->w_dhi.as<uint16_t>();
+    P.b_lo = mx.tf32 ? nullptr : c->w_dlo.as<uint16_t>();
+    P.nkb = mx.tf32 ? mx.nkb : dg.nkb;
     P.nrb = dg.nrb;
     P.rows = c->X + 1;
     P.n_mt = (mx.n_mt + 1) & ~1;  // row-tile pairs (the padding tile is zeros)
     P.n_wt = ceil_div(2L * W, kCBN);
-    P.nk = c->ntot * dg.nkb;
+    P.nk = c->ntot * P.nkb;
     const int tiles = (P.n_mt / 2) * P.n_wt;
     // the split fixes the chain boundaries of the FP32 accumulation, so it depends
     // on the device only (not on an SM budget): results do not depend on scheduling
     // at least 64 k-chunks (32 chains) per unit: every unit ends in an FP64 write of
     // its partial sums, whose cost does not shrink with the unit
-    P.n_split = wave_splits(tiles, std::max(1, std::min(16, P.nk / 64)), c->sm_count / 2);
+    P.n_split = wave_splits(tiles, std::max(1, std::min(16, P.nk / (mx.tf32 ? 128 : 64))), c->sm_count / 2);
     P.ldp = P.n_wt * kCBN;
-    P.idesc = tc::idesc_f16(2 * kBM, kCBN, bf16);  // pair MMA: M = 256, N = 128
+    // pair MMA: M = 256, N = 128
+    P.idesc = mx.tf32 ? tc::idesc_tf32(2 * kBM, kCBN) : tc::idesc_f16(2 * kBM, kCBN, bf16);
     P.err = err;
     c->w_cpart.ensure((size_t)P.n_split * P.rows * P.ldp * sizeof(double));
     P.part = c->w_cpart.as<double>();
@@ -2048,7 +2158,13 @@ void coulomb_mixed(loaf_ctx* c, MixedOps& mx, int W, bool bf16, const float* inv
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     StageScope csc(c, "coulomb_tc", 1);
-    LOAF_CUDA(cudaLaunchKernelEx(&cfg, coulomb_tc_pair_kernel, P));
+    if (mx.tf32) {
+        LOAF_CUDA(cudaFuncSetAttribute(coulomb_tc_pair_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kCoulPairSmem));
+        LOAF_CUDA(cudaLaunchKernelEx(&cfg, coulomb_tc_pair_kernel<true>, P));
+    } else {
+        LOAF_CUDA(cudaLaunchKernelEx(&cfg, coulomb_tc_pair_kernel<false>, P));
+    }
     LOAF_LAUNCH_CHECK();
     csc.end();
     StageScope rsc(c, "coulomb_reduce", 2);
@@ -2099,8 +2215,8 @@ void tc_split_gemm(loaf_ctx* c, const uint16_t* a_hi, const uint16_t* a_lo, int 
 
 void run_force_bias_mixed(loaf_ctx* c, int W, int precision, double2* e_scratch, double2* j_out) {
     const bool bf16 = precision == LOAF_PREC_BF16X3;
-    MixedOps& mx = c->mix[bf16 ? 1 : 0];
-    ensure_coulomb_ops(c, mx, bf16);
+    MixedOps& mx = c->mix[mix_slot(precision)];
+    ensure_coulomb_ops(c, mx, bf16, false);
     float* inv_t = c->w_dscale.as<float>();
     c->w_flag.ensure(16);
     coulomb_mixed(c, mx, W, bf16, inv_t, c->w_flag.as<int>(), e_scratch, j_out);
@@ -2108,26 +2224,25 @@ void run_force_bias_mixed(loaf_ctx* c, int W, int precision, double2* e_scratch,
 
 void setup_mixed_operands(loaf_ctx* c, int mode, bool bf16) {
     MixedOps& mx = c->mix[bf16 ? 1 : 0];
-    ensure_coulomb_ops(c, mx, bf16);
-    if (mode != LOAF_MODE_FULL) ensure_lo_ops(c, mx, bf16, mode == LOAF_MODE_LO);
+    ensure_coulomb_ops(c, mx, bf16, false);
+    if (mode != LOAF_MODE_FULL) ensure_lo_ops(c, mx, bf16, false, mode == LOAF_MODE_LO);
 }
 
 int prepare_lo_operands(loaf_ctx* c, int mode, int precision) {
     if (mode == LOAF_MODE_FULL || precision == LOAF_PREC_FP64) return 0;
-    const bool bf16 = precision == LOAF_PREC_BF16X3;
-    MixedOps& mx = c->mix[bf16 ? 1 : 0];
-    ensure_lo_ops(c, mx, bf16, mode == LOAF_MODE_LO);
-    return mx.n_dpt > 0 ? mx.Sd : 0;
+    const bool bf16 = precision == LOAF_PREC_BF16X3, tf32 = precision == LOAF_PREC_TF32;
+    MixedOps& mx = c->mix[mix_slot(precision)];
+    ensure_lo_ops(c, mx, bf16, tf32, mode == LOAF_MODE_LO);
+    // TF32 cuts its Delta tiles from the FP32 copy, dense pairs or not
+    return (mx.n_dpt > 0 || tf32) ? mx.Sd : 0;
 }
 
 void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2* theta,
                       double2* e_out, double2* e_pairs) {
-    const bool bf16 = precision == LOAF_PREC_BF16X3;
-    MixedOps& mx = c->mix[bf16 ? 1 : 0];
-    if (e_out) ensure_coulomb_ops(c, mx, bf16);
-    if (mode != LOAF_MODE_FULL) ensure_lo_ops(c, mx, bf16, mode == LOAF_MODE_LO);
-    mx.r_pad = (c->M + 7) / 8 * 8;
-    mx.kflat = (long)c->ntot * mx.r_pad;
+    const bool bf16 = precision == LOAF_PREC_BF16X3, tf32 = precision == LOAF_PREC_TF32;
+    MixedOps& mx = c->mix[mix_slot(precision)];
+    if (e_out) ensure_coulomb_ops(c, mx, bf16, tf32);
+    if (mode != LOAF_MODE_FULL) ensure_lo_ops(c, mx, bf16, tf32, mode == LOAF_MODE_LO);
 
     // Delta planes for this batch: formed here from an FP64 Theta, or already
     // written by the tensor-core Theta stage when theta is NULL
@@ -2156,7 +2271,18 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         LOAF_LAUNCH_CHECK();
     }
     // pair MMA: M = 256; N is set per unit from the chunk's rank count
-    const uint32_t idesc = tc::idesc_f16(2 * kBM, kBN, bf16);
+    const uint32_t idesc = tf32 ? tc::idesc_tf32(2 * kBM, kBN) : tc::idesc_f16(2 * kBM, kBN, bf16);
+    if (tf32) {
+        // TF32 Delta tiles of 32-wide basis blocks, cut from the FP32 copy the
+        // Theta stage wrote
+        LOAF_REQUIRE(theta == nullptr, LOAF_ERR_UNSUPPORTED, "the TF32 precision needs the tensor-core Theta stage");
+        const size_t n_tiles = (size_t)c->ntot * dg.nrb * mx.nkb;
+        c->w_dtf.ensure(n_tiles * kTileBytes);
+        StageScope tsc(c, "delta_tf32", 1);
+        delta_tf32_tiles_kernel<<<(unsigned)n_tiles, 256, 0, c->stream>>>(
+            dg.nrb, mx.Sd, mx.nkb, c->w_dfull.as<float4>(), c->w_dtf.as<float4>());
+        LOAF_LAUNCH_CHECK();
+    }
 
     if (e_out) coulomb_mixed(c, mx, W, bf16, inv_t, err, e_out, nullptr);
     if (mode != LOAF_MODE_FULL) {
@@ -2197,9 +2323,9 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
         if (n_dpt > 0) {
             LoDenseParams P;
             P.y_hi = mx.Yb_hi.as<uint16_t>();
-            P.y_lo = mx.Yb_lo.as<uint16_t>();
-            P.d_hi = c->w_dhi.as<uint16_t>();
-            P.d_lo = c->w_dlo.as<uint16_t>();
+            P.y_lo = tf32 ? nullptr : mx.Yb_lo.as<uint16_t>();
+            P.d_hi = tf32 ? c->w_dtf.as<uint16_t>() : c->w_dhi.as<uint16_t>();
+            P.d_lo = tf32 ? nullptr : c->w_dlo.as<uint16_t>();
             P.dfull = c->w_dfull.as<float>();
             P.nrb = dg.nrb;
             P.Sd = mx.Sd;
@@ -2211,7 +2337,7 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             P.n_wt = n_wt;
             P.W = W;
             P.ldp = Wpad;
-            P.nk = dg.nkb;
+            P.nk = tf32 ? mx.nkb : dg.nkb;
             P.M = c->M;
             P.idesc = idesc;
             P.err = err;
@@ -2222,7 +2348,13 @@ void run_energy_mixed(loaf_ctx* c, int W, int mode, int precision, const double2
             cfg.attrs = cl_attr;
             cfg.numAttrs = 1;
             StageScope dsc(c, "lo_dense_tc", 1);
-            LOAF_CUDA(cudaLaunchKernelEx(&cfg, lo_dense_tc_kernel, P));
+            if (tf32) {
+                LOAF_CUDA(cudaFuncSetAttribute(lo_dense_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kLoSmem));
+                LOAF_CUDA(cudaLaunchKernelEx(&cfg, lo_dense_tc_kernel<true>, P));
+            } else {
+                LOAF_CUDA(cudaLaunchKernelEx(&cfg, lo_dense_tc_kernel<false>, P));
+            }
             LOAF_LAUNCH_CHECK();
         }
         // one launch of the factored CTA-pair kernel over a tile list with its

@@ -19,9 +19,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblo_afqmc.so")
 
 MODE_FULL, MODE_LO, MODE_LO_JK = 0, 1, 2
-PREC_FP64, PREC_FP16X3, PREC_BF16X3, PREC_FP16X3_F64INV = 0, 1, 2, 3
+PREC_FP64, PREC_FP16X3, PREC_BF16X3, PREC_FP16X3_F64INV, PREC_TF32 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": PREC_FP64, "fp16x3": PREC_FP16X3, "bf16x3": PREC_BF16X3,
-              "fp16x3_f64inv": PREC_FP16X3_F64INV}
+              "fp16x3_f64inv": PREC_FP16X3_F64INV, "tf32": PREC_TF32}
 MODES = {"full": MODE_FULL, "lo": MODE_LO, "lo_jk": MODE_LO_JK}
 
 STATUS = {0: "LOAF_OK", 1: "LOAF_ERR_ARG", 2: "LOAF_ERR_SHAPE", 3: "LOAF_ERR_CUDA",
