@@ -33,7 +33,7 @@ from paper_2202_00832_b300 import synth  # noqa: E402
 
 METRIC = "walker local-energy evals/sec at pentacene scale"
 WORKLOADS = {"pentacene": synth.PENTACENE_440, "naphthalene": synth.NAPHTHALENE_250,
-             "chain": synth.CHAIN_60}
+             "chain": synth.CHAIN_60, "acene_n73": synth.PROFILE_N73}
 UNIT = "walker-energies/s"
 
 
@@ -174,27 +174,27 @@ PROFILE_TRAFFIC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "prof
                                "lo_dense_tc_naphthalene_M250_W1024.md")
 
 
-def chunk_geom(k: int):
-    """Balanced chunks of at most 256 rows, a multiple of 16 (the library's rule)."""
+def chunk_geom(k: int, cap: int = 256):
+    """Balanced chunks of at most cap rows, a multiple of 16 (the library's rule)."""
     if k <= 0:
         return 0, 0
-    nch = (k + 255) // 256
+    nch = (k + cap - 1) // cap
     return nch, ((k + nch - 1) // nch + 15) // 16 * 16
 
 
-def lo_work(M: int, N: int, msvd, W: int, ntot=None):
+def lo_work(M: int, N: int, msvd, W: int, ntot=None, cap: int = 256):
     """Work of the LO exchange split as the library splits it: a pair whose dense
     block (M + 1 rows) takes fewer MMA columns than its two factor sides runs in
     the dense kernel.  Flops are real flops per launch over W walkers."""
     nkb = (M + 63) // 64
     n_wt = (W + 127) // 128
-    dn, dnc = chunk_geom(M + 1)
+    dn, dnc = chunk_geom(M + 1, cap)
     dense_cols = dn * dnc
     out = {p: {"method_flops": 0.0, "performed_flops": 0.0, "issued_flops": 0.0, "pairs": 0,
                "alg_bytes": 0.0} for p in ("dense", "factored")}
     for k in msvd:
         k = int(k)
-        fn, fnc = chunk_geom(k)
+        fn, fnc = chunk_geom(k, cap)
         if fn > 0 and dense_cols < 2 * fn * fnc:
             d = out["dense"]
             d["performed_flops"] += 4.0 * M * (M + 1) * W
@@ -387,7 +387,8 @@ def run_ours(args, rank, world, local):
     kernels = {k: v for k, v in prof.items() if k not in ("h2d_walkers", "finalize_d2h")}
     dominant = max(kernels, key=lambda k: kernels[k][0])
     per_launch_ms = {k: v[0] / max(v[1], 1) for k, v in kernels.items()}
-    lo = lo_work(M, N, msvd, W, ntot=N if mol.closed_shell else mol.n_alpha + mol.n_beta)
+    lo = lo_work(M, N, msvd, W, ntot=N if mol.closed_shell else mol.n_alpha + mol.n_beta,
+                 cap=ctx.tiles()[0])
     coul_flops = 4.0 * (X + 1) * N * M * W            # dJ_g = sum_ir Lbar_gir Delta_ri (complex)
     theta_flops = (4.0 * N * N * M + 8.0 / 3.0 * N ** 3 + 8.0 * M * N * N) * W
     fp64_peak_tflops = 1.25  # nominal B300 FP64 (2 DFMA / clk / SM class figure)
@@ -705,7 +706,13 @@ def hetero_report(args):
         for c, p, x in zip(ctxs, phis, e):
             c.walkers_energy(p, mode="lo", precision=args.precision, e_out=x)
 
+    # the graph with the library's default tile shapes and SM budgets, then with
+    # the autotuner's choices (tile shapes per system, then SM budgets)
+    walkers_energy_multi(ctxs, phis, e, precision=args.precision, autotune=False)
+    t_default = timed(lambda: walkers_energy_multi(ctxs, phis, e, precision=args.precision, autotune=False))
+    t1 = time.perf_counter()
     caps = walkers_energy_multi(ctxs, phis, e, precision=args.precision, autotune=True)
+    t_tune = time.perf_counter() - t1
     t_multi = timed(lambda: walkers_energy_multi(ctxs, phis, e, precision=args.precision, autotune=True))
     t_seq = timed(sequential)
     walkers_energy_multi(ctxs, phis, e, precision=args.precision, autotune=True)
@@ -714,12 +721,16 @@ def hetero_report(args):
         e64, _, _ = c.walkers_energy(walks[k][:4], mode="lo", precision="fp64")
         info[k]["max_abs_dE_vs_fp64_lo_mha"] = float(np.abs(got - e64).max() * 1e3)
         info[k]["sm_budget"] = caps[k]
+        info[k]["lo_chunk_cap"], info[k]["coulomb_split"] = c.tiles()
     out = {"hetero_report": {
-        "molecules": info, "walkers_total": total_w, "setup_s": t_setup,
+        "molecules": info, "walkers_total": total_w, "setup_s": t_setup, "autotune_s": t_tune,
+        "multi_graph_default_tiles": {"ms_per_batch": t_default,
+                                      "walker_energies_per_s": total_w / (t_default / 1e3)},
         "multi_graph": {"ms_per_batch": t_multi, "walker_energies_per_s": total_w / (t_multi / 1e3)},
         "sequential_calls": {"ms_per_batch": t_seq, "walker_energies_per_s": total_w / (t_seq / 1e3)},
         "speedup": t_seq / t_multi,
-        "sm_budget_note": "0 = the persistent kernels may fill all 148 SMs"}}
+        "sm_budget_note": "0 = the persistent kernels may fill all 148 SMs",
+        "tile_note": "lo_chunk_cap: largest LO chunk (MMA N); coulomb_split 0 = the library's rule"}}
     print(json.dumps(out), flush=True)
 
 

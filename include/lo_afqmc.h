@@ -177,16 +177,42 @@ loaf_status walkers_energy(loaf_ctx *ctx, int W, const void *phi, int mode, int 
                            void *e_out, void *logdet_out, int *walker_status);
 
 /*
+ * loaf_set_tiles / loaf_get_tiles -- tile shapes of the tensor-core kernels of
+ * one context (the paper has no counterpart: its batched contractions of
+ * Sec. 4.4 leave the tiling to the GEMM library).
+ *   lo_chunk_cap   the largest chunk of a pair's rows (kept ranks, or rows of a
+ *                  dense truncated block) one LO unit takes as the MMA's N
+ *                  dimension; a pair's rows are cut into balanced chunks of at
+ *                  most this many (a multiple of 16 each).  A multiple of 32 in
+ *                  [64, 256]; default 256.
+ *   coulomb_split  how many parts the Coulomb contraction over (orbital, basis)
+ *                  is split into across CTA pairs; 0 (default) = the rule that
+ *                  fills the last round of the persistent grid to >= 90 %.
+ * The shapes change only the order of the sums (the split also moves the
+ * boundaries of the 128-term FP32 accumulation chains), not the method.  A new
+ * chunk cap rebuilds the LO operands on the next call.  walkers_energy_multi
+ * with autotune = 1 sets both per context by timing candidates; loaf_get_tiles
+ * reads the shapes in use.  Errors: LOAF_ERR_ARG for a NULL context or a value
+ * out of range (the shapes are left unchanged).
+ */
+loaf_status loaf_set_tiles(loaf_ctx *ctx, int lo_chunk_cap, int coulomb_split);
+loaf_status loaf_get_tiles(const loaf_ctx *ctx, int *lo_chunk_cap, int *coulomb_split);
+
+/*
  * walkers_energy_multi -- local energies of several systems in one launch.
  *
  * The walkers_energy computation (mode LO, precision FP16X3 or BF16X3) for n
  * loaded contexts (for example molecules of different sizes), each with its
  * own batch, recorded once as a single CUDA graph whose branches run side by
  * side and replayed on later calls with the same signature (contexts, sizes,
- * buffers, loaded trial and screen).  With autotune = 1 the first call also
- * chooses how many SMs the persistent kernels of each system may fill (all of
- * them, or shares proportional to each system's LO work) by timing the
- * candidate graphs; sm_caps reports the choice.
+ * buffers, loaded trial, screen and tile shapes).  With autotune = 1 the first
+ * call also chooses, for each system with the GPU to itself, its tile shapes
+ * (loaf_set_tiles: the LO chunk cap among 256, 192 and 128, then the Coulomb
+ * split among the rule's, half and twice it) by timing eager calls, and keeps
+ * them in the context; then how many SMs the persistent kernels of each
+ * system may fill in the graph (all of them, or shares proportional to each
+ * system's LO work) by timing the candidate graphs; sm_caps reports that
+ * choice and loaf_get_tiles the shapes.
  *   ctxs          n distinct contexts on the same device, each after
  *                 lo_localize_compress
  *   W             n batch sizes (>= 1)

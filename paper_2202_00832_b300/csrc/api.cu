@@ -207,6 +207,29 @@ loaf_status loaf_test_withhold_stage(loaf_ctx* c, int n) {
     return LOAF_OK;
 }
 
+loaf_status loaf_set_tiles(loaf_ctx* c, int lo_chunk_cap, int coulomb_split) {
+    if (!c) return LOAF_ERR_ARG;
+    if (lo_chunk_cap < 64 || lo_chunk_cap > 256 || lo_chunk_cap % 32 != 0 || coulomb_split < 0 ||
+        coulomb_split > 64) {
+        c->err = "lo_chunk_cap must be a multiple of 32 in [64, 256] and coulomb_split in [0, 64]";
+        return LOAF_ERR_ARG;
+    }
+    if (c->tile_lo_cap != lo_chunk_cap || c->tile_coul_split != coulomb_split) {
+        c->tile_lo_cap = lo_chunk_cap;
+        c->tile_coul_split = coulomb_split;
+        c->tile_version += 1;
+        forget_plans(c);
+    }
+    return LOAF_OK;
+}
+
+loaf_status loaf_get_tiles(const loaf_ctx* c, int* lo_chunk_cap, int* coulomb_split) {
+    if (!c) return LOAF_ERR_ARG;
+    if (lo_chunk_cap) *lo_chunk_cap = c->tile_lo_cap;
+    if (coulomb_split) *coulomb_split = c->tile_coul_split;
+    return LOAF_OK;
+}
+
 loaf_status loaf_profile_get(const loaf_ctx* c, int idx, const char** name, double* total_ms,
                              long* calls, long* launches) {
     if (!c || idx < 0 || idx >= (int)c->prof.size()) return LOAF_ERR_ARG;
@@ -265,7 +288,7 @@ loaf_status loaf_destroy(loaf_ctx* c) {
                             &c->w_dlo, &c->w_dscale, &c->w_host_stage, &c->w_cpart,
                             &c->w_lopart, &c->w_red, &c->w_flag, &c->d_keep, &c->w_oz_at, &c->w_oz_bs,
                             &c->w_oz_bt, &c->w_oz_S, &c->w_oz_int, &c->w_oz_key, &c->w_prop_x, &c->w_prop_part,
-                            &c->w_dfull})
+                            &c->w_dfull, &c->w_dtf})
         b->release();
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     for (cudaEvent_t e : {c->ev_start, c->ev_copied[0], c->ev_copied[1], c->ev_free[0], c->ev_free[1]})
@@ -530,11 +553,12 @@ namespace {
 
 struct MultiPlan {
     std::vector<loaf_ctx*> ctxs;
-    std::vector<int> W, screen_v, trial_v, caps;
+    std::vector<int> W, screen_v, trial_v, tile_v, caps;
     std::vector<const void*> phi;
     std::vector<void*> e, ld;
     std::vector<int*> st;
     int mode = 0, precision = 0;
+    bool tuned = false;  // recorded after the autotuner chose tile shapes and SM budgets
     // device allocations and frees seen when the graph was recorded: any later
     // one may have moved a buffer the graph holds, and the graph is re-recorded
     unsigned long long alloc_gen = 0;
@@ -555,9 +579,8 @@ struct MultiPlan {
 std::mutex g_multi_mu;
 std::vector<MultiPlan*> g_plans;
 
-// drop every plan that uses context c (it is being destroyed)
-void forget_plans(loaf_ctx* c) {
-    std::lock_guard<std::mutex> lk(g_multi_mu);
+// drop every plan that uses context c (the caller holds g_multi_mu)
+void drop_plans_locked(loaf_ctx* c) {
     for (auto it = g_plans.begin(); it != g_plans.end();) {
         if (std::find((*it)->ctxs.begin(), (*it)->ctxs.end(), c) != (*it)->ctxs.end()) {
             (*it)->release();
@@ -567,6 +590,13 @@ void forget_plans(loaf_ctx* c) {
             ++it;
         }
     }
+}
+
+// drop every plan that uses context c (it is being destroyed, or its tile
+// shapes changed)
+void forget_plans(loaf_ctx* c) {
+    std::lock_guard<std::mutex> lk(g_multi_mu);
+    drop_plans_locked(c);
 }
 
 // The n branches of one multi-system graph: each context's batch on its own
@@ -672,43 +702,103 @@ loaf_status walkers_energy_multi(loaf_ctx* const* ctxs, int n, const int* W, con
         }
         LOAF_CUDA(cudaSetDevice(c0->device));
         std::lock_guard<std::mutex> lk(g_multi_mu);
-        // find the plan of this signature
-        MultiPlan* P = nullptr;
-        for (MultiPlan* q : g_plans) {
-            if ((int)q->ctxs.size() != n || q->mode != mode || q->precision != precision) continue;
-            bool same = true;
-            for (int k = 0; k < n && same; ++k)
-                same = q->ctxs[k] == ctxs[k] && q->W[k] == W[k] && q->phi[k] == phi[k] && q->e[k] == e_out[k] &&
-                       q->ld[k] == (logdet_out ? logdet_out[k] : nullptr) &&
-                       q->st[k] == (walker_status ? walker_status[k] : nullptr) &&
-                       q->screen_v[k] == ctxs[k]->screen_version && q->trial_v[k] == ctxs[k]->trial_version;
-            if (same) { P = q; break; }
-        }
+        // the plan of this signature (contexts, sizes, buffers, loaded trial,
+        // screen and tile shapes), if one was recorded
+        auto find_plan = [&]() -> MultiPlan* {
+            for (MultiPlan* q : g_plans) {
+                if ((int)q->ctxs.size() != n || q->mode != mode || q->precision != precision) continue;
+                if (autotune && !q->tuned) continue;  // a tuned plan is recorded instead
+                bool same = true;
+                for (int k = 0; k < n && same; ++k)
+                    same = q->ctxs[k] == ctxs[k] && q->W[k] == W[k] && q->phi[k] == phi[k] &&
+                           q->e[k] == e_out[k] && q->ld[k] == (logdet_out ? logdet_out[k] : nullptr) &&
+                           q->st[k] == (walker_status ? walker_status[k] : nullptr) &&
+                           q->screen_v[k] == ctxs[k]->screen_version &&
+                           q->trial_v[k] == ctxs[k]->trial_version && q->tile_v[k] == ctxs[k]->tile_version;
+                if (same) return q;
+            }
+            return nullptr;
+        };
+        MultiPlan* P = find_plan();
+        // one eager batch of system k on its context's stream (operands and
+        // workspace are set up on the way; stage timers off)
+        auto run_system = [&](int k) {
+            loaf_ctx* c = ctxs[k];
+            check_ready(c, W[k], phi[k], mode, precision);
+            ensure_workspace(c, W[k], mode);
+            double2* de = c->w_host_stage.as<double2>();
+            double2* dld = de + W[k];
+            int* dst = reinterpret_cast<int*>(dld + W[k]);
+            int* dflags = dst + W[k];
+            const bool prof = c->prof_on;
+            c->prof_on = false;
+            LOAF_CUDA(cudaMemsetAsync(dflags, 0, 2 * sizeof(int), c->stream));
+            energy_batch(c, W[k], static_cast<const double2*>(phi[k]), mode, precision, de, dld, dst,
+                         dflags, dflags + 1);
+            c->prof_on = prof;
+        };
         // an eager pass on each context sets up its operands and workspace, so
         // that recording a graph allocates nothing and waits on nothing
         auto eager_pass = [&] {
             for (int k = 0; k < n; ++k) {
                 loaf_ctx* c = ctxs[k];
-                check_ready(c, W[k], phi[k], mode, precision);
-                ensure_workspace(c, W[k], mode);
                 if (!c->branch_stream) {
                     LOAF_CUDA(cudaStreamCreateWithFlags(&c->branch_stream, cudaStreamNonBlocking));
                     LOAF_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
                     LOAF_CUDA(cudaHostAlloc(&c->h_flags, 2 * sizeof(int), cudaHostAllocDefault));
                 }
-                double2* de = c->w_host_stage.as<double2>();
-                double2* dld = de + W[k];
-                int* dst = reinterpret_cast<int*>(dld + W[k]);
-                int* dflags = dst + W[k];
-                const bool prof = c->prof_on;
-                c->prof_on = false;
-                LOAF_CUDA(cudaMemsetAsync(dflags, 0, 2 * sizeof(int), c->stream));
-                energy_batch(c, W[k], static_cast<const double2*>(phi[k]), mode, precision, de, dld, dst,
-                             dflags, dflags + 1);
+                run_system(k);
                 LOAF_CUDA(cudaStreamSynchronize(c->stream));
-                c->prof_on = prof;
             }
         };
+        // Tile shapes of each system, timed with the GPU to itself: first the
+        // largest LO chunk (the MMA's N: 256, 192, 128) with the Coulomb split of
+        // the rule, then, with the best chunk, half and twice the rule's split.
+        // A shape's result differs from another's only in the order of sums.
+        auto tune_tiles = [&](int k) {
+            loaf_ctx* c = ctxs[k];
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            LOAF_CUDA(cudaEventCreate(&e0));
+            LOAF_CUDA(cudaEventCreate(&e1));
+            auto time_shape = [&](int cap, int split) {
+                c->tile_lo_cap = cap;
+                c->tile_coul_split = split;
+                run_system(k);  // builds the operands of this shape (untimed)
+                LOAF_CUDA(cudaEventRecord(e0, c->stream));
+                for (int r = 0; r < 3; ++r) run_system(k);
+                LOAF_CUDA(cudaEventRecord(e1, c->stream));
+                LOAF_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                LOAF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                return ms;
+            };
+            int best_cap = 256, best_split = 0;
+            float best = time_shape(256, 0);
+            for (int cap : {192, 128}) {
+                const float ms = time_shape(cap, 0);
+                if (ms < best) { best = ms; best_cap = cap; }
+            }
+            const int rule = coulomb_split_rule(c, W[k], precision);
+            for (int split : {rule / 2, std::min(2 * rule, 16)}) {
+                if (split < 1 || split == rule) continue;
+                const float ms = time_shape(best_cap, split);
+                if (ms < best) { best = ms; best_split = split; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            c->tile_lo_cap = best_cap;
+            c->tile_coul_split = best_split;
+            c->tile_version += 1;
+            drop_plans_locked(c);  // recorded with the previous shapes
+            LOAF_CUDA(cudaStreamSynchronize(c->stream));
+        };
+        if (!P && autotune) {
+            // first call of this signature with the autotuner: tile shapes per
+            // system (a new signature, since the tile versions change)
+            eager_pass();
+            for (int k = 0; k < n; ++k) tune_tiles(k);
+            P = find_plan();
+        }
         if (P && P->alloc_gen != devbuf_generation().load()) {
             // a buffer of some context may have moved since the graph was
             // recorded (another call grew a workspace, a setup call rebuilt the
@@ -736,6 +826,7 @@ loaf_status walkers_energy_multi(loaf_ctx* const* ctxs, int n, const int* W, con
                 P->st.push_back(walker_status ? walker_status[k] : nullptr);
                 P->screen_v.push_back(ctxs[k]->screen_version);
                 P->trial_v.push_back(ctxs[k]->trial_version);
+                P->tile_v.push_back(ctxs[k]->tile_version);
             }
             P->mode = mode;
             P->precision = precision;
@@ -779,6 +870,7 @@ loaf_status walkers_energy_multi(loaf_ctx* const* ctxs, int n, const int* W, con
             }
             for (int k = 0; k < n; ++k) ctxs[k]->prof_on = prof[k];
             P->alloc_gen = devbuf_generation().load();
+            P->tuned = autotune != 0;
         }
         LOAF_CUDA(cudaGraphLaunch(P->exec, P->stream));
         LOAF_CUDA(cudaStreamSynchronize(P->stream));

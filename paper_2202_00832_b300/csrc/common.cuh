@@ -249,6 +249,7 @@ struct MixedOps {
     // densely; their half-tiles (B rows: Ytil rows s, then g = Vbar^T p) come
     // first in pair_pt0.  lo_dense_ok records which plan the LO operands hold.
     bool lo_dense_ok = false;
+    int chunk_cap = 0;         // largest chunk (MMA N) the LO operands were cut with
     int n_dpt = 0;             // dense half-tiles
     int Sd = 0;                // s-extent of the FP32 Delta copy the dense kernel reads
     DevBuf dpt, Yb_hi, Yb_lo;  // dense half-tile list {row0, nvalid | H << 16, ci << 24 | cj << 16 | s0, offset}, B tiles
@@ -302,6 +303,13 @@ struct loaf_ctx {
     // SMs the persistent tensor-core kernels of this context may fill (0: all);
     // set by the multi-system launch so that several systems share the GPU
     int grid_cap = 0;
+    // tile shapes of the tensor-core kernels (loaf_set_tiles; the multi-system
+    // autotuner sets them per context): the largest LO chunk, i.e. the MMA's N
+    // (a multiple of 32 in [64, 256]), and the Coulomb k-split (0: the rule that
+    // fills the last round of the persistent grid)
+    int tile_lo_cap = 256;
+    int tile_coul_split = 0;
+    int tile_version = 0;  // bumped whenever the tile shapes change
     int persistent_grid() const { return grid_cap > 0 ? std::min(grid_cap, sm_count) : sm_count; }
     // multi-system launches: a private branch stream, fork/join events, pinned flags
     cudaStream_t branch_stream = nullptr;
@@ -435,6 +443,7 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision, int Sd 
 // LO operands of the mode (LO: rank-adaptive, LO_JK: factored); returns the
 // s-extent of the FP32 Delta copy the dense kernel reads (0: no dense pair)
 int prepare_lo_operands(loaf_ctx* c, int mode, int precision);
+int coulomb_split_rule(loaf_ctx* c, int W, int precision);
 void setup_load(loaf_ctx* c, int M, int X, const double* h, const double* L, int na, int nb,
                 const double* ta, const double* tb, double e0, int on_device);
 void setup_compress(loaf_ctx* c, double t_svd, const double* r_ops, int n_ops, int localize,

@@ -1547,16 +1547,17 @@ void ensure_coulomb_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool tf32) {
     mx.coul_ready = true;
 }
 
-// rank chunks of a list of K rows: ceil(K / 256) balanced chunks of Nc rows
-// (a multiple of 16, the MMA's N), two half-tiles of Nc / 2 rows each
+// rank chunks of a list of K rows: ceil(K / cap) balanced chunks of Nc rows
+// (a multiple of 16, the MMA's N, at most cap <= 256), two half-tiles of Nc / 2
+// rows each
 struct ChunkGeom {
     int nch = 0, Nc = 0;
     int cols() const { return nch * Nc; }
 };
-inline ChunkGeom chunk_geom(int K) {
+inline ChunkGeom chunk_geom(int K, int cap) {
     ChunkGeom g;
     if (K <= 0) return g;
-    g.nch = (K + 255) / 256;
+    g.nch = (K + cap - 1) / cap;
     g.Nc = ((K + g.nch - 1) / g.nch + 15) / 16 * 16;
     return g;
 }
@@ -1635,11 +1636,13 @@ void release_lo(MixedOps& mx) {
 // Without dense_ok (mode LO_JK) every pair goes through its factors, and the
 // swapped lists of the compressed Coulomb are built too (closed shells).
 void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool tf32, bool dense_ok) {
-    if (mx.lo_ready && mx.lo_dense_ok == dense_ok) return;
+    if (mx.lo_ready && mx.lo_dense_ok == dense_ok && mx.chunk_cap == c->tile_lo_cap) return;
     if (mx.lo_ready) release_lo(mx);
     mx.bf16 = bf16;
     mx.tf32 = tf32;
     mx.lo_dense_ok = dense_ok;
+    const int cap = c->tile_lo_cap;
+    mx.chunk_cap = cap;
     mx.r_pad = plane_pad(c->M, tf32);
     const int M = c->M;
     long R = 0;
@@ -1671,7 +1674,7 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool tf32, bool dense_o
     mx.pair_w.ensure(std::max(npairs, 1) * sizeof(double));
 
     const int nkb = ceil_div(M, tf32 ? kTileK / 2 : kTileK);
-    const ChunkGeom dg = chunk_geom(M + 1);  // dense: the rows s of Ytil and g
+    const ChunkGeom dg = chunk_geom(M + 1, cap);  // dense: the rows s of Ytil and g
     std::vector<double> pw;
     std::vector<int4> tiles, dtiles;
     std::vector<int> pt0(npairs), npt(npairs);
@@ -1746,7 +1749,7 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool tf32, bool dense_o
             prow[g] = row_base + pt.off[n];
             pspin[g] = s;
             plocal[g] = n;
-            const ChunkGeom fg = chunk_geom(pt.K[n]);
+            const ChunkGeom fg = chunk_geom(pt.K[n], cap);
             is_dense[g] = fg.nch > 0 && (tf32 || (dense_ok && dg.cols() < 2 * fg.cols()));
             pw.push_back(0.5 * sd.mult * (pt.i[n] == pt.j[n] ? 1.0 : 2.0));
         }
@@ -1795,11 +1798,11 @@ void ensure_lo_ops(loaf_ctx* c, MixedOps& mx, bool bf16, bool tf32, bool dense_o
         pt0[g] = n_dpt + (int)tiles.size();
         int cnt = 0;
         const int cij = ((sd.col0 + pt.i[n]) << 16) | (sd.col0 + pt.j[n]);
-        // the pair's ranks in balanced chunks of at most 256 (the MMA's N, a
+        // the pair's ranks in balanced chunks of at most cap (the MMA's N, a
         // multiple of 16); each chunk is two half-tiles of H = N / 2 rows, one
         // per CTA of the pair, stored at element offset woff
         const int K = pt.K[n];
-        const ChunkGeom fg = chunk_geom(K);
+        const ChunkGeom fg = chunk_geom(K, cap);
         const int H = fg.Nc / 2;
         for (int ch = 0; ch < fg.nch; ++ch)
             for (int hf = 0; hf < 2; ++hf) {
@@ -2072,6 +2075,11 @@ int wave_splits(int tiles, int max_split, int slots) {
     return best;
 }
 
+// the largest Coulomb k-split: at least 64 k-chunks (32 chains) per unit, since
+// every unit ends in an FP64 write of its partial sums, whose cost does not
+// shrink with the unit
+int coul_max_split(int nk, bool tf32) { return std::max(1, std::min(16, nk / (tf32 ? 128 : 64))); }
+
 // CTA pairs of the LO kernel that fit on the GPU at once (the persistent grid):
 // clusters sit inside a GPC, so this can be below half the SM count
 int lo_max_clusters(loaf_ctx* c) {
@@ -2133,10 +2141,10 @@ void coulomb_mixed(loaf_ctx* c, MixedOps& mx, int W, bool bf16, const float* inv
     P.nk = c->ntot * P.nkb;
     const int tiles = (P.n_mt / 2) * P.n_wt;
     // the split fixes the chain boundaries of the FP32 accumulation, so it depends
-    // on the device only (not on an SM budget): results do not depend on scheduling
-    // at least 64 k-chunks (32 chains) per unit: every unit ends in an FP64 write of
-    // its partial sums, whose cost does not shrink with the unit
-    P.n_split = wave_splits(tiles, std::max(1, std::min(16, P.nk / (mx.tf32 ? 128 : 64))), c->sm_count / 2);
+    // on the device and the context's tile shapes only (not on an SM budget):
+    // results do not depend on scheduling
+    P.n_split = c->tile_coul_split > 0 ? std::min(c->tile_coul_split, P.nk)
+                                        : wave_splits(tiles, coul_max_split(P.nk, mx.tf32), c->sm_count / 2);
     P.ldp = P.n_wt * kCBN;
     // pair MMA: M = 256, N = 128
     P.idesc = mx.tf32 ? tc::idesc_tf32(2 * kBM, kCBN) : tc::idesc_f16(2 * kBM, kCBN, bf16);
@@ -2226,6 +2234,16 @@ void setup_mixed_operands(loaf_ctx* c, int mode, bool bf16) {
     MixedOps& mx = c->mix[bf16 ? 1 : 0];
     ensure_coulomb_ops(c, mx, bf16, false);
     if (mode != LOAF_MODE_FULL) ensure_lo_ops(c, mx, bf16, false, mode == LOAF_MODE_LO);
+}
+
+// the k-split rule for W walkers once the Coulomb operands exist (0 before)
+int coulomb_split_rule(loaf_ctx* c, int W, int precision) {
+    const MixedOps& mx = c->mix[mix_slot(precision)];
+    if (!mx.coul_ready) return 0;
+    const DeltaGeom dg = delta_geom(c->M, c->ntot, W);
+    const int nk = c->ntot * (mx.tf32 ? mx.nkb : dg.nkb);
+    const int tiles = (((mx.n_mt + 1) & ~1) / 2) * ceil_div(2L * W, kCBN);
+    return wave_splits(tiles, coul_max_split(nk, mx.tf32), c->sm_count / 2);
 }
 
 int prepare_lo_operands(loaf_ctx* c, int mode, int precision) {

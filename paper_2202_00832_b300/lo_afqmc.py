@@ -55,6 +55,8 @@ SIGNATURES = [
     ("pair_screen_query", _I, [_P, _P, _P, _P, _P, _P]),
     ("mlp_loss_grad", _I, [_I, _I, _P, _P, _P, _P, _P]),
     ("loaf_test_withhold_stage", _I, [_P, _I]),
+    ("loaf_set_tiles", _I, [_P, _I, _I]),
+    ("loaf_get_tiles", _I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     ("loaf_profile", _I, [_P, _I]),
     ("loaf_profile_count", _I, [_P]),
     ("loaf_profile_get", _I, [_P, _I, ctypes.POINTER(ctypes.c_char_p),
@@ -210,6 +212,20 @@ class Context:
         """Failure-path test hook: the next n LO tensor-core launches leave one
         pipeline stage unfilled, so their bounded waits run out (LOAF_ERR_TIMEOUT)."""
         self._check(self._lib.loaf_test_withhold_stage(self._h, int(n)), "loaf_test_withhold_stage")
+
+    # -- tile shapes ----------------------------------------------------------
+    def set_tiles(self, lo_chunk_cap: int = 256, coulomb_split: int = 0):
+        """Largest LO chunk (the MMA's N, a multiple of 32 in [64, 256]) and the
+        Coulomb k-split (0: the library's rule) of this context's kernels."""
+        self._check(self._lib.loaf_set_tiles(self._h, int(lo_chunk_cap), int(coulomb_split)),
+                    "loaf_set_tiles")
+
+    def tiles(self) -> tuple:
+        """(lo_chunk_cap, coulomb_split) in use (split 0: the library's rule)."""
+        cap, split = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.loaf_get_tiles(self._h, ctypes.byref(cap), ctypes.byref(split)),
+                    "loaf_get_tiles")
+        return cap.value, split.value
 
     # -- stage timers ---------------------------------------------------------
     def profile(self, enable: bool = True):
@@ -384,7 +400,8 @@ def mlp_loss_grad(x, t, params, device: int = 0):
 def walkers_energy_multi(ctxs, phis, e_outs, logdet_outs=None, statuses=None, mode="lo",
                          precision="fp16x3", autotune: bool = True):
     """Energies of several systems in one graph launch (device tensors only).
-    Returns the SM budget chosen for each system (0 = the whole GPU)."""
+    Returns the SM budget chosen for each system (0 = the whole GPU); with
+    autotune the tile shapes chosen per system are read by Context.tiles()."""
     lib = load_library()
     n = len(ctxs)
     for a in phis:

@@ -328,6 +328,9 @@ NAPHTHALENE_250 = Workload("honeycomb_M250_N34_X1000", 250, 34, 34, 1000, 512, 0
                            "honeycomb", 1002, 2002)
 PENTACENE_440 = Workload("acene_M440_N73_X1800", 440, 73, 73, 1800, 1024, 0.1,
                          "acene", 1003, 2003)
+# a small system with the pentacene-scale occupied count (N = 73, five column
+# slots of the inverse kernels) and 1024 walkers, for kernel profiles
+PROFILE_N73 = Workload("acene_M220_N73_X440", 220, 73, 73, 440, 1024, 0.1, "acene", 1060, 2060)
 HETERO_BATCH = [
     Workload(f"acene_M{M}_N{N}_X{X}", M, N, N, X, W, 0.1, "acene", 1040 + k, 2040 + 10000 * k)
     for k, (M, N, X, W) in enumerate([(100, 14, 400, 512), (180, 25, 720, 512),
@@ -344,7 +347,7 @@ METALLOCENE_500 = Workload("cage_M500_Na48_Nb47_X2000", 500, 48, 47, 2000, 2048,
 FRAGMENTS_480 = Workload("fragments4_M480_N80_X960", 480, 80, 80, 960, 1024, 0.3, "fragments",
                          1007, 2007, decay=0.5, n_frag=4, frag_gap=20.0, band=3.0)
 
-WORKLOADS = {w.name: w for w in [CHAIN_60, NAPHTHALENE_250, PENTACENE_440,
+WORKLOADS = {w.name: w for w in [CHAIN_60, NAPHTHALENE_250, PENTACENE_440, PROFILE_N73,
                                  METALLOCENE_500, FRAGMENTS_480, *HETERO_BATCH]}
 
 

@@ -59,6 +59,8 @@ def test_null_arguments_return_status(lib):
     assert lib.walkers_energy(None, 1, None, 0, 0, None, None, None) == 1
     assert lib.loaf_destroy(None) == 0
     assert lib.loaf_num_pairs(None) == 0
+    assert lib.loaf_set_tiles(None, 256, 0) == 1
+    assert lib.loaf_get_tiles(None, None, None) == 1
     assert b"null" in lib.loaf_last_error(None)
 
 

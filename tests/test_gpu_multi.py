@@ -1,9 +1,9 @@
 """Several systems in one graph launch (walkers_energy_multi) against each
 system's own walkers_energy call and the FP64 LO path, through the C ABI.
 
-The graph runs the same kernels; with the autotuned SM budgets the Coulomb
-contraction may be split differently, which changes only the summation order,
-so per-walker energies agree to 1e-9 relative.  Against the FP64 LO path the
+The graph runs the same kernels with the same tile shapes (the autotuner keeps
+its choice in each context) and differs only in scheduling, so per-walker
+energies agree to 1e-9 relative.  Against the FP64 LO path the
 bar is the mixed-precision 0.1 mHa.
 """
 import numpy as np
@@ -53,6 +53,11 @@ def test_multi_matches_single_calls(systems):
     e, ld, st = _outs(phis)
     caps = walkers_energy_multi(ctxs, phis, e, ld, st, autotune=True)
     assert len(caps) == 3 and all(c >= 0 for c in caps)
+    # tile shapes chosen per system among the autotuner's candidates; the single
+    # calls below run with the same shapes
+    for c in ctxs:
+        cap, split = c.tiles()
+        assert cap in (256, 192, 128) and 0 <= split <= 16
     for k, (c, (mol, walk)) in enumerate(zip(ctxs, sys_)):
         e1, ld1, st1 = c.walkers_energy(walk, mode="lo", precision="fp16x3")
         got = e[k].cpu().numpy()
