@@ -373,6 +373,16 @@ __device__ __forceinline__ double f2d_bits(float x) {
     return e == 0 ? 0.0 : __longlong_as_double((long long)bits);
 }
 
+// two columns at once: the same operations on the two lanes of sm_100 FP32x2
+// instructions (the _rn forms are never contracted)
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void two_sum_acc2(float2& hi, float2& lo, float2 x) {
+    const float2 s = __fadd2_rn(hi, x);
+    const float2 bp = __fadd2_rn(s, neg2(hi));
+    const float2 e = __fadd2_rn(__fadd2_rn(hi, neg2(__fadd2_rn(s, neg2(bp)))), __fadd2_rn(x, neg2(bp)));
+    hi = s;
+    lo = __fadd2_rn(lo, e);
+}
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
     const float s = hi + x;
     const float bp = s - hi;
@@ -711,7 +721,7 @@ coulomb_tc_pair_kernel(CoulParams P) {
         volatile int never = 0;
         tc::mbar_wait(&sh.drain, 0, &never);
     } else if (warp >= 2) {
-        // ---------------- epilogue (both CTAs): as in coulomb_tc_kernel ----------------
+        // ---------------- epilogue (both CTAs) ----------------
         const int q = warp & 3;          // TMEM lane quarter
         const int h = (warp - 2) >> 2;   // column block: 32 columns per warp
         const uint32_t even_acc_empty0 = tc::mapa_shared(&sh.acc_empty[0], 0);
@@ -721,11 +731,13 @@ coulomb_tc_pair_kernel(CoulParams P) {
             const int mp = u % n_mp, wt = (u / n_mp) % P.n_wt, sp = u / (n_mp * P.n_wt);
             const int mt = 2 * mp + (int)rank;
             const int k0 = (int)((long)sp * P.nk / P.n_split), k1 = (int)((long)(sp + 1) * P.nk / P.n_split);
-            // hi in registers, lo in shared memory ([column][epilogue thread])
-            float hi[32];
-            float* lo = reinterpret_cast<float*>(base + kCPStages * kCPStageBytes) + (threadIdx.x - 64);
+            // the double-float sums of this thread's 32 columns as 16 column pairs
+            // (column 2k in .x, 2k + 1 in .y): hi in registers, lo in shared memory
+            // ([pair][epilogue thread], 8-byte accesses)
+            float2 hi[16];
+            float2* lo = reinterpret_cast<float2*>(base + kCPStages * kCPStageBytes) + (threadIdx.x - 64);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) { hi[k] = 0.f; lo[k * kCEpiWarps * 32] = 0.f; }
+            for (int k = 0; k < 16; ++k) { hi[k] = make_float2(0.f, 0.f); lo[k * kCEpiWarps * 32] = make_float2(0.f, 0.f); }
             for (int g0 = k0; g0 < k1; g0 += kGroup, ++gcount) {
                 const uint32_t b = gcount % kCBufs, use = gcount / kCBufs;
                 if (!tc::mbar_wait_cluster(&sh.acc_full[b], use & 1, abort)) { ok = false; break; }
@@ -737,8 +749,11 @@ coulomb_tc_pair_kernel(CoulParams P) {
                     tc::tmem_ld16(taddr + part * 16, v);
                     tc::tmem_wait_ld();
 #pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        two_sum_acc(hi[part * 16 + k], lo[(part * 16 + k) * kCEpiWarps * 32], v[k]);
+                    for (int k = 0; k < 8; ++k) {
+                        float2 l = lo[(part * 8 + k) * kCEpiWarps * 32];
+                        two_sum_acc2(hi[part * 8 + k], l, make_float2(v[2 * k], v[2 * k + 1]));
+                        lo[(part * 8 + k) * kCEpiWarps * 32] = l;
+                    }
                 }
                 tc::tc_fence_before();
                 __syncwarp();
@@ -751,9 +766,10 @@ coulomb_tc_pair_kernel(CoulParams P) {
                     P.part + ((size_t)sp * P.rows + g) * P.ldp + (size_t)wt * kCBN + h * 32);
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    dst[k] = make_double2(f2d_bits(hi[2 * k]) + f2d_bits(lo[(2 * k) * kCEpiWarps * 32]),
-                                          f2d_bits(hi[2 * k + 1]) +
-                                              f2d_bits(lo[(2 * k + 1) * kCEpiWarps * 32]));
+                {
+                    const float2 l = lo[k * kCEpiWarps * 32];
+                    dst[k] = make_double2(f2d_bits(hi[k].x) + f2d_bits(l.x), f2d_bits(hi[k].y) + f2d_bits(l.y));
+                }
             }
         }
     }
