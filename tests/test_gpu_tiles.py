@@ -83,3 +83,20 @@ def test_bad_shapes_rejected(case, cap, split):
     assert ex.value.status == "LOAF_ERR_ARG"
     assert ctx.tiles() == (192, 2)
     ctx.set_tiles(256, 0)
+
+
+def test_open_shell_shapes():
+    """Open shell (both spins' pair lists cut with the same shapes): a small chunk
+    cap and an explicit split against the FP64 LO path and the default shapes."""
+    mol, walk = synth.small_case(M=160, N=21, X=220, W=70, seed=212, geometry="acene", n_beta=18)
+    ctx = Context(0)
+    ctx.load_molecule(mol)
+    ctx.lo_localize_compress(1e-3, position_operators(mol), localize=True)
+    e64, _, _ = ctx.walkers_energy(walk, mode="lo", precision="fp64")
+    ref, _, st = ctx.walkers_energy(walk, mode="lo", precision="fp16x3")
+    assert np.all(st == 0)
+    ctx.set_tiles(96, 5)
+    e, _, st = ctx.walkers_energy(walk, mode="lo", precision="fp16x3")
+    assert np.all(st == 0)
+    assert np.abs(e - e64).max() < TOL_MIXED
+    assert np.abs(e - ref).max() < 1e-5
