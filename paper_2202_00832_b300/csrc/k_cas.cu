@@ -253,14 +253,42 @@ struct CasParams {
     const double2* PL;          // [W][R][C]
     const double2* PR;          // [W][R][C]
     const double2* PJ;          // [W][X + 1][Nc][C]; plane X: hbar Theta^0
+    const double2* G;           // [walker - w0][pair][C][C]: sum over the pair's rows of PL[c1] PR[c2]
+    int w0;                     // first walker of this launch
+    int npairs;
     double e0;
     double2* Ed;                // [W][n_det]
     double2* rd;                // [W][n_det]
 };
 
+// The pair Gram blocks of the exchange (the determinant-independent
+// intermediates of the table of Sec. 3.1.2): for every stored CAS orbital pair
+// n = [ab] and walker, G_n[c1][c2] = sum over the pair's kept ranks of
+// (Ubar^[ab]T Theta^0)[c1] (Vbar^[ab] Theta^0)[c2], c1, c2 over the projected
+// columns.  A determinant's pair value (Ubar^T Q^d_t) . (Vbar Q^d_s) is then a
+// bilinear form in G with the SMW coefficients S_d (eq. BigQ), so the ranks
+// are summed once per walker instead of once per determinant.
+// grid (pairs, walkers of the slice), threads over (c1, c2)
+__global__ void cas_pair_gram_kernel(int C, const long* __restrict__ off, const int* __restrict__ K,
+                                     const double2* __restrict__ PL, const double2* __restrict__ PR, long R,
+                                     int npairs, int w0, double2* __restrict__ G) {
+    const int n = blockIdx.x, ws = blockIdx.y, w = w0 + ws;
+    const long o = off[n];
+    const int Kn = K[n];
+    const double2* pl = PL + ((size_t)w * R + o) * C;
+    const double2* pr = PR + ((size_t)w * R + o) * C;
+    double2* g = G + ((size_t)ws * npairs + n) * C * C;
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+        const int c1 = e / C, c2 = e - c1 * C;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int kk = 0; kk < Kn; ++kk) acc = zmad(acc, pl[(size_t)kk * C + c1], pr[(size_t)kk * C + c2]);
+        g[e] = acc;
+    }
+}
+
 // one CTA per (determinant, walker): S_d, the overlap ratio and E_d
 __global__ void __launch_bounds__(kCasThreads) cas_det_energy_kernel(CasParams P) {
-    const int d = blockIdx.x, w = blockIdx.y, tid = threadIdx.x;
+    const int d = blockIdx.x, ws = blockIdx.y, w = P.w0 + ws, tid = threadIdx.x;
     const int N = P.N, Nc = P.Nc;
     __shared__ int occ[kCasMaxN], slot[kCasMaxExc], neworb[kCasMaxExc], oldorb[kCasMaxExc];
     __shared__ int s_k, s_sing;
@@ -373,23 +401,31 @@ __global__ void __launch_bounds__(kCasThreads) cas_det_energy_kernel(CasParams P
     // exchange: sum_{s,t} (Ubar^[ij]T Q_t) . (Vbar^[ij] Q_s), (i, j) = (occ_s, occ_t);
     // for i > j the [ji] factors with U and V exchanged (Y^[ij] = Y^[ji]T).  In
     // both cases the Ubar rows of the stored pair (a, b) = (min, max) meet the
-    // column of b's slot and the Vbar rows that of a's slot.
-    const double2* PLw = P.PL + (size_t)w * P.R * Cc;
-    const double2* PRw = P.PR + (size_t)w * P.R * Cc;
+    // column of b's slot and the Vbar rows that of a's slot.  With Q_t = col_t -
+    // sum_e col(slot_e) S[e][t] on both sides, the sum over the pair's ranks is
+    //   G(ct, cs) - sum_f S[f][s] G(ct, c_f) - sum_e S[e][t] G(c_e, cs)
+    //   + sum_{e,f} S[e][t] S[f][s] G(c_e, c_f)
+    // with G the pair's Gram block (transposed for i > j), ct = col of slot t,
+    // c_e = col of the e-th changed slot.
+    const double2* Gw = P.G + (size_t)ws * P.npairs * Cc * Cc;
     double2 ek = make_double2(0.0, 0.0);
     for (int e = tid; e < N * N; e += blockDim.x) {
         const int s = e / N, t = e - s * N;
         const int i = occ[s], j = occ[t];
         const int n = P.pair_id[(size_t)min(i, j) * Nc + max(i, j)];
-        const double2* Lside = i <= j ? PLw : PRw;
-        const double2* Rside = i <= j ? PRw : PLw;
-        const long o = P.off[n];
-        const int K = P.K[n];
-        for (int kk = 0; kk < K; ++kk) {
-            const double2 qL = qcol(Lside + (size_t)(o + kk) * Cc, t);
-            const double2 qR = qcol(Rside + (size_t)(o + kk) * Cc, s);
-            ek = zmad(ek, qL, qR);
+        const double2* g = Gw + (size_t)n * Cc * Cc;
+        const bool fwd = i <= j;
+        auto gat = [&](int cl, int cr) { return fwd ? g[cl * Cc + cr] : g[cr * Cc + cl]; };
+        const int ct = scol[t], cs = scol[s];
+        double2 v = gat(ct, cs);
+        for (int f = 0; f < k; ++f) v = zsub(v, zmul(S[f][s], gat(ct, scol[slot[f]])));
+        for (int e2 = 0; e2 < k; ++e2) {
+            const int ce = scol[slot[e2]];
+            double2 inner = gat(ce, cs);
+            for (int f = 0; f < k; ++f) inner = zsub(inner, zmul(S[f][s], gat(ce, scol[slot[f]])));
+            v = zsub(v, zmul(S[e2][t], inner));
         }
+        ek = zadd(ek, v);
     }
     ek = block_sum2(ek, red);
     if (tid == 0) {
@@ -474,8 +510,12 @@ void run_energy_cas(loaf_ctx* c, int W, int N, const double2* phi, int n_det, co
     const size_t per_w = (size_t)Nc * N + (size_t)N * N + (size_t)M * N + 2 * (size_t)R * C +
                          (size_t)(X + 1) * Nc * C + 2 * (size_t)n_det + 1;
     const size_t n_int = (size_t)n_det * N + 1 + pid.size() + row_pair.size() + var_slot.size() + N + Nc + 8;
-    c->w_cas.ensure((size_t)W * per_w * sizeof(double2) + (size_t)n_det * sizeof(double) + n_int * sizeof(int) +
-                    4096);
+    // pair Gram blocks for a slice of walkers at a time (at most 512 MB of them)
+    const int npairs = pt.npairs;
+    const size_t g_per_w = (size_t)std::max(npairs, 1) * C * C;
+    const int Ws = (int)std::max<size_t>(1, std::min<size_t>((size_t)W, ((size_t)512 << 20) / (g_per_w * sizeof(double2))));
+    c->w_cas.ensure((size_t)W * per_w * sizeof(double2) + (size_t)Ws * g_per_w * sizeof(double2) +
+                    (size_t)n_det * sizeof(double) + n_int * sizeof(int) + 4096);
     double2* B = c->w_cas.as<double2>();
     double2* Ainv = B + (size_t)W * Nc * N;
     double2* th0 = Ainv + (size_t)W * N * N;
@@ -485,7 +525,8 @@ void run_energy_cas(loaf_ctx* c, int W, int N, const double2* phi, int n_det, co
     double2* Ed = PJ + (size_t)W * (X + 1) * Nc * C;
     double2* rd = Ed + (size_t)W * n_det;
     double2* ldA = rd + (size_t)W * n_det;
-    double* d_coeffs = reinterpret_cast<double*>(ldA + W);
+    double2* Gbuf = ldA + W;
+    double* d_coeffs = reinterpret_cast<double*>(Gbuf + (size_t)Ws * g_per_w);
     int* d_dets = reinterpret_cast<int*>(d_coeffs + n_det);
     int* d_pid = d_dets + (size_t)n_det * N;
     int* d_row_pair = d_pid + pid.size();
@@ -502,7 +543,7 @@ void run_energy_cas(loaf_ctx* c, int W, int N, const double2* phi, int n_det, co
     up(d_var, var_slot.data(), var_slot.size() * sizeof(int));
     up(d_slot_col, slot_col.data(), (size_t)N * sizeof(int));
     up(d_fixed, fixed_slot.data(), (size_t)Nc * sizeof(int));
-    StageScope sc(c, "cas_energy", R > 0 ? 9 : 7);
+    StageScope sc(c, "cas_energy", (R > 0 ? 7 : 5) + 2 * ceil_div(W, Ws));
     cas_overlap_kernel<<<dim3(W, Nc), 64, 0, c->stream>>>(M, Nc, N, sp.d_trial.as<double>(), phi, B);
     LOAF_LAUNCH_CHECK();
     const size_t smem = (size_t)(N * N + N) * sizeof(double2);
@@ -535,8 +576,18 @@ void run_energy_cas(loaf_ctx* c, int W, int N, const double2* phi, int n_det, co
     P.M = M; P.N = N; P.Nc = Nc; P.X = X; P.n_det = n_det; P.R = R; P.C = C; P.slot_col = d_slot_col;
     P.dets = d_dets; P.pair_id = d_pid; P.K = pt.d_K.as<int>(); P.off = pt.d_off.as<long>();
     P.B = B; P.Ainv = Ainv; P.PL = PL; P.PR = PR; P.PJ = PJ; P.e0 = c->e0; P.Ed = Ed; P.rd = rd;
-    cas_det_energy_kernel<<<dim3(n_det, W), kCasThreads, 0, c->stream>>>(P);
-    LOAF_LAUNCH_CHECK();
+    P.G = Gbuf; P.npairs = npairs;
+    for (int w0 = 0; w0 < W; w0 += Ws) {
+        const int wn = std::min(Ws, W - w0);
+        if (npairs > 0) {
+            cas_pair_gram_kernel<<<dim3(npairs, wn), 128, 0, c->stream>>>(C, pt.d_off.as<long>(), pt.d_K.as<int>(),
+                                                                        PL, PR, R, npairs, w0, Gbuf);
+            LOAF_LAUNCH_CHECK();
+        }
+        P.w0 = w0;
+        cas_det_energy_kernel<<<dim3(n_det, wn), kCasThreads, 0, c->stream>>>(P);
+        LOAF_LAUNCH_CHECK();
+    }
     cas_combine_kernel<<<ceil_div(W, 128), 128, 0, c->stream>>>(W, n_det, d_coeffs, Ed, rd, ldA, status_dev, e_dev,
                                                                 logov_dev);
     LOAF_LAUNCH_CHECK();
