@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblo_afqmc.so")
 SOURCES = ["api.cu", "setup.cu", "k_theta.cu", "k_fp64.cu", "k_tc.cu", "k_mlp.cu", "k_ozaki.cu",
            "k_prop.cu", "k_cas.cu"]
-HEADERS = ["common.cuh", "tc_ptx.cuh", "split16.cuh"]
+HEADERS = ["common.cuh", "tc_ptx.cuh", "split16.cuh", "dfloat.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -19,6 +19,7 @@
 //   (eq. BigQ), which gives E1, E_J and E_K of the determinant;
 //   E = sum_d c_d r_d^2 E_d / sum_d c_d r_d^2 (closed shell: r_d^2).
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace loaf {
 
@@ -208,35 +209,91 @@ __global__ void cas_theta_kernel(int M, int N, const double2* __restrict__ phi, 
 //   out[w * out_stride + row C + c] = sum_r F[row][r] Theta^0[w][r][slot(row, c)]
 // The row's orbital: mode 0, orbital b of its pair (Ubar rows), mode 1,
 // orbital a (Vbar rows), mode 2, row mod Nc (Lbar and hbar rows).
-__global__ void cas_project_kernel(int M, int N, int C, long rows, const double* __restrict__ F,
-                                   const double2* __restrict__ th0, double2* __restrict__ out,
-                                   size_t out_stride, int mode, int Nc, const int* __restrict__ row_pair,
-                                   const int* __restrict__ pa, const int* __restrict__ pb,
-                                   const int* __restrict__ fixed_slot, const int* __restrict__ var_slot) {
-    const int w = blockIdx.y;
-    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= rows * C) return;
-    const long row = e / C;
-    const int c = (int)(e - row * C);
-    int s;
-    if (c > 0) {
-        s = var_slot[c - 1];
-    } else {
-        const int orb = mode == 0 ? pb[row_pair[row]] : mode == 1 ? pa[row_pair[row]] : (int)(row % Nc);
-        s = fixed_slot[orb];
-    }
-    double2 acc = make_double2(0.0, 0.0);
-    if (s >= 0) {
-        const double* f = F + row * M;
-        const double2* t = th0 + (size_t)w * M * N + s;
-        for (int r = 0; r < M; ++r) {
-            const double cf = f[r];
-            const double2 v = t[(size_t)r * N];
-            acc.x = fma(cf, v.x, acc.x);
-            acc.y = fma(cf, v.y, acc.y);
+// Computed on the FP32 pipe in double-float (about 48 significant bits: the
+// FP64 results to ~1e-14 relative, at B300's FP32 rate instead of its FP64
+// rate, about 1/64 of it).  A CTA takes 64 rows and kProjW walkers; the
+// factor rows and the walkers' Theta^0 rows are staged kProjRB at a time in
+// shared memory, split into hi + lo as they are stored.  Each thread keeps the
+// double-float sums of one (row, walker) for up to kProjC columns at a time.
+constexpr int kProjRows = 64, kProjW = 4, kProjRB = 16, kProjC = 8;
+__global__ void __launch_bounds__(kProjRows * kProjW)
+cas_project_df_kernel(int M, int N, int C, long rows, int W, const double* __restrict__ F,
+                      const double2* __restrict__ th0, double2* __restrict__ out, size_t out_stride, int mode,
+                      int Nc, const int* __restrict__ row_pair, const int* __restrict__ pa,
+                      const int* __restrict__ pb, const int* __restrict__ fixed_slot,
+                      const int* __restrict__ var_slot) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    // strides padded so that the 4 walkers' and the 8 rows' values of a warp's
+    // loads fall in different banks
+    const int th_w = kProjRB * N + 1;                                                  // float4 per walker
+    float4* th = reinterpret_cast<float4*>(sm);                                        // [kProjW][kProjRB][N]
+    float2* fs = reinterpret_cast<float2*>(th + (size_t)kProjW * th_w);                // [kProjRows][kProjRB + 1]
+    const int tid = threadIdx.x;
+    const int wq = tid % kProjW, rl = tid / kProjW;
+    const int w0 = blockIdx.y * kProjW;
+    const int nw = min(kProjW, W - w0);
+    const long row0 = (long)blockIdx.x * kProjRows;
+    const long row = row0 + rl;
+    const bool active = row < rows && wq < nw;
+    int orb = 0;
+    if (active) orb = mode == 0 ? pb[row_pair[row]] : mode == 1 ? pa[row_pair[row]] : (int)(row % Nc);
+    for (int cb = 0; cb < C; cb += kProjC) {
+        int sl[kProjC];
+#pragma unroll
+        for (int q = 0; q < kProjC; ++q) {
+            const int c = cb + q;
+            sl[q] = c >= C ? -1 : (c > 0 ? var_slot[c - 1] : fixed_slot[orb]);
+        }
+        dfl are[kProjC], aim[kProjC];
+#pragma unroll
+        for (int q = 0; q < kProjC; ++q) { are[q] = dfl{0.f, 0.f}; aim[q] = dfl{0.f, 0.f}; }
+        for (int r0 = 0; r0 < M; r0 += kProjRB) {
+            const int nr = min(kProjRB, M - r0);
+            __syncthreads();  // the previous block's reads are done
+            for (int e = tid; e < kProjW * nr * N; e += blockDim.x) {
+                const int ww = e / (nr * N), rem = e - ww * nr * N;
+                const int r = rem / N, sidx = rem - r * N;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ww < nw) {
+                    const double2 z = th0[((size_t)(w0 + ww) * M + r0 + r) * N + sidx];
+                    const dfl a = df_split_bits(z.x), b = df_split_bits(z.y);
+                    v = make_float4(a.hi, a.lo, b.hi, b.lo);
+                }
+                th[(size_t)ww * th_w + r * N + sidx] = v;
+            }
+            for (int e = tid; e < kProjRows * nr; e += blockDim.x) {
+                const int rr = e / nr, r = e - rr * nr;
+                float2 v = make_float2(0.f, 0.f);
+                if (row0 + rr < rows) {
+                    const dfl a = df_split_bits(F[(size_t)(row0 + rr) * M + r0 + r]);
+                    v = make_float2(a.hi, a.lo);
+                }
+                fs[rr * (kProjRB + 1) + r] = v;
+            }
+            __syncthreads();
+            if (active) {
+                const float4* thw = th + (size_t)wq * th_w;
+                for (int r = 0; r < nr; ++r) {
+                    const float2 f2 = fs[rl * (kProjRB + 1) + r];
+                    const dfl fv{f2.x, f2.y};
+#pragma unroll
+                    for (int q = 0; q < kProjC; ++q) {
+                        if (sl[q] < 0) continue;
+                        const float4 t = thw[r * N + sl[q]];
+                        are[q] = df_fma(fv, dfl{t.x, t.y}, are[q]);
+                        aim[q] = df_fma(fv, dfl{t.z, t.w}, aim[q]);
+                    }
+                }
+            }
+        }
+        if (active) {
+#pragma unroll
+            for (int q = 0; q < kProjC; ++q) {
+                const int c = cb + q;
+                if (c < C) out[(size_t)(w0 + wq) * out_stride + (size_t)row * C + c] = make_double2(df_to(are[q]), df_to(aim[q]));
+            }
         }
     }
-    out[(size_t)w * out_stride + e] = acc;
 }
 
 struct CasParams {
@@ -554,24 +611,22 @@ void run_energy_cas(loaf_ctx* c, int W, int N, const double2* phi, int n_det, co
     LOAF_LAUNCH_CHECK();
     const int* pa = pt.d_i.as<int>();
     const int* pb = pt.d_j.as<int>();
-    if (R > 0) {
-        cas_project_kernel<<<dim3(ceil_div(R * C, 256), W), 256, 0, c->stream>>>(
-            M, N, C, R, pt.d_U.as<double>(), th0, PL, (size_t)R * C, 0, Nc, d_row_pair, pa, pb, d_fixed, d_var);
+    const size_t proj_smem = (size_t)kProjW * (kProjRB * N + 1) * sizeof(float4) +
+                             (size_t)kProjRows * (kProjRB + 1) * sizeof(float2);
+    LOAF_CUDA(cudaFuncSetAttribute(cas_project_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)proj_smem));
+    auto project = [&](const double* F, long rows, double2* out, size_t stride, int mode) {
+        if (rows <= 0) return;
+        cas_project_df_kernel<<<dim3(ceil_div(rows, kProjRows), ceil_div(W, kProjW)), kProjRows * kProjW, proj_smem,
+                                c->stream>>>(M, N, C, rows, W, F, th0, out, stride, mode, Nc, d_row_pair, pa, pb,
+                                             d_fixed, d_var);
         LOAF_LAUNCH_CHECK();
-        cas_project_kernel<<<dim3(ceil_div(R * C, 256), W), 256, 0, c->stream>>>(
-            M, N, C, R, pt.d_V.as<double>(), th0, PR, (size_t)R * C, 1, Nc, d_row_pair, pa, pb, d_fixed, d_var);
-        LOAF_LAUNCH_CHECK();
-    }
+    };
+    project(pt.d_U.as<double>(), R, PL, (size_t)R * C, 0);
+    project(pt.d_V.as<double>(), R, PR, (size_t)R * C, 1);
     // planes g < X: Lbar_g Theta^0 (the X Nc Lbar rows are contiguous); plane X: hbar Theta^0
     const size_t pj_stride = (size_t)(X + 1) * Nc * C;
-    cas_project_kernel<<<dim3(ceil_div((long)X * Nc * C, 256), W), 256, 0, c->stream>>>(
-        M, N, C, (long)X * Nc, sp.d_Lbar.as<double>(), th0, PJ, pj_stride, 2, Nc, d_row_pair, pa, pb, d_fixed,
-        d_var);
-    LOAF_LAUNCH_CHECK();
-    cas_project_kernel<<<dim3(ceil_div((long)Nc * C, 256), W), 256, 0, c->stream>>>(
-        M, N, C, Nc, sp.d_hbar.as<double>(), th0, PJ + (size_t)X * Nc * C, pj_stride, 2, Nc, d_row_pair, pa, pb,
-        d_fixed, d_var);
-    LOAF_LAUNCH_CHECK();
+    project(sp.d_Lbar.as<double>(), (long)X * Nc, PJ, pj_stride, 2);
+    project(sp.d_hbar.as<double>(), Nc, PJ + (size_t)X * Nc * C, pj_stride, 2);
     CasParams P;
     P.M = M; P.N = N; P.Nc = Nc; P.X = X; P.n_det = n_det; P.R = R; P.C = C; P.slot_col = d_slot_col;
     P.dets = d_dets; P.pair_id = d_pid; P.K = pt.d_K.as<int>(); P.off = pt.d_off.as<long>();
