@@ -266,7 +266,8 @@ loaf_status walkers_propagator(loaf_ctx *ctx, int W, const void *x, int precisio
  * walkers_energy_cas -- mixed-estimate local energy with a multi-determinant
  * (CAS) trial sum_d c_d |Phi_d>, through Sherman-Morrison-Woodbury updates of
  * the reference determinant (Sec. 3.1.2: eqs. Q_SMW_reg, Q_SMW, BigQ and
- * 2e_HR_RCAS).  FP64.  The context holds the CAS orbitals as its trial:
+ * 2e_HR_RCAS).  FP64 (the projections onto the factor rows in double-float,
+ * about 48 significant bits).  The context holds the CAS orbitals as its trial:
  * ao_load_cholesky with a closed shell of n_alpha = n_beta = n_cas orbitals
  * (inactive orbitals first, localized as the caller wants them), then
  * lo_localize_compress(localize = 0) for the factors of every CAS orbital pair.
