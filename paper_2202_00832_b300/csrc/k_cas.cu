@@ -215,8 +215,8 @@ __global__ void cas_theta_kernel(int M, int N, const double2* __restrict__ phi, 
 // factor rows and the walkers' Theta^0 rows are staged kProjRB at a time in
 // shared memory, split into hi + lo as they are stored.  Each thread keeps the
 // double-float sums of one (row, walker) for up to kProjC columns at a time.
-constexpr int kProjRows = 64, kProjW = 4, kProjRB = 16, kProjC = 8;
-__global__ void __launch_bounds__(kProjRows * kProjW)
+constexpr int kProjRows = 64, kProjW = 4, kProjRB = 16, kProjC = 6;
+__global__ void __launch_bounds__(kProjRows * kProjW, 3)
 cas_project_df_kernel(int M, int N, int C, long rows, int W, const double* __restrict__ F,
                       const double2* __restrict__ th0, double2* __restrict__ out, size_t out_stride, int mode,
                       int Nc, const int* __restrict__ row_pair, const int* __restrict__ pa,
