@@ -54,4 +54,27 @@ __device__ inline dfl df_fma(dfl a, dfl b, dfl c) {
 }
 __device__ inline dfl df_mul(dfl a, dfl b) { return df_fma(a, b, dfl{0.f, 0.f}); }
 
+// Two double-floats as the lanes of float2 pairs (hi, lo), e.g. the real and
+// imaginary parts of a complex value: df2_fma is df_fma on both lanes, one
+// sm_100 FP32x2 instruction per step (the same operations in the same order).
+struct dfl2 {
+    float2 hi, lo;
+};
+__device__ inline float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ inline dfl2 df2_fma(dfl2 a, dfl2 b, dfl2 c) {
+    const float2 p = __fmul2_rn(a.hi, b.hi);
+    float2 e = __ffma2_rn(a.hi, b.hi, neg2(p));  // exact error of the product
+    e = __ffma2_rn(a.hi, b.lo, e);
+    e = __ffma2_rn(a.lo, b.hi, e);
+    const float2 s = __fadd2_rn(c.hi, p);  // TwoSum(c.hi, p)
+    const float2 v = __fadd2_rn(s, neg2(c.hi));
+    float2 t = __fadd2_rn(__fadd2_rn(c.hi, neg2(__fadd2_rn(s, neg2(v)))), __fadd2_rn(p, neg2(v)));
+    t = __fadd2_rn(t, c.lo);
+    t = __fadd2_rn(t, e);
+    dfl2 r;
+    r.hi = __fadd2_rn(s, t);  // renormalise
+    r.lo = __fadd2_rn(t, neg2(__fadd2_rn(r.hi, neg2(s))));
+    return r;
+}
+
 }  // namespace loaf

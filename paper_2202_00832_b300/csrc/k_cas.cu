@@ -244,9 +244,10 @@ cas_project_df_kernel(int M, int N, int C, long rows, int W, const double* __res
             const int c = cb + q;
             sl[q] = c >= C ? -1 : (c > 0 ? var_slot[c - 1] : fixed_slot[orb]);
         }
-        dfl are[kProjC], aim[kProjC];
+        // (re, im) as the two lanes of one packed double-float per column
+        dfl2 acc[kProjC];
 #pragma unroll
-        for (int q = 0; q < kProjC; ++q) { are[q] = dfl{0.f, 0.f}; aim[q] = dfl{0.f, 0.f}; }
+        for (int q = 0; q < kProjC; ++q) acc[q] = dfl2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         for (int r0 = 0; r0 < M; r0 += kProjRB) {
             const int nr = min(kProjRB, M - r0);
             __syncthreads();  // the previous block's reads are done
@@ -257,7 +258,7 @@ cas_project_df_kernel(int M, int N, int C, long rows, int W, const double* __res
                 if (ww < nw) {
                     const double2 z = th0[((size_t)(w0 + ww) * M + r0 + r) * N + sidx];
                     const dfl a = df_split_bits(z.x), b = df_split_bits(z.y);
-                    v = make_float4(a.hi, a.lo, b.hi, b.lo);
+                    v = make_float4(a.hi, b.hi, a.lo, b.lo);  // {re.hi, im.hi, re.lo, im.lo}
                 }
                 th[(size_t)ww * th_w + r * N + sidx] = v;
             }
@@ -275,13 +276,12 @@ cas_project_df_kernel(int M, int N, int C, long rows, int W, const double* __res
                 const float4* thw = th + (size_t)wq * th_w;
                 for (int r = 0; r < nr; ++r) {
                     const float2 f2 = fs[rl * (kProjRB + 1) + r];
-                    const dfl fv{f2.x, f2.y};
+                    const dfl2 fv{make_float2(f2.x, f2.x), make_float2(f2.y, f2.y)};
 #pragma unroll
                     for (int q = 0; q < kProjC; ++q) {
                         if (sl[q] < 0) continue;
                         const float4 t = thw[r * N + sl[q]];
-                        are[q] = df_fma(fv, dfl{t.x, t.y}, are[q]);
-                        aim[q] = df_fma(fv, dfl{t.z, t.w}, aim[q]);
+                        acc[q] = df2_fma(fv, dfl2{make_float2(t.x, t.y), make_float2(t.z, t.w)}, acc[q]);
                     }
                 }
             }
@@ -290,7 +290,9 @@ cas_project_df_kernel(int M, int N, int C, long rows, int W, const double* __res
 #pragma unroll
             for (int q = 0; q < kProjC; ++q) {
                 const int c = cb + q;
-                if (c < C) out[(size_t)(w0 + wq) * out_stride + (size_t)row * C + c] = make_double2(df_to(are[q]), df_to(aim[q]));
+                if (c < C)
+                    out[(size_t)(w0 + wq) * out_stride + (size_t)row * C + c] =
+                        make_double2(df_to(dfl{acc[q].hi.x, acc[q].lo.x}), df_to(dfl{acc[q].hi.y, acc[q].lo.y}));
             }
         }
     }
