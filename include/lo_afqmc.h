@@ -177,6 +177,30 @@ loaf_status walkers_energy(loaf_ctx *ctx, int W, const void *phi, int mode, int 
                            void *e_out, void *logdet_out, int *walker_status);
 
 /*
+ * walkers_energy_submit / walkers_energy_wait -- walkers_energy as a stream
+ * of calls.  The same computation and outputs as walkers_energy (eq. Q and
+ * eq. 2e_HR_RCAS_LO for mode LO; the same kernels, so results identical to a
+ * walkers_energy call on the same W device-resident walkers), but submit
+ * returns once the work is queued: the upload of one call's walkers (host
+ * phi, two copies on two copy streams) runs while the previous call computes.
+ * Two calls alternate between two device copies of the walkers owned by the
+ * context; submitting a third first waits for the first.
+ *   arguments as walkers_energy; host buffers must stay valid and unread
+ *   until walkers_energy_wait returns, and must be page-locked (pinned) for
+ *   the copies to overlap (pageable buffers work but serialise the call).
+ *   A change of (W, mode, precision) between submitted calls first waits for
+ *   those in flight (the workspace is sized for one shape at a time).
+ * Errors: argument errors as walkers_energy, at submit.  Walker failures and
+ * pipeline timeouts of the submitted calls are reported by walkers_energy_wait
+ * (LOAF_ERR_SINGULAR / LOAF_ERR_NAN / LOAF_ERR_TIMEOUT, the worst over the
+ * calls since the last wait); each call's walker_status marks its walkers.
+ * walkers_energy_wait returns when every submitted call's outputs are written.
+ */
+loaf_status walkers_energy_submit(loaf_ctx *ctx, int W, const void *phi, int mode, int precision,
+                                  void *e_out, void *logdet_out, int *walker_status);
+loaf_status walkers_energy_wait(loaf_ctx *ctx);
+
+/*
  * loaf_set_tiles / loaf_get_tiles -- tile shapes of the tensor-core kernels of
  * one context (the paper has no counterpart: its batched contractions of
  * Sec. 4.4 leave the tiling to the GEMM library).

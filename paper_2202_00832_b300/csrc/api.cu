@@ -280,6 +280,12 @@ loaf_status loaf_destroy(loaf_ctx* c) {
     if (c->branch_stream) cudaStreamDestroy(c->branch_stream);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->h_flags) cudaFreeHost(c->h_flags);
+    for (auto& sl : c->aslot) {
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.h_flags) cudaFreeHost(sl.h_flags);
+        sl.phi.release();
+        sl.out.release();
+    }
     for (auto& s : c->sp) s.release();
     for (auto& m : c->mix) m.release();
     c->d_h.release(); c->d_L.release();
@@ -441,6 +447,16 @@ void energy_batch(loaf_ctx* c, int W, const double2* dphi, int mode, int precisi
     }
 }
 
+// the two upload streams and their events, created on first use
+void ensure_copy_streams(loaf_ctx* c) {
+    if (c->copy_stream[0]) return;
+    for (cudaStream_t* cs : {&c->copy_stream[0], &c->copy_stream[1]})
+        LOAF_CUDA(cudaStreamCreateWithFlags(cs, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&c->ev_start, &c->ev_copied[0][0], &c->ev_copied[0][1], &c->ev_copied[1][0],
+                           &c->ev_copied[1][1], &c->ev_free[0], &c->ev_free[1]})
+        LOAF_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+}
+
 // Upload chunks for a host array of W walkers (empty: one piece).  At
 // pentacene scale uploading a walker over the host link takes a little longer
 // than computing it (about 10.3 against 8.8 us), so the copies run back to back
@@ -501,13 +517,7 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
             }
         } else {
             // upload chunk k + 1 on the copy stream while chunk k computes
-            if (!c->copy_stream[0]) {
-                for (cudaStream_t* cs : {&c->copy_stream[0], &c->copy_stream[1]})
-                    LOAF_CUDA(cudaStreamCreateWithFlags(cs, cudaStreamNonBlocking));
-                for (cudaEvent_t* e : {&c->ev_start, &c->ev_copied[0][0], &c->ev_copied[0][1], &c->ev_copied[1][0],
-                                       &c->ev_copied[1][1], &c->ev_free[0], &c->ev_free[1]})
-                    LOAF_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-            }
+            ensure_copy_streams(c);
             const size_t per_w = (size_t)c->M * c->ntot;
             const double2* hphi = static_cast<const double2*>(phi);
             int even_max = 0;
@@ -551,6 +561,114 @@ loaf_status walkers_energy(loaf_ctx* c, int W, const void* phi, int mode, int pr
         return flags[0] == LOAF_WALKER_SINGULAR ? LOAF_ERR_SINGULAR : LOAF_ERR_NAN;
     }
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// submitted calls: the upload of one call overlaps the compute of the previous
+// ---------------------------------------------------------------------------
+namespace {
+
+// wait for a submitted call and fold its flags into the context's
+void harvest(loaf_ctx* c, loaf_ctx::AsyncSlot& s) {
+    if (!s.pending) return;
+    LOAF_CUDA(cudaEventSynchronize(s.done));
+    c->async_flags[0] = std::max(c->async_flags[0], s.h_flags[0]);
+    c->async_flags[1] |= s.h_flags[1];
+    s.pending = false;
+}
+
+// every submitted call, oldest first
+void drain(loaf_ctx* c) {
+    const int a = c->aslot_next;
+    harvest(c, c->aslot[a]);
+    harvest(c, c->aslot[a ^ 1]);
+}
+
+}  // namespace
+
+loaf_status walkers_energy_submit(loaf_ctx* c, int W, const void* phi, int mode, int precision,
+                                  void* e_out, void* logdet_out, int* walker_status) {
+    if (!c) return LOAF_ERR_ARG;
+    return guarded(c, [&] {
+        LOAF_CUDA(cudaSetDevice(c->device));
+        check_ready(c, W, phi, mode, precision);
+        LOAF_REQUIRE(e_out != nullptr, LOAF_ERR_ARG, "e_out is NULL");
+        // the workspace is sized for one (W, mode, precision); a call with
+        // another first lets the calls in flight finish, so that no buffer
+        // they use is reallocated under them
+        const long long key = ((long long)W * 8 + mode) * 8 + precision;
+        if (key != c->async_key) {
+            drain(c);
+            c->async_key = key;
+        }
+        loaf_ctx::AsyncSlot& sl = c->aslot[c->aslot_next];
+        harvest(c, sl);  // the call two back used this slot's buffers
+        if (!sl.done) {
+            LOAF_CUDA(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+            LOAF_CUDA(cudaMallocHost(&sl.h_flags, 2 * sizeof(int)));
+        }
+        ensure_workspace(c, W, mode);
+        const size_t per_w = (size_t)c->M * c->ntot;
+        sl.out.ensure((size_t)W * (2 * sizeof(double2) + sizeof(int)) + 64);
+        double2* de = sl.out.as<double2>();
+        double2* dld = de + W;
+        int* dst = reinterpret_cast<int*>(dld + W);
+        int* dflags = dst + W;
+        LOAF_CUDA(cudaMemsetAsync(dflags, 0, 2 * sizeof(int), c->stream));
+        const double2* dphi = static_cast<const double2*>(phi);
+        if (!is_device_ptr(phi)) {
+            // the whole call in two halves on the two copy streams; they wait
+            // for nothing on the compute stream (this slot's last call is done)
+            ensure_copy_streams(c);
+            sl.phi.ensure((size_t)W * per_w * sizeof(double2));
+            const double2* hphi = static_cast<const double2*>(phi);
+            double2* buf = sl.phi.as<double2>();
+            for (int h = 0; h < 2; ++h) {
+                const int a0 = h == 0 ? 0 : W / 2, a1 = h == 0 ? W / 2 : W;
+                if (a1 == a0) continue;
+                cudaStream_t cs = c->copy_stream[h];
+                LOAF_CUDA(cudaMemcpyAsync(buf + (size_t)a0 * per_w, hphi + (size_t)a0 * per_w,
+                                          (size_t)(a1 - a0) * per_w * sizeof(double2), cudaMemcpyHostToDevice, cs));
+                LOAF_CUDA(cudaEventRecord(c->ev_copied[0][h], cs));
+                LOAF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_copied[0][h], 0));
+            }
+            dphi = buf;
+        }
+        for (int w0 = 0; w0 < W; w0 += kMaxBatch) {
+            const int Wk = std::min(kMaxBatch, W - w0);
+            energy_batch(c, Wk, dphi + (size_t)w0 * per_w, mode, precision, de + w0, dld + w0, dst + w0,
+                         dflags, dflags + 1);
+        }
+        deliver(c, e_out, de, (size_t)W * sizeof(double2));
+        deliver(c, logdet_out, dld, (size_t)W * sizeof(double2));
+        deliver(c, walker_status, dst, (size_t)W * sizeof(int));
+        LOAF_CUDA(cudaMemcpyAsync(sl.h_flags, dflags, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        LOAF_CUDA(cudaEventRecord(sl.done, c->stream));
+        sl.pending = true;
+        c->aslot_next ^= 1;
+    });
+}
+
+loaf_status walkers_energy_wait(loaf_ctx* c) {
+    if (!c) return LOAF_ERR_ARG;
+    loaf_status st = guarded(c, [&] {
+        LOAF_CUDA(cudaSetDevice(c->device));
+        drain(c);
+        LOAF_CUDA(cudaStreamSynchronize(c->stream));
+        prof_collect(c);
+    });
+    const int worst = c->async_flags[0], timeout = c->async_flags[1];
+    c->async_flags[0] = c->async_flags[1] = 0;
+    if (st != LOAF_OK) return st;
+    if (timeout) {
+        c->err = "a tensor-core kernel gave up waiting on a pipeline barrier";
+        return LOAF_ERR_TIMEOUT;
+    }
+    if (worst) {
+        c->err = "at least one walker overlap is singular or non-finite";
+        return worst == LOAF_WALKER_SINGULAR ? LOAF_ERR_SINGULAR : LOAF_ERR_NAN;
+    }
+    return LOAF_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -313,6 +313,19 @@ struct loaf_ctx {
     int tile_coul_split = 0;
     int tile_version = 0;  // bumped whenever the tile shapes change
     int persistent_grid() const { return grid_cap > 0 ? std::min(grid_cap, sm_count) : sm_count; }
+    // walkers_energy_submit: two call slots used in turn, each with its own
+    // device copy of the walkers, device results and pinned flags, so that one
+    // call's upload runs on the copy streams while the previous call computes
+    struct AsyncSlot {
+        loaf::DevBuf phi, out;
+        int* h_flags = nullptr;  // [worst walker status, timeout], pinned host memory
+        cudaEvent_t done = nullptr;
+        bool pending = false;    // submitted and not yet harvested
+    };
+    AsyncSlot aslot[2];
+    int aslot_next = 0;
+    long long async_key = -1;         // (W, mode, precision) of the calls the workspace is sized for
+    int async_flags[2] = {0, 0};      // harvested flags of the calls not yet waited for
     // multi-system launches: a private branch stream, fork/join events, pinned flags
     cudaStream_t branch_stream = nullptr;
     cudaEvent_t ev_join = nullptr;

@@ -40,6 +40,8 @@ SIGNATURES = [
     ("ao_load_cholesky", _I, [_P, _I, _I, _P, _P, _I, _I, _P, _P, _D, _I]),
     ("lo_localize_compress", _I, [_P, _D, _P, _I, _I, _P, _P]),
     ("walkers_energy", _I, [_P, _I, _P, _I, _I, _P, _P, _P]),
+    ("walkers_energy_submit", _I, [_P, _I, _P, _I, _I, _P, _P, _P]),
+    ("walkers_energy_wait", _I, [_P]),
     ("walkers_energy_multi", _I, [_P, _I, _P, _P, _I, _I, _P, _P, _P, _I, _P]),
     ("walkers_theta", _I, [_P, _I, _P, _P, _P, _P]),
     ("walkers_force_bias", _I, [_P, _I, _P, _I, _P, _P, _P]),
@@ -265,6 +267,33 @@ class Context:
             return e_out, logdet_out, walker_status
         self._check(code, "walkers_energy")
         return e_out, logdet_out, walker_status
+
+    def walkers_energy_submit(self, phi, e_out, logdet_out=None, walker_status=None, mode="lo",
+                              precision="fp16x3"):
+        """Queue walkers_energy on phi (pinned host or device) into the given
+        output buffers and return; the buffers are held until walkers_energy_wait."""
+        _check_dtype(phi, "c16")
+        _check_dtype(e_out, "c16")
+        _check_dtype(logdet_out, "c16")
+        _check_dtype(walker_status, "i4")
+        W = int(phi.shape[0])
+        code = self._lib.walkers_energy_submit(self._h, W, _ptr(phi), MODES.get(mode, mode),
+                                               PRECISIONS.get(precision, precision), _ptr(e_out),
+                                               _ptr(logdet_out), _ptr(walker_status))
+        self._check(code, "walkers_energy_submit")
+        if not hasattr(self, "_inflight"):
+            self._inflight = []
+        self._inflight.append((phi, e_out, logdet_out, walker_status))
+
+    def walkers_energy_wait(self, raise_on_singular: bool = True):
+        """Wait for every submitted call; returns the status code (0 or a
+        walker failure when raise_on_singular is False)."""
+        code = self._lib.walkers_energy_wait(self._h)
+        self._inflight = []
+        if code in (5, 8) and not raise_on_singular:
+            return code
+        self._check(code, "walkers_energy_wait")
+        return code
 
     def walkers_propagator(self, x, precision="fp64", out=None):
         """V_w = sum_g x_wg L_g for fields x (W x X complex128): W x M x M complex128."""

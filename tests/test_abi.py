@@ -57,6 +57,8 @@ def test_null_arguments_return_status(lib):
     assert lib.loaf_create(None, 0, None) == 1
     assert lib.ao_load_cholesky(None, 1, 1, None, None, 1, 1, None, None, 0.0, 0) == 1
     assert lib.walkers_energy(None, 1, None, 0, 0, None, None, None) == 1
+    assert lib.walkers_energy_submit(None, 1, None, 0, 0, None, None, None) == 1
+    assert lib.walkers_energy_wait(None) == 1
     assert lib.loaf_destroy(None) == 0
     assert lib.loaf_num_pairs(None) == 0
     assert lib.loaf_set_tiles(None, 256, 0) == 1
