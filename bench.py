@@ -104,6 +104,28 @@ def max_over_ranks(x: float, dist) -> float:
     return float(t.item())
 
 
+def host_link_gbs(src, reps: int = 4) -> float:
+    """H2D rate of the pinned walker array alone (GB/s): each copy in two
+    halves on two streams, as the library uploads a call; the bound on an
+    end-to-end rate that uploads every step's walkers."""
+    import torch
+    flat = src.view(-1)
+    dst = torch.empty(flat.shape, dtype=flat.dtype, device="cuda")
+    half = flat.numel() // 2
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for h, st in enumerate(streams):
+            sl = slice(0, half) if h == 0 else slice(half, flat.numel())
+            with torch.cuda.stream(st):
+                dst[sl].copy_(flat[sl], non_blocking=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    del dst
+    return reps * flat.numel() * flat.element_size() / dt / 1e9
+
+
 def whole_job_rate(world: int, W: int, steps: int, seconds: float) -> float:
     """Walker energies per second of all ranks together."""
     return world * W * steps / seconds
@@ -391,6 +413,7 @@ def run_ours(args, rank, world, local):
     e2e = whole_job_rate(world, W, args.steps, t_e2e)
     h2d = W * mol.M * (mol.n_alpha if mol.closed_shell else mol.n_alpha + mol.n_beta) * 16
     d2h = W * (16 + 16 + 4)
+    link_gbs = host_link_gbs(phi_h)
 
     if rank != 0:
         if dist is not None:
@@ -568,6 +591,8 @@ def run_ours(args, rank, world, local):
                 "api": "walkers_energy_submit per step (pinned host walkers in, pinned host energies, "
                        "log-dets and statuses out), walkers_energy_wait after the last",
                 "blocking_value": e2e_blocking,
+                "host_link_h2d_gbs": link_gbs,
+                "host_link_bound": link_gbs * 1e9 / (h2d / W) * world,
                 "blocking_api": "one walkers_energy call per step (returns with the outputs written)"},
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
