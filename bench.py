@@ -104,21 +104,21 @@ def max_over_ranks(x: float, dist) -> float:
     return float(t.item())
 
 
-def host_link_gbs(src, reps: int = 4) -> float:
-    """H2D rate of the pinned walker array alone (GB/s): each copy in two
-    halves on two streams, as the library uploads a call; the bound on an
-    end-to-end rate that uploads every step's walkers."""
+def host_link_gbs(src, reps: int = 4, pieces: int = 16) -> float:
+    """H2D rate of the pinned walker array alone (GB/s): each copy in 16
+    pieces taken in turn by two streams, as the library uploads a submitted
+    call; the bound on an end-to-end rate that uploads every step's walkers."""
     import torch
     flat = src.view(-1)
     dst = torch.empty(flat.shape, dtype=flat.dtype, device="cuda")
-    half = flat.numel() // 2
+    n = flat.numel()
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(reps):
-        for h, st in enumerate(streams):
-            sl = slice(0, half) if h == 0 else slice(half, flat.numel())
-            with torch.cuda.stream(st):
+        for i in range(pieces):
+            sl = slice(i * n // pieces, (i + 1) * n // pieces)
+            with torch.cuda.stream(streams[i % 2]):
                 dst[sl].copy_(flat[sl], non_blocking=True)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0

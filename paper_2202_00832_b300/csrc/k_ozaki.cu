@@ -694,7 +694,10 @@ gauss_jordan_kernel(int N, int kpad, int W, const double2* __restrict__ S,
     }
     __syncthreads();
     __shared__ T s_akk;
-    for (int k = 0; k < N && s_flag == 0; ++k) {
+    // s_flag is written (phase A) only before the first barrier of a step and
+    // read only after it, so every thread leaves the loop at the same step
+    const bool run = s_flag == 0;
+    for (int k = 0; run && k < N; ++k) {
         // phase A (one warp): pivot row p of column k, 1/pivot, the old A[k][k]
         if (tid < 32) {
             R best = -1;
