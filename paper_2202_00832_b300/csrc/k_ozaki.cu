@@ -349,7 +349,7 @@ struct OzShared {
     uint64_t full[kOStages];
     uint64_t empty[kOStages];
     uint64_t tmem_full;
-    uint64_t tmem_empty;
+    uint64_t diag_empty[kND];  // diagonal D of the accumulators read by every epilogue warp
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
@@ -399,7 +399,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
     if (threadIdx.x == 0) {
         for (int s = 0; s < kOStages; ++s) { tc::mbar_init(&sh.full[s], 1); tc::mbar_init(&sh.empty[s], 1); }
         tc::mbar_init(&sh.tmem_full, 1);
-        tc::mbar_init(&sh.tmem_empty, kOEpiWarps);
+        for (int D = 0; D < kND; ++D) tc::mbar_init(&sh.diag_empty[D], kOEpiWarps);
         tc::mbar_init(&sh.drain, 1);
         sh.abort = 0;
         tc::fence_barrier_init();
@@ -446,29 +446,38 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
         int s = 0;
         uint32_t ph = 0, tph = 0;
         for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
-            if (!tc::mbar_wait(&sh.tmem_empty, tph ^ 1, abort)) break;
-            tc::tc_fence_after();
             bool ok = true;
-            uint32_t started = 0;  // bit D-2: diagonal D already has a product this unit
-            for (int kc = 0; kc < P.nk; ++kc) {
+            uint32_t started = 0;  // bit D: diagonal D already has a product this unit
+            uint32_t owned = 0;    // bit D: the previous unit's epilogue has read diagonal D
+            for (int kc = 0; kc < P.nk && ok; ++kc) {
                 if (!tc::mbar_wait(&sh.full[s], ph, abort)) { ok = false; break; }
                 tc::tc_fence_after();
                 const uint32_t st = tc::smem_u32(base + s * kOStage);
+                // diagonal by diagonal, so that this unit's first products only
+                // wait for the diagonals the last unit's epilogue has read; the
+                // order of the products within a diagonal is that of k
 #pragma unroll
-                for (int kk = 0; kk < kOBK / 16; ++kk) {
+                for (int D = 0; D < kND; ++D) {
+                    if (!((owned >> D) & 1u)) {
+                        if (!tc::mbar_wait(&sh.diag_empty[D], tph ^ 1, abort)) { ok = false; break; }
+                        tc::tc_fence_after();
+                        owned |= 1u << D;
+                    }
 #pragma unroll
-                    for (int a = 0; a < kNS; ++a)
+                    for (int kk = 0; kk < kOBK / 16; ++kk) {
 #pragma unroll
-                        for (int bq = 0; bq < kNS; ++bq) {
-                            const int D = a + bq;  // (s-1) + (t-1): diagonal index 0..5 kept
-                            if (D >= kND) continue;
+                        for (int a = 0; a < kNS; ++a) {
+                            const int bq = D - a;  // digit pairs with a + bq = D
+                            if (bq < 0 || bq >= kNS) continue;
                             const uint64_t da = tc::smem_desc(st + a * kOTileA + kk * 32, 64);
                             const uint64_t db = tc::smem_desc(st + kNS * kOTileA + bq * kOTileB + kk * 32, 64);
                             const uint32_t acc = (started >> D) & 1u;
                             tc::mma_f16(tmem + D * kOBN, da, db, P.idesc, acc);
                             started |= 1u << D;
                         }
+                    }
                 }
+                if (!ok) break;
                 tc::mma_commit(&sh.empty[s]);
                 if (++s == kOStages) { s = 0; ph ^= 1; }
             }
@@ -481,12 +490,35 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
         tc::mbar_wait(&sh.drain, 0, &never);
     } else if (warp >= 2) {
         const int q = warp & 3;
-        const int h = (warp - 2) >> 2;  // chunk h, h + 4, ... of 8 columns
+        const int h = (warp - 2) >> 2;  // chunks h, h + 4, h + 8 of 8 columns
+        constexpr int kCh = (kOBN + 31) / 32;  // chunks per thread at most
         uint32_t tph = 0;
         for (int u = blockIdx.x; u < n_units && !*abort; u += gridDim.x) {
             const int ct = u % P.n_ct, rt = (u / P.n_ct) % P.n_rt, b = u / (P.n_ct * P.n_rt);
             if (!tc::mbar_wait(&sh.tmem_full, tph, abort)) break;
             tc::tc_fence_after();
+            // z = sum_D acc_D 2^(7 (kND - 1 - D)) by Horner's rule, most
+            // significant diagonal first; each diagonal is handed back to the
+            // MMA issuer (the next unit) as soon as every warp has read it
+            long long z[kCh][8];
+#pragma unroll
+            for (int D = 0; D < kND; ++D) {
+#pragma unroll
+                for (int i = 0; i < kCh; ++i) {
+                    if (h * 8 + 32 * i >= kOBN) continue;
+                    float v[8];
+                    tc::tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + D * kOBN + h * 8 + 32 * i, v);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {  // |v| < 2^24: exact as int32
+                        const long long a = (long long)__float2int_rn(v[c]);
+                        z[i][c] = D == 0 ? a : z[i][c] * 128 + a;
+                    }
+                }
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&sh.diag_empty[D]);
+            }
             const int row = rt * kOBM + q * 32 + lane;
             // mode 0: row = (2w + ri) N + j of the walker slices
             int w0 = 0, ri0 = 0, j0 = 0;
@@ -497,10 +529,11 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
                 j0 = rem - ri0 * P.N;
             }
             const int wexp_b = P.mode == 1 ? P.wexp[b] : 0, texp_b = P.mode == 1 ? P.texp[b] : 0;
-#pragma unroll 1
-            for (int c0 = h * 8; c0 < kOBN; c0 += 32) {
-                // mode 1: the chunk's four orbitals k: exponents and trial values,
-                // fetched before the accumulators are read
+#pragma unroll
+            for (int i = 0; i < kCh; ++i) {
+                const int c0 = h * 8 + 32 * i;
+                if (c0 >= kOBN) continue;
+                // mode 1: the chunk's four orbitals k: exponents and trial values
                 int ek[4] = {0, 0, 0, 0};
                 long long tk[4] = {0, 0, 0, 0};
                 if (P.mode == 1) {
@@ -514,31 +547,19 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
                         }
                     }
                 }
-                float v[kND][8];
-#pragma unroll
-                for (int D = 0; D < kND; ++D)
-                    tc::tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + D * kOBN + c0, v[D]);
-                tc::tmem_wait_ld();
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    long long z = 0;
-#pragma unroll
-                    for (int D = 0; D < kND; ++D)  // |v| < 2^24: exact as int32
-                        z += (long long)__float2int_rn(v[D][c]) * (1LL << (7 * (kND - 1 - D)));
                     const int col = ct * kOBN + c0 + c;
                     if (row >= P.rows_valid || col >= P.cols_valid) continue;
                     if (P.mode == 0) {
                         // S_w[i][j] (part ri) for column col = i of Phi_T
                         P.S_out[(((size_t)w0 * P.N + col) * P.N + j0) * 2 + ri0] =
-                            (double)z * pow2d(P.row_exp[col] + P.wexp[w0] - 49);
+                            (double)z[i][c] * pow2d(P.row_exp[col] + P.wexp[w0] - 49);
                     } else {
-                        store_delta(P, b, row, col, z, wexp_b + ek[c >> 1] - 49, texp_b, tk[c >> 1]);
+                        store_delta(P, b, row, col, z[i][c], wexp_b + ek[c >> 1] - 49, texp_b, tk[c >> 1]);
                     }
                 }
             }
-            tc::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&sh.tmem_empty);
             tph ^= 1;
         }
     }
