@@ -189,7 +189,10 @@ loaf_status walkers_energy(loaf_ctx *ctx, int W, const void *phi, int mode, int 
  *   until walkers_energy_wait returns, and must be page-locked (pinned) for
  *   the copies to overlap (pageable buffers work but serialise the call).
  *   A change of (W, mode, precision) between submitted calls first waits for
- *   those in flight (the workspace is sized for one shape at a time).
+ *   those in flight (the workspace is sized for one shape at a time), and so
+ *   do ao_load_cholesky, lo_localize_compress, loaf_set_tiles (when the shapes
+ *   change), pair_screen_train, pair_screen_set and walkers_energy_multi: a
+ *   queued call computes with the operands it was queued with.
  * Errors: argument errors as walkers_energy, at submit.  Walker failures and
  * pipeline timeouts of the submitted calls are reported by walkers_energy_wait
  * (LOAF_ERR_SINGULAR / LOAF_ERR_NAN / LOAF_ERR_TIMEOUT, the worst over the

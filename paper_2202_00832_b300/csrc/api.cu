@@ -171,6 +171,18 @@ void StageScope::end() {
     idx = -1;
 }
 
+void drain_submitted(loaf_ctx* c) {
+    const int a = c->aslot_next;  // the oldest call first
+    for (int k = 0; k < 2; ++k) {
+        loaf_ctx::AsyncSlot& s = c->aslot[a ^ k];
+        if (!s.pending) continue;
+        LOAF_CUDA(cudaEventSynchronize(s.done));
+        c->async_flags[0] = std::max(c->async_flags[0], s.h_flags[0]);
+        c->async_flags[1] |= s.h_flags[1];
+        s.pending = false;
+    }
+}
+
 void prof_collect(loaf_ctx* c) {
     for (auto& m : c->prof_open) {
         float ms = 0.f;
@@ -214,13 +226,14 @@ loaf_status loaf_set_tiles(loaf_ctx* c, int lo_chunk_cap, int coulomb_split) {
         c->err = "lo_chunk_cap must be a multiple of 32 in [64, 256] and coulomb_split in [0, 64]";
         return LOAF_ERR_ARG;
     }
-    if (c->tile_lo_cap != lo_chunk_cap || c->tile_coul_split != coulomb_split) {
+    if (c->tile_lo_cap == lo_chunk_cap && c->tile_coul_split == coulomb_split) return LOAF_OK;
+    return guarded(c, [&] {
+        drain_submitted(c);
         c->tile_lo_cap = lo_chunk_cap;
         c->tile_coul_split = coulomb_split;
         c->tile_version += 1;
         forget_plans(c);
-    }
-    return LOAF_OK;
+    });
 }
 
 loaf_status loaf_get_tiles(const loaf_ctx* c, int* lo_chunk_cap, int* coulomb_split) {
@@ -332,6 +345,7 @@ loaf_status ao_load_cholesky(loaf_ctx* c, int M, int X, const double* h, const d
     if (!c) return LOAF_ERR_ARG;
     return guarded(c, [&] {
         LOAF_CUDA(cudaSetDevice(c->device));
+        drain_submitted(c);
         setup_load(c, M, X, h, L, n_alpha, n_beta, trial_a, trial_b, e0, inputs_on_device);
     });
 }
@@ -341,6 +355,7 @@ loaf_status lo_localize_compress(loaf_ctx* c, double t_svd, const double* r_ops,
     if (!c) return LOAF_ERR_ARG;
     return guarded(c, [&] {
         LOAF_CUDA(cudaSetDevice(c->device));
+        drain_submitted(c);
         setup_compress(c, t_svd, r_ops, n_ops, localize, compression_pct, m_svd_per_pair);
     });
 }
@@ -570,22 +585,6 @@ namespace {
 
 constexpr int kUploadPieces = 16;
 
-// wait for a submitted call and fold its flags into the context's
-void harvest(loaf_ctx* c, loaf_ctx::AsyncSlot& s) {
-    if (!s.pending) return;
-    LOAF_CUDA(cudaEventSynchronize(s.done));
-    c->async_flags[0] = std::max(c->async_flags[0], s.h_flags[0]);
-    c->async_flags[1] |= s.h_flags[1];
-    s.pending = false;
-}
-
-// every submitted call, oldest first
-void drain(loaf_ctx* c) {
-    const int a = c->aslot_next;
-    harvest(c, c->aslot[a]);
-    harvest(c, c->aslot[a ^ 1]);
-}
-
 }  // namespace
 
 loaf_status walkers_energy_submit(loaf_ctx* c, int W, const void* phi, int mode, int precision,
@@ -600,11 +599,11 @@ loaf_status walkers_energy_submit(loaf_ctx* c, int W, const void* phi, int mode,
         // they use is reallocated under them
         const long long key = ((long long)W * 8 + mode) * 8 + precision;
         if (key != c->async_key) {
-            drain(c);
+            drain_submitted(c);
             c->async_key = key;
         }
         loaf_ctx::AsyncSlot& sl = c->aslot[c->aslot_next];
-        harvest(c, sl);  // the call two back used this slot's buffers
+        if (sl.pending) drain_submitted(c);  // the call two back used this slot's buffers
         if (!sl.done) {
             LOAF_CUDA(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
             LOAF_CUDA(cudaMallocHost(&sl.h_flags, 2 * sizeof(int)));
@@ -659,7 +658,7 @@ loaf_status walkers_energy_wait(loaf_ctx* c) {
     if (!c) return LOAF_ERR_ARG;
     loaf_status st = guarded(c, [&] {
         LOAF_CUDA(cudaSetDevice(c->device));
-        drain(c);
+        drain_submitted(c);
         LOAF_CUDA(cudaStreamSynchronize(c->stream));
         prof_collect(c);
     });
@@ -817,6 +816,8 @@ loaf_status walkers_energy_multi(loaf_ctx* const* ctxs, int n, const int* W, con
     int flags[2] = {0, 0};
     loaf_status st = guarded(c0, [&] {
         LOAF_REQUIRE(mode == LOAF_MODE_LO, LOAF_ERR_UNSUPPORTED, "the multi-system launch runs the LO mode");
+        for (int i = 0; i < n; ++i)
+            if (ctxs[i]) drain_submitted(ctxs[i]);
         LOAF_REQUIRE(precision == LOAF_PREC_FP16X3 || precision == LOAF_PREC_BF16X3 ||
                          precision == LOAF_PREC_FP16X3_F64INV,
                      LOAF_ERR_UNSUPPORTED,

@@ -395,6 +395,11 @@ struct StageScope {
     ~StageScope() { end(); }
 };
 void prof_collect(loaf_ctx* c);
+// Waits for the calls queued by walkers_energy_submit, keeping their walker
+// and timeout flags for walkers_energy_wait; entry points that change the
+// context's operands, tile shapes or screen call it first, so that no queued
+// call computes with operands rewritten under it.
+void drain_submitted(loaf_ctx* c);
 }  // namespace loaf
 
 namespace loaf {

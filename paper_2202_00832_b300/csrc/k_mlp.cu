@@ -208,6 +208,7 @@ extern "C" loaf_status pair_screen_train(loaf_ctx* c, int W_train, const void* p
                                          float lr, const float* init_params, float* loss_history) {
     if (!c) return LOAF_ERR_ARG;
     return guard(c, [&] {
+        drain_submitted(c);
         LOAF_REQUIRE(c->compressed, LOAF_ERR_NOT_READY, "pair_screen_train needs lo_localize_compress");
         LOAF_REQUIRE(W_train >= 1 && phi && epochs >= 1 && lr > 0.f && init_params, LOAF_ERR_ARG,
                      "pair_screen_train: W_train, phi, epochs, lr and init_params are required");
@@ -290,6 +291,7 @@ extern "C" loaf_status pair_screen_train(loaf_ctx* c, int W_train, const void* p
 extern "C" loaf_status pair_screen_set(loaf_ctx* c, double cutoff_ha, int* kept_pairs) {
     if (!c) return LOAF_ERR_ARG;
     return guard(c, [&] {
+        drain_submitted(c);
         LOAF_REQUIRE(c->compressed, LOAF_ERR_NOT_READY, "pair_screen_set needs lo_localize_compress");
         const int np = loaf_num_pairs(c);
         if (cutoff_ha < 0.0) {

@@ -176,3 +176,30 @@ def test_stream_timeout_reaches_the_wait(case):
     assert ctx.walkers_energy_wait() == 0
     re, _, _ = resident_call(ctx, walk, "fp16x3")
     assert np.array_equal(e.numpy(), re)
+
+
+def test_operand_changes_wait_for_submitted_calls(case):
+    """Changing the tile shapes or the compression while calls are queued
+    first lets those calls finish with the operands they were queued with:
+    the first call runs with the default shapes, the second with the new
+    shapes, both at T_SVD = 1e-3, although T_SVD = 1e-2 is set before the wait."""
+    ctx, mol, walk, msvd = case
+    b = batches(walk, 1, 19)[0]
+    ref_a, _, _ = resident_call(ctx, b, "fp16x3")
+    ctx.set_tiles(128, 3)
+    ref_b, _, _ = resident_call(ctx, b, "fp16x3")
+    ctx.set_tiles(256, 0)
+    h = torch.from_numpy(b).pin_memory()
+    e1, ld1, st1 = pinned_outputs(len(b))
+    e2, ld2, st2 = pinned_outputs(len(b))
+    try:
+        ctx.walkers_energy_submit(h, e1, ld1, st1, mode="lo", precision="fp16x3")
+        ctx.set_tiles(128, 3)
+        ctx.walkers_energy_submit(h, e2, ld2, st2, mode="lo", precision="fp16x3")
+        ctx.lo_localize_compress(1e-2, position_operators(mol), localize=True)
+        assert ctx.walkers_energy_wait() == 0
+        assert np.array_equal(e1.numpy(), ref_a)
+        assert np.array_equal(e2.numpy(), ref_b)
+    finally:
+        ctx.set_tiles(256, 0)
+        ctx.lo_localize_compress(1e-3, position_operators(mol), localize=True)
