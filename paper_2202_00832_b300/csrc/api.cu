@@ -305,7 +305,7 @@ loaf_status loaf_destroy(loaf_ctx* c) {
     for (loaf::DevBuf* b : {&c->w_phi, &c->w_theta, &c->w_z, &c->w_lu, &c->w_perm, &c->w_logdet,
                             &c->w_status, &c->w_out, &c->w_part, &c->w_part2, &c->w_dhi,
                             &c->w_dlo, &c->w_dscale, &c->w_host_stage, &c->w_cpart,
-                            &c->w_lopart, &c->w_red, &c->w_flag, &c->d_keep, &c->w_oz_at, &c->w_oz_bs,
+                            &c->w_lopart, &c->w_red, &c->w_flag, &c->d_keep, &c->w_oz_at,
                             &c->w_oz_bt, &c->w_oz_S, &c->w_oz_int, &c->w_oz_key, &c->w_prop_x, &c->w_prop_part,
                             &c->w_dfull, &c->w_dtf})
         b->release();

@@ -359,7 +359,7 @@ struct loaf_ctx {
     // workspace for walkers_energy (grown to the largest W seen)
     int ws_W = 0;
     loaf::DevBuf w_phi, w_theta, w_z, w_lu, w_perm, w_logdet, w_status, w_out, w_part,
-        w_part2, w_dhi, w_dlo, w_dscale, w_host_stage, w_cpart, w_lopart, w_red, w_flag, w_oz_at, w_oz_bs,
+        w_part2, w_dhi, w_dlo, w_dscale, w_host_stage, w_cpart, w_lopart, w_red, w_flag, w_oz_at,
         w_oz_bt, w_oz_S, w_oz_int, w_oz_key, w_prop_x, w_prop_part;
     // FP32 copy of the scaled Delta for the dense LO epilogue (dfull_elem layout);
     // zeroed whenever its geometry changes (the columns past M stay zero)

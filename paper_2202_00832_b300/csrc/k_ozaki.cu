@@ -44,6 +44,9 @@ constexpr int kOStages = 2;
 constexpr uint32_t kOTileA = kOBM * 64;              // 8 KB
 constexpr uint32_t kOTileB = kOBN * 64;              // 5 KB
 constexpr uint32_t kOStage = kNS * (kOTileA + kOTileB);  // 78 KB
+// S GEMM, MN-major A tile (two 64-row boxes of 32 k-rows of 128 bytes): bytes
+// between the 64-row blocks and between groups of 8 k-rows
+constexpr uint32_t kMnLbo = kOTileA / 2, kMnSbo = 8 * 128;
 constexpr size_t kOSmem = kOStages * kOStage + 1024;
 
 PFN_cuTensorMapEncodeTiled_v12000 encode() {
@@ -58,6 +61,34 @@ PFN_cuTensorMapEncodeTiled_v12000 encode() {
         fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     }
     return fn;
+}
+
+// walker slices At[slice][p][w][kpad] as the MN-major A operand of the S GEMM:
+// x = row (w, 2j + ri) (extent W kpad), y = k = p (extent M), z = 1, w = slice;
+// boxes of 64 rows x 32 k with the 128-byte swizzle
+void map_slices_mn(CUtensorMap* m, const void* base, uint64_t rows, uint64_t k) {
+    cuuint64_t dims[4] = {rows, k, 1, (cuuint64_t)kNS};
+    cuuint64_t strides[3] = {rows * 2, rows * k * 2, rows * k * 2};
+    cuuint32_t box[4] = {64, (cuuint32_t)kOBK, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = encode()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void*>(base), dims,
+                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    LOAF_REQUIRE(r == CUDA_SUCCESS, LOAF_ERR_CUDA, "cuTensorMapEncodeTiled (MN-major slices) failed");
+}
+
+// walker slices At[slice][p][w][kpad] as the K-major A operand of the Theta GEMM:
+// x = K = 2j + ri (extent 2N), y = walker, z = row p (extent M), w = slice;
+// boxes of 32 k x 1 walker x 128 rows with the 64-byte swizzle
+void map_slices_rows(CUtensorMap* m, const void* base, uint64_t k, uint64_t kpad, uint64_t W, uint64_t M) {
+    cuuint64_t dims[4] = {k, W, M, (cuuint64_t)kNS};
+    cuuint64_t strides[3] = {kpad * 2, kpad * W * 2, kpad * W * M * 2};
+    cuuint32_t box[4] = {(cuuint32_t)kOBK, 1, (cuuint32_t)kOBM, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = encode()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void*>(base), dims,
+                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    LOAF_REQUIRE(r == CUDA_SUCCESS, LOAF_ERR_CUDA, "cuTensorMapEncodeTiled (row slices) failed");
 }
 
 // 16-bit slices [slice][batch][rows][ld]: x = K (extent k), y = row, z = batch, w = slice
@@ -231,11 +262,12 @@ __global__ void slice_trial_kernel(int M, int N, int p_pad, const double* __rest
     if (threadIdx.x == 0) row_exp[i] = E;
 }
 
-// One walker's spin block of phi (M x N complex) -> digits in two layouts:
-//   At[s][w][p][kpad]        K = 2j + ri  (A operand of the Theta GEMM)
-//   Bs[s][(2w + ri) N + j][p_pad]          (B operand of the S GEMM)
-// with one exponent per walker and spin.  64 basis rows per step through
-// shared memory (transpose for Bs).
+// One walker's spin block of phi (M x N complex) -> digits, one exponent per
+// walker and spin, in the layout
+//   At[s][p][w][kpad]        K = 2j + ri, zero for 2j + ri >= 2N
+// which is the K-major A operand of the Theta GEMM (rows p of one walker) and,
+// read with k = p, the MN-major A operand of the S GEMM (rows (w, 2j + ri) of
+// all walkers contiguous for each p).  64 basis rows per CTA.
 constexpr int kSliceRows = 64;
 // Largest |phi| of each walker's spin block: kMaxSplit CTAs per walker over
 // row ranges, integer maxima of the absolute bit patterns (key[w] starts at 0).
@@ -258,66 +290,39 @@ phi_max_kernel(int M, int N, int ntot, int col0, const double2* __restrict__ phi
     if (threadIdx.x == 0) atomicMax(key + w, m);
 }
 
-// One (walker, 64-row chunk) per CTA: the chunk's digits in both layouts, with
-// the walker's exponent from its maximum key.  The (row, orbital) elements of
-// the chunk are spread over all threads (row-major, so the reads of phi and the
-// writes of At stay coalesced).
+// One (walker, 64-row chunk) per CTA: the chunk's digits, with the walker's
+// exponent from its maximum key.  The (row, orbital pair) elements of the chunk
+// are spread over all threads, row-major, so that the reads of phi and the
+// writes of At stay coalesced.
 __global__ void __launch_bounds__(256)
-slice_phi_kernel(int M, int N, int ntot, int col0, int p_pad, int kpad, int W,
+slice_phi_kernel(int M, int N, int ntot, int col0, int kpad, int W,
                  const double2* __restrict__ phi, const unsigned long long* __restrict__ key,
-                 uint16_t* __restrict__ At, uint16_t* __restrict__ Bs, int* __restrict__ wexp) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    signed char* dg = reinterpret_cast<signed char*>(sm);  // [kNS][kSliceRows][2N]
+                 uint16_t* __restrict__ At, int* __restrict__ wexp) {
     const int w = blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const double2* pw = phi + (size_t)w * M * ntot + col0;
     const int E = slice_exponent(__longlong_as_double((long long)key[w]));
     if (blockIdx.y == 0 && threadIdx.x == 0) wexp[w] = E;
-    const int twoN = 2 * N;
+    const int half = kpad >> 1;  // (re, im) pairs per row, those past N zero
     const int p0 = blockIdx.y * kSliceRows;
-    const int np = min(kSliceRows, p_pad - p0);
-    const size_t at_s = (size_t)W * M * kpad;  // At slice stride
-    // digits of (re, im) of phi[p][j]: K = 2j, 2j + 1 stored together
-    const int dpp = blockDim.x / N, dj = blockDim.x - dpp * N;
-    int pp = threadIdx.x / N, j = threadIdx.x - pp * N;
+    const int np = min(kSliceRows, M - p0);
+    const size_t at_s = (size_t)M * W * kpad;  // At slice stride
+    const int dpp = blockDim.x / half, dj = blockDim.x - dpp * half;
+    int pp = threadIdx.x / half, j = threadIdx.x - pp * half;
     while (pp < np) {
         const int p = p0 + pp;
         double2 z = make_double2(0.0, 0.0);
-        if (p < M) z = pw[(size_t)p * ntot + j];
+        if (j < N) z = pw[(size_t)p * ntot + j];
         int dr[kNS], di[kNS];
         digits6(z.x, E, dr);
         digits6(z.y, E, di);
-        uint32_t* at = reinterpret_cast<uint32_t*>(At + ((size_t)w * M + p) * kpad + 2 * j);
-        signed char* d2 = dg + (size_t)pp * twoN + 2 * j;
+        uint32_t* at = reinterpret_cast<uint32_t*>(At + ((size_t)p * W + w) * kpad + 2 * j);
 #pragma unroll
-        for (int s = 0; s < kNS; ++s) {
-            char2 c2;
-            c2.x = (signed char)dr[s];
-            c2.y = (signed char)di[s];
-            *reinterpret_cast<char2*>(d2 + (size_t)s * kSliceRows * twoN) = c2;
-            if (p < M) at[s * at_s / 2] = h16x2(dr[s], di[s]);
-        }
+        for (int s = 0; s < kNS; ++s) at[s * at_s / 2] = h16x2(dr[s], di[s]);
         pp += dpp;
         j += dj;
-        if (j >= N) {
-            j -= N;
+        if (j >= half) {
+            j -= half;
             ++pp;
-        }
-    }
-    __syncthreads();
-    // transpose: one warp per (slice, ri, j) row of Bs, two basis rows per lane
-    const int q = 2 * lane;
-    if (q < np) {
-        for (int s = 0; s < kNS; ++s) {
-            const signed char* src_s = dg + ((size_t)s * kSliceRows + q) * twoN;
-            uint16_t* dst_s = Bs + ((size_t)s * 2 * N * W + (size_t)2 * w * N) * p_pad + p0 + q;
-            for (int col = warp; col < twoN; col += nwarp) {  // col = ri N + j
-                const int ri = col >= N ? 1 : 0, jj = col - ri * N;
-                const signed char* src = src_s + 2 * jj + ri;
-                const int a = src[0];
-                const int b = q + 1 < np ? src[twoN] : 0;
-                *reinterpret_cast<uint32_t*>(dst_s + (size_t)col * p_pad) = h16x2(a, b);
-            }
         }
     }
 }
@@ -326,11 +331,12 @@ slice_phi_kernel(int M, int N, int ntot, int col0, int p_pad, int kpad, int W,
 // the slice GEMM (tcgen05, 21 products into six diagonal accumulators)
 // ---------------------------------------------------------------------------
 struct OzParams {
-    int n_rt, n_ct, n_b, nk, a_batched;
+    int n_rt, n_ct, n_b, nk;
     uint32_t idesc;
     int* err;
     int mode;  // 0: overlap S, 1: Theta -> Delta planes
     int M, N, ntot, col0, r_pad, W, rows_valid, cols_valid;
+    int kpad;             // mode 0: rows (w, 2j + ri) of the walker slices per walker
     int nrb, nkb;         // mode 1: Delta tile geometry
     const int* row_exp;   // mode 0: exponent of each Phi_T^T row i (column i of the GEMM)
     const int* wexp;      // exponent of each walker's phi block
@@ -425,8 +431,16 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
                 uint8_t* st = base + s * kOStage;
                 tc::mbar_arrive_expect_tx(&sh.full[s], kOStage);
                 for (int q = 0; q < kNS; ++q) {
-                    tc::tma_load_4d(st + q * kOTileA, &mA, &sh.full[s], kc * kOBK, rt * kOBM,
-                                    P.a_batched ? b : 0, q);
+                    if (P.mode == 0) {
+                        // MN-major: rows (w, 2j + ri) contiguous for each k = p, two
+                        // boxes of 64 rows x 32 k
+                        tc::tma_load_4d(st + q * kOTileA, &mA, &sh.full[s], rt * kOBM, kc * kOBK, 0, q);
+                        tc::tma_load_4d(st + q * kOTileA + kOTileA / 2, &mA, &sh.full[s], rt * kOBM + 64,
+                                        kc * kOBK, 0, q);
+                    } else {
+                        // K-major rows p of walker b
+                        tc::tma_load_4d(st + q * kOTileA, &mA, &sh.full[s], kc * kOBK, b, rt * kOBM, q);
+                    }
                     tc::tma_load_4d(st + kNS * kOTileA + q * kOTileB, &mB, &sh.full[s], kc * kOBK,
                                     ct * kOBN, b, q);
                 }
@@ -469,7 +483,10 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
                         for (int a = 0; a < kNS; ++a) {
                             const int bq = D - a;  // digit pairs with a + bq = D
                             if (bq < 0 || bq >= kNS) continue;
-                            const uint64_t da = tc::smem_desc(st + a * kOTileA + kk * 32, 64);
+                            const uint64_t da =
+                                P.mode == 0
+                                    ? tc::smem_desc_mn128(st + a * kOTileA + kk * 16 * 128, kMnLbo, kMnSbo)
+                                    : tc::smem_desc(st + a * kOTileA + kk * 32, 64);
                             const uint64_t db = tc::smem_desc(st + kNS * kOTileA + bq * kOTileB + kk * 32, 64);
                             const uint32_t acc = (started >> D) & 1u;
                             tc::mma_f16(tmem + D * kOBN, da, db, P.idesc, acc);
@@ -520,13 +537,15 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
                 if (lane == 0) tc::mbar_arrive(&sh.diag_empty[D]);
             }
             const int row = rt * kOBM + q * 32 + lane;
-            // mode 0: row = (2w + ri) N + j of the walker slices
+            // mode 0: row = w kpad + 2j + ri of the walker slices
             int w0 = 0, ri0 = 0, j0 = 0;
+            bool row_ok = row < P.rows_valid;
             if (P.mode == 0) {
-                w0 = row / (2 * P.N);
-                const int rem = row - w0 * 2 * P.N;
-                ri0 = rem >= P.N ? 1 : 0;
-                j0 = rem - ri0 * P.N;
+                w0 = row / P.kpad;
+                const int cc = row - w0 * P.kpad;
+                ri0 = cc & 1;
+                j0 = cc >> 1;
+                row_ok = row_ok && j0 < P.N;
             }
             const int wexp_b = P.mode == 1 ? P.wexp[b] : 0, texp_b = P.mode == 1 ? P.texp[b] : 0;
 #pragma unroll
@@ -550,7 +569,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int col = ct * kOBN + c0 + c;
-                    if (row >= P.rows_valid || col >= P.cols_valid) continue;
+                    if (!row_ok || col >= P.cols_valid) continue;
                     if (P.mode == 0) {
                         // S_w[i][j] (part ri) for column col = i of Phi_T
                         P.S_out[(((size_t)w0 * P.N + col) * P.N + j0) * 2 + ri0] =
@@ -915,7 +934,6 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision, int Sd)
     const size_t bt_spin = (size_t)kNS * W * 2 * nmax * kpad_max;
     c->w_oz_at.ensure(at_spin * c->nspin * 2);
     c->w_oz_bt.ensure(bt_spin * c->nspin * 2);
-    c->w_oz_bs.ensure((size_t)kNS * 2 * nmax * W * p_pad * 2);
     c->w_oz_S.ensure((size_t)W * nmax * nmax * sizeof(double2));
     c->w_oz_key.ensure((size_t)W * sizeof(unsigned long long));
     c->w_oz_int.ensure((size_t)(2 * W * (2 + nmax) + W) * sizeof(int) + 256);
@@ -970,38 +988,35 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision, int Sd)
         }
         {
             StageScope sc(c, "theta_slice", 2);
-            const size_t smem = (size_t)kNS * twoN * kSliceRows;
-            LOAF_CUDA(cudaFuncSetAttribute(slice_phi_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             unsigned long long* key = c->w_oz_key.as<unsigned long long>();
             LOAF_CUDA(cudaMemsetAsync(key, 0, (size_t)W * sizeof(unsigned long long), c->stream));
             phi_max_kernel<<<W * kMaxSplit, 256, 0, c->stream>>>(M, N, c->ntot, sd.col0, phi, key);
             LOAF_LAUNCH_CHECK();
-            slice_phi_kernel<<<dim3(W, ceil_div(p_pad, kSliceRows)), 256, smem, c->stream>>>(
-                M, N, c->ntot, sd.col0, p_pad, kpad, W, phi, key, At + at_spin * s, c->w_oz_bs.as<uint16_t>(),
-                wexp(s));
+            slice_phi_kernel<<<dim3(W, ceil_div(M, kSliceRows)), 256, 0, c->stream>>>(
+                M, N, c->ntot, sd.col0, kpad, W, phi, key, At + at_spin * s, wexp(s));
             LOAF_LAUNCH_CHECK();
         }
         {
-            // S = Phi_T^T phi computed as its transpose: rows (2w + ri) N + j of the
-            // walker slices (128-row tiles, all used), columns i of Phi_T (80-wide
+            // S = Phi_T^T phi computed as its transpose: rows w kpad + 2j + ri of the
+            // walker slices read MN-major from the Theta GEMM's layout (128-row
+            // tiles; rows 2j + ri >= 2N are zero), columns i of Phi_T (80-wide
             // tiles, little padding for N <= 80), K = basis
             StageScope sc(c, "overlap_tc", 1);
             CUtensorMap mA, mB;
-            map_slices(&mA, c->w_oz_bs.ptr, p_pad, p_pad, (uint64_t)twoN * W, 1, kOBM);
+            map_slices_mn(&mA, At + at_spin * s, (uint64_t)W * kpad, M);
             map_slices(&mB, sd.oz_trialT.ptr, p_pad, p_pad, N, 1, kOBN);
             OzParams P{};
-            P.n_rt = ceil_div((long)twoN * W, kOBM);
+            P.n_rt = ceil_div((long)kpad * W, kOBM);
             P.n_ct = ceil_div(N, kOBN);
             P.n_b = 1;
             P.nk = ceil_div(p_pad, kOBK);
-            P.a_batched = 0;
-            P.idesc = tc::idesc_f16(kOBM, kOBN, false);
+            P.idesc = tc::idesc_f16(kOBM, kOBN, false) | tc::kIdescAMnMajor;
+            P.kpad = kpad;
             P.err = err;
             P.mode = 0;
             P.M = M; P.N = N; P.ntot = c->ntot; P.col0 = sd.col0; P.r_pad = r_pad; P.W = W;
             P.nrb = dg.nrb; P.nkb = dg.nkb;
-            P.rows_valid = twoN * W;
+            P.rows_valid = kpad * W;
             P.cols_valid = N;
             P.row_exp = sd.oz_rowexp.as<int>();
             P.wexp = wexp(s);
@@ -1061,14 +1076,13 @@ void run_theta_tc(loaf_ctx* c, int W, const double2* phi, int precision, int Sd)
         const int N = sd.N, twoN = 2 * N, kpad = (twoN + 15) / 16 * 16;
         StageScope sc(c, "theta_tc", 1);
         CUtensorMap mA, mB;
-        map_slices(&mA, At + at_spin * s, twoN, kpad, M, W, kOBM);
+        map_slices_rows(&mA, At + at_spin * s, twoN, kpad, W, M);
         map_slices(&mB, Bt + bt_spin * s, twoN, kpad, twoN, W, kOBN);
         OzParams P{};
         P.n_rt = ceil_div(M, kOBM);
         P.n_ct = ceil_div(twoN, kOBN);
         P.n_b = W;
         P.nk = ceil_div(twoN, kOBK);
-        P.a_batched = 1;
         P.idesc = tc::idesc_f16(kOBM, kOBN, false);
         P.err = err;
         P.mode = 1;

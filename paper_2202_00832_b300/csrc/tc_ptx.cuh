@@ -314,12 +314,28 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t row_bytes
     return d;
 }
 
+// Matrix descriptor of an MN-major operand with the 128-byte swizzle: rows of
+// 64 16-bit values along M (or N), one row per k, as a TMA box of 64 x k
+// with SWIZZLE_128B writes them; lbo = bytes from one 64-wide block along
+// M/N to the next, sbo = bytes from one group of 8 k-rows to the next.
+__device__ __forceinline__ uint64_t smem_desc_mn128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version
+    d |= (uint64_t)2 << 61;  // 128-byte swizzle
+    return d;
+}
+
 // Instruction descriptor, kind::f16: D = F32, A/B = F16 (0) or BF16 (1),
 // both K-major, dense, M x N tile.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
     return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// bit of the kind::f16 instruction descriptor that marks A as MN-major
+constexpr uint32_t kIdescAMnMajor = 1u << 15;
 // kind::tf32: D = F32, A/B format TF32 (2), both K-major, dense, M x N tile.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
