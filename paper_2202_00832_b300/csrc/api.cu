@@ -171,16 +171,19 @@ void StageScope::end() {
     idx = -1;
 }
 
+// wait for one submitted call and fold its flags into the context's
+static void harvest_slot(loaf_ctx* c, loaf_ctx::AsyncSlot& s) {
+    if (!s.pending) return;
+    LOAF_CUDA(cudaEventSynchronize(s.done));
+    c->async_flags[0] = std::max(c->async_flags[0], s.h_flags[0]);
+    c->async_flags[1] |= s.h_flags[1];
+    s.pending = false;
+}
+
 void drain_submitted(loaf_ctx* c) {
     const int a = c->aslot_next;  // the oldest call first
-    for (int k = 0; k < 2; ++k) {
-        loaf_ctx::AsyncSlot& s = c->aslot[a ^ k];
-        if (!s.pending) continue;
-        LOAF_CUDA(cudaEventSynchronize(s.done));
-        c->async_flags[0] = std::max(c->async_flags[0], s.h_flags[0]);
-        c->async_flags[1] |= s.h_flags[1];
-        s.pending = false;
-    }
+    harvest_slot(c, c->aslot[a]);
+    harvest_slot(c, c->aslot[a ^ 1]);
 }
 
 void prof_collect(loaf_ctx* c) {
@@ -603,7 +606,9 @@ loaf_status walkers_energy_submit(loaf_ctx* c, int W, const void* phi, int mode,
             c->async_key = key;
         }
         loaf_ctx::AsyncSlot& sl = c->aslot[c->aslot_next];
-        if (sl.pending) drain_submitted(c);  // the call two back used this slot's buffers
+        // only the call two back, which used this slot's buffers: the previous
+        // call keeps computing while this one uploads
+        harvest_slot(c, sl);
         if (!sl.done) {
             LOAF_CUDA(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
             LOAF_CUDA(cudaMallocHost(&sl.h_flags, 2 * sizeof(int)));
